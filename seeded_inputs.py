@@ -1,0 +1,76 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds workload sizes and random draws only -- none of the
+method's arithmetic -- so that both the CUDA path and the oracle can take the
+identical inputs without sharing any code of the method.
+
+Rayleigh-Benard initial state recipe (used by both sides): the buoyancy on
+the scale-1 grid is b = 1 - z + A xi(z, x) z (1 - z) with A = 1e-3 and xi
+i.i.d. standard normals of shape (N_z, N_x) (row = Chebyshev node in
+ascending z, column = Fourier node), drawn in C order from
+``numpy.random.default_rng(seed).standard_normal``.  Each side turns xi into
+coefficients with its own transforms.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+NOISE_AMPLITUDE = 1e-3
+
+
+@dataclass(frozen=True)
+class RBWorkload:
+    name: str
+    n_x: int
+    n_z: int
+    Ra: float
+    Pr: float = 1.0
+    L_x: float = 4.0
+    scheme: str = "RK222"
+    dt: float = 1e-3
+    steps: int = 100
+    seed: int = 42
+    n_y: int = 1
+    L_y: float = 4.0
+
+    @property
+    def dof(self):
+        """Real unknowns S * N_x * N_y * N_z (S = 7 fields in 2D, 9 in 3D)."""
+        s = 7 if self.n_y == 1 else 9
+        return s * self.n_x * self.n_y * self.n_z
+
+    @property
+    def modes(self):
+        return self.n_x * self.n_y * self.n_z
+
+
+# The five workloads.  Small one: 2D 64x32 RK222.  Headline: 2D 512x256 SBDF2.
+WORKLOADS = {
+    "rb2d_64x32_rk222": RBWorkload("rb2d_64x32_rk222", 64, 32, 1e6, scheme="RK222",
+                                   dt=1e-3, steps=100),
+    "rb2d_512x256_sbdf2": RBWorkload("rb2d_512x256_sbdf2", 512, 256, 1e8, scheme="SBDF2",
+                                     dt=1e-4, steps=1000),
+    "rb3d_256x256x128_rk222": RBWorkload("rb3d_256x256x128_rk222", 256, 128, 1e7,
+                                         scheme="RK222", dt=5e-4, steps=200, n_y=256),
+    "rb2d_256x128_rk222_adjoint": RBWorkload("rb2d_256x128_rk222_adjoint", 256, 128, 1e6,
+                                             scheme="RK222", dt=1e-3, steps=500),
+}
+
+
+def rb_noise(seed, n_z, n_x):
+    """xi[z, x]: i.i.d. standard normals on the scale-1 grid."""
+    return np.random.default_rng(seed).standard_normal((n_z, n_x))
+
+
+def batched_workloads(count=64, seed=7):
+    """Uneven batch: N_x from {64..512}, N_z from {32..256}, Ra log-uniform."""
+    rng = np.random.default_rng(seed)
+    nx = rng.choice([64, 128, 256, 512], size=count)
+    nz = rng.choice([32, 64, 128, 256], size=count)
+    ra = 10.0 ** rng.uniform(5.0, 8.0, size=count)
+    out = []
+    for i in range(count):
+        out.append(RBWorkload(f"batch{i}", int(nx[i]), int(nz[i]), float(ra[i]),
+                              scheme="RK222", dt=1e-3 * 32.0 / float(nz[i]),
+                              steps=500, seed=1000 + i))
+    return out

@@ -1,0 +1,126 @@
+"""Pins for oracle.timesteppers on linear problems with closed-form solutions.
+
+* a z-independent diffusion mode cos(k x) under Neumann walls is a T_0-only
+  polynomial, so the tau discretisation is exact and the step must multiply
+  it by the scheme's amplification factor, to rounding:
+  RK222 (ARS(2,2,2)): R(h) = (1 + (2 gamma - 1) h) / (1 + gamma h)^2,
+  SBDF1 then SBDF2: x_1 = x_0 / (1 + h), (3/2 + h) x_{n+1} = 2 x_n - x_{n-1} / 2;
+* a Dirichlet mode sin(pi z) cos(k x) decays at lambda = kappa (k^2 + pi^2)
+  to spectral accuracy, and the time error is second order;
+* the tau polynomial U_{N-1} has zero integral for even N, so the Neumann
+  diffusion step conserves the mean exactly (Sec. "Integration").
+"""
+import numpy as np
+import pytest
+
+from oracle import bases
+from oracle.problem import TauProblem, LinearPencilSystem
+from oracle import timesteppers as ts
+
+KAPPA = 0.05
+L_X = 4.0
+
+
+def diffusion(N, bc="neumann"):
+    pr = TauProblem(["c", "cz"], N, 0.0, 1.0)
+    pr.add_equation("cz_def", L_terms=[("c", "dz", 1.0), ("cz", "I", -1.0)])
+    pr.add_equation("c", M_terms=[("c", "I", 1.0)],
+                    L_terms=[("c", "I", lambda k: KAPPA * k * k), ("cz", "dz", -KAPPA)])
+    v = "cz" if bc == "neumann" else "c"
+    pr.add_bc(v, "left", value=0.0)
+    pr.add_bc(v, "right", value=0.0)
+    return pr
+
+
+def _mode_state(sysm, N, n_kx, zfun, dzfun):
+    z = bases.chebyshev_grid(N)
+    X = np.zeros((2, sysm.P, N), complex)
+    X[0, n_kx] = 0.5 * bases.chebyshev_forward(zfun(z), N)    # cos(k x) -> 1/2 e^{ikx}
+    X[1, n_kx] = 0.5 * bases.chebyshev_forward(dzfun(z), N)
+    return X
+
+
+def R_rk222(h):
+    g = ts.GAMMA
+    return (1 + (2 * g - 1) * h) / (1 + g * h) ** 2
+
+
+def test_ars222_tableau_order_conditions():
+    H, A, c = ts.RK222["H"], ts.RK222["A"], ts.RK222["c"]
+    b = H[-1]                                   # stiffly accurate: weights = last row
+    assert np.allclose(A[-1, :-1].sum(), 1.0) and np.allclose(b.sum(), 1.0)
+    assert np.allclose(b @ c, 0.5)             # second-order condition (implicit)
+    assert np.allclose(A[-1] @ c, 0.5)         # second-order condition (explicit)
+    assert np.allclose(H.sum(axis=1), c) and np.allclose(A.sum(axis=1), c)
+
+
+@pytest.mark.parametrize("N", [8, 16])
+def test_rk222_neumann_mode_exact_amplification(N):
+    kx = 2 * np.pi * np.arange(4) / L_X
+    sysm = LinearPencilSystem(diffusion(N), kx)
+    X = _mode_state(sysm, N, 3, np.ones_like, np.zeros_like)
+    stepper = ts.RungeKuttaIMEX(sysm)
+    dt = 0.3
+    amp0 = X[0, 3, 0]
+    for n in range(1, 8):
+        X = stepper.step(X, dt)
+        h = KAPPA * kx[3] ** 2 * dt
+        assert abs(X[0, 3, 0] - amp0 * R_rk222(h) ** n) < 1e-14
+        assert np.abs(X[0, 3, 1:]).max() < 1e-14 and np.abs(X[1]).max() < 1e-13
+
+
+def test_sbdf2_neumann_mode_recurrence():
+    N = 12
+    kx = 2 * np.pi * np.arange(3) / L_X
+    sysm = LinearPencilSystem(diffusion(N), kx)
+    X = _mode_state(sysm, N, 2, np.ones_like, np.zeros_like)
+    stepper = ts.SBDF(sysm, order=2)
+    dt = 0.2
+    h = KAPPA * kx[2] ** 2 * dt
+    seq = [X[0, 2, 0]]
+    seq.append(seq[0] / (1 + h))
+    for n in range(6):
+        seq.append((2 * seq[-1] - 0.5 * seq[-2]) / (1.5 + h))
+    for n in range(1, 8):
+        X = stepper.step(X, dt)
+        assert abs(X[0, 2, 0] - seq[n]) < 1e-14
+
+
+def test_dirichlet_mode_spectral_accuracy_and_second_order():
+    N = 32
+    kx = 2 * np.pi * np.arange(3) / L_X
+    sysm = LinearPencilSystem(diffusion(N, "dirichlet"), kx)
+    lam = KAPPA * (kx[1] ** 2 + np.pi ** 2)
+    T = 1.0
+    errs = {}
+    for name, make in [("rk", lambda: ts.RungeKuttaIMEX(sysm)), ("sbdf", lambda: ts.SBDF(sysm, 2))]:
+        errs[name] = []
+        for nsteps in (20, 40, 80):
+            dt = T / nsteps
+            X = _mode_state(sysm, N, 1, lambda z: np.sin(np.pi * z), lambda z: np.pi * np.cos(np.pi * z))
+            a0 = X[0, 1].copy()
+            st = make()
+            for _ in range(nsteps):
+                X = st.step(X, dt)
+            if name == "rk":
+                # spectral accuracy: time-discrete amplification of the exact mode
+                assert np.abs(X[0, 1] - a0 * R_rk222(lam * dt) ** nsteps).max() < 1e-12
+            errs[name].append(np.abs(X[0, 1] - a0 * np.exp(-lam * T)).max())
+        r = np.array(errs[name][:-1]) / np.array(errs[name][1:])
+        assert np.all((r > 3.6) & (r < 4.4)), (name, r)
+
+
+def test_neumann_diffusion_conserves_mean_even_N():
+    N = 16
+    sysm = LinearPencilSystem(diffusion(N), np.array([0.0]))
+    z = bases.chebyshev_grid(N)
+    X = np.zeros((2, 1, N), complex)
+    X[0, 0] = bases.chebyshev_forward(2 + np.cos(np.pi * z) + 0.3 * np.cos(2 * np.pi * z), N)
+    X[1, 0] = bases.chebyshev_forward(-np.pi * np.sin(np.pi * z) - 0.6 * np.pi * np.sin(2 * np.pi * z), N)
+    integ = bases.cheb_integrate_vector(N) * 0.5          # int_0^1 dz
+    m0 = integ @ X[0, 0]
+    st = ts.RungeKuttaIMEX(sysm)
+    for _ in range(20):
+        X = st.step(X, 0.05)
+    assert abs(integ @ X[0, 0] - m0) < 1e-14
+    assert abs(m0 - 2.0) < 1e-11          # truncation of cos(pi z) at N = 16
