@@ -1,0 +1,279 @@
+"""Benchmark: DOF*steps/s of the IMEX spectral-tau step on GB300.
+
+Workload (default): 2D Rayleigh-Benard, Fourier x N_x = 512 (L_x = 4) by
+Chebyshev z N_z = 256, Ra = 1e8, Pr = 1, 3/2 dealiasing, SBDF2 with
+dt = 1e-4, seeded synthetic initial state.  One "step" is one full IMEX
+step: dealiased transforms and products of the advective RHS, right-hand
+side assembly and one banded FP64 tau solve per Fourier pencil.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and
+torch.cuda.synchronize(), timed with CUDA events on the library's stream;
+the step's working set (factor + state, > 129 MB) is larger than L2.
+The pencil-solve kernel is timed per launch with CUDA events inside the
+timed region for the roofline entry.  Clocks are sampled with nvidia-smi
+while the timed region runs.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+import seeded_inputs as si
+
+METRIC = "DOF·steps/s of IMEX step at stated error vs FP64 form; adjoint/forward time"
+UNIT = "DOF*steps/s"
+WORKLOAD = "rb2d_512x256_sbdf2"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# FP64 FMA throughput of this GB300 pool, measured with a dependent-free
+# DFMA stream over all SMs (2 flops per FMA): 1.008 TFLOP/s at 1995 MHz.
+FP64_PEAK_TFLOPS = 1.008
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def solve_flops_bytes(s):
+    """Algorithmic FP64 flops and bytes of one pencil-solve launch.
+
+    Per pencil and per real right-hand side (real and imaginary parts share
+    the real factor): forward substitution kl FMAs per row, back
+    substitution kl + ku FMAs per row and one multiply by 1/U_jj; plus the
+    right-hand-side assembly (one CSR matvec with the pattern's nnz, the
+    combination of stored vectors) and the epilogue matvec M~ X~.
+    Bytes: the factor (L multipliers, pivots, U band) plus the vectors read
+    and written, all FP64.
+    """
+    n, kl, ku = s.band()
+    P = s.P
+    nnz = len(s.assembly["indices"])
+    nnz_M = int(np.count_nonzero(s.assembly["M"][1]))
+    solve = 2 * (2 * kl + ku) * n + n                  # per real RHS
+    flops = P * 2 * solve + P * 2 * 2 * nnz_M          # + epilogue M~ X~ (complex vector)
+    flops += P * 2 * 2 * 3 * n                         # prologue combination of 2 vectors + F rows
+    factor_bytes = P * n * (kl + (kl + ku + 1)) * 8 + P * n
+    vec_bytes = P * n * 16 * 5                         # 2 stored vectors in, X~, X, M~X~ out
+    vec_bytes += P * nnz_M * 8 + 3 * P * s.Nz * 16 * 2  # M~ values, two F coefficient arrays
+    return flops, factor_bytes + vec_bytes
+
+
+def run_ours(args):
+    import torch
+    distributed = int(os.environ.get("WORLD_SIZE", "1")) > 1
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if distributed:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1905_10388_gb300 import build as _b  # noqa: F401
+    from paper_1905_10388_gb300.solver import Context, RBSolver
+    w = si.WORKLOADS[args.workload]
+    ctx = Context(local, torch.cuda.current_stream(local).cuda_stream)
+    s = RBSolver(ctx, w.n_x, w.n_z, w.Ra, w.Pr, w.L_x, scheme=w.scheme, precision=args.precision)
+    s.factor(w.dt)
+    xi = si.rb_noise(w.seed + rank, w.n_z, w.n_x)
+    s.set_initial_state(xi)
+    s.step(args.warmup)
+    s.sync()
+    stages = 2 if w.scheme == "RK222" else 1
+    s.set_timing(args.steps * stages)
+    stream = torch.cuda.current_stream(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    if distributed:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(args.steps, graph=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if distributed:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    s.sync()
+    solve_ms, solve_launches = s.solve_time()
+    if distributed:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.dof * args.steps / (ms * 1e-3)
+
+    # end to end through the public API with host buffers: upload the state,
+    # K steps each followed by a device-to-host read of the buoyancy field
+    X0 = s.get_state()
+    host_state = [np.ascontiguousarray(X0[i]) for i in range(s.S)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_state(host_state)
+    for _ in range(args.steps):
+        s.step(1)
+        _ = s.get_field("b")
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    state_bytes = s.S * s.P * s.Nz * 16
+    e2e = {"value": world * w.dof * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": s.P * s.Nz * 16}
+
+    flops, nbytes = solve_flops_bytes(s)
+    achieved = flops / (solve_ms * 1e-3) / 1e12
+    peaks = measured_peaks()
+    roof = {"kernel": "k_pencil_solve", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "measured FP64 DFMA stream (this pool)",
+            "ms_per_launch": solve_ms, "launches": solve_launches,
+            "hbm_achieved_gbs": nbytes / (solve_ms * 1e-3) / 1e9,
+            "hbm_peak_gbs": peaks.get("hbm_gbs")}
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic (seeded Rayleigh-Benard initial state)",
+            "config": {"workload": args.workload, "n_x": w.n_x, "n_z": w.n_z, "Ra": w.Ra, "Pr": w.Pr,
+                       "scheme": w.scheme, "dt": w.dt, "dof": w.dof, "precision": args.precision,
+                       "parallelism": f"replicas{world}", "l2": "working set > L2 (factor ~147 MB)"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": 4 * args.steps if stages == 1 else 8 * args.steps,
+            "clocks": clk,
+        }
+    ctx.close()
+    if distributed:
+        torch.distributed.destroy_process_group()
+    return result
+
+
+def oracle_rate(workload, steps_timed, warm):
+    """The FP64 CPU oracle on the same workload: returns (DOF*steps/s, seconds)."""
+    from oracle import rb as orb
+    from oracle import timesteppers as ots
+    w = si.WORKLOADS[workload]
+    sysr = orb.RB2D(w.n_x, w.n_z, w.Ra, w.Pr, w.L_x)
+    X = sysr.initial_state(si.rb_noise(w.seed, w.n_z, w.n_x))
+    st = ots.RungeKuttaIMEX(sysr) if w.scheme == "RK222" else ots.SBDF(sysr, 2)
+    for _ in range(warm):
+        X = st.step(X, w.dt)
+    t0 = time.perf_counter()
+    for _ in range(steps_timed):
+        X = st.step(X, w.dt)
+    dt = time.perf_counter() - t0
+    return w.dof * steps_timed / dt, dt
+
+
+def cpu_baseline(workload, steps=2):
+    rate, secs = oracle_rate(workload, steps, warm=2)
+    return {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{steps} steps of {workload} after 2 warm-up steps (factorizations), "
+                      f"{secs:.1f} s; numpy/scipy FP64, SuperLU single-threaded"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    steps = max(1, min(args.steps, 3))
+    rate, secs = oracle_rate(args.workload, steps, warm=max(1, min(args.warmup, 2)))
+    w = si.WORKLOADS[args.workload]
+    return {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": secs / steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "n_x": w.n_x, "n_z": w.n_z, "scheme": w.scheme},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{steps} steps after warm-up, {secs:.1f} s"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        res = run_ours(args)
+        if res is not None and not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+            res["cpu_baseline"] = cpu_baseline(args.workload)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * spectau.h -- C ABI of the GB300 (sm_103a) IMEX spectral-tau timestep.
+ *
+ * The library advances first-order problems  M dt(X) + L X = F(X)  on a
+ * Fourier(x) x Chebyshev(z) domain with the sparse generalized tau method
+ * (paper Sec. "A general sparse tau method", Sec. "Initial value solver",
+ * Eq. ivp).  Coefficient space splits into independent pencils, one per
+ * Fourier wavenumber k_x (Sec. "Linear boundary value solver": the pencil
+ * systems couple only through F).  Each pencil holds S variables x N_z
+ * Chebyshev modes, n = S N_z unknowns.
+ *
+ * Conventions for every entry point:
+ *  - every call returns an sp_status; on failure sp_last_error() returns a
+ *    message describing the first error of the last call;
+ *  - host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership;
+ *  - device memory owned by the library is released by sp_destroy;
+ *  - work is queued on the context's CUDA stream and runs asynchronously;
+ *    device-side failures (singular pivot, non-finite state, bounded wait
+ *    expiry) are latched in a device status word read by sp_sync_status;
+ *  - a pointer passed with on_device = 1 must be device memory of the
+ *    context's device, valid until the stream reaches the queued work;
+ *  - there is no CPU fallback: without a usable CUDA device sp_create fails.
+ *
+ * Layouts (all little-endian, C order):
+ *  - coefficient layout 'c': complex FP64 interleaved (re, im), indexed
+ *    [p][m], p = 0 .. P-1 the stored k_x >= 0 modes (k_x = 2 pi p / L_x,
+ *    Nyquist dropped, Sec. "Fourier basis"), m = 0 .. N_z-1 the Chebyshev
+ *    mode (Sec. "Chebyshev basis");
+ *  - grid layout 'g': real FP64 indexed [iz][ix] on the Gauss-Chebyshev nodes
+ *    z_i = a + (b - a)(1 - cos(pi (i + 1/2) / N_gz)) / 2 (ascending) and
+ *    the Fourier nodes x_i = L_x i / N_gx.
+ */
+#ifndef SPECTAU_H
+#define SPECTAU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sp_ctx sp_ctx;
+
+typedef enum {
+  SP_OK = 0,
+  SP_ERR_ARG = -1,           /* invalid argument (checked on the host)        */
+  SP_ERR_CUDA = -2,          /* a CUDA runtime call failed                    */
+  SP_ERR_OOM = -3,           /* device allocation failed                      */
+  SP_ERR_SINGULAR = -4,      /* zero pivot in a pencil factorization          */
+  SP_ERR_NOT_FACTORED = -5,  /* sp_step with a dt that was not factored       */
+  SP_ERR_NONFINITE = -6,     /* NaN or Inf in the state after a step          */
+  SP_ERR_TIMEOUT = -7,       /* a bounded device wait expired                 */
+  SP_ERR_STATE = -8          /* call out of order (e.g. step before setup)    */
+} sp_status;
+
+typedef enum { SP_FOURIER = 0, SP_CHEBYSHEV = 1 } sp_basis_kind;
+
+/* One axis (Sec. "Spectral bases"): kind, coefficient count N_c, interval
+ * [a, b] (Fourier: length b - a), dealias scale num/den (Sec. "Scaled
+ * transforms & dealiasing"; 3/2 dealiases quadratic products). */
+typedef struct {
+  int32_t kind;
+  int32_t n_coeff;
+  double a, b;
+  int32_t dealias_num, dealias_den;
+} sp_basis;
+
+/* IMEX schemes (Sec. "Timesteppers"): RK222 = ARS(2,2,2) and RK111 of
+ * Ascher, Ruuth & Spiteri (1997); SBDF1/SBDF2 of Wang & Ruuth (2008).
+ * SBDF2 takes its first step as SBDF1 (lower-order start). */
+typedef enum { SP_RK222 = 0, SP_SBDF1 = 1, SP_SBDF2 = 2, SP_RK111 = 3 } sp_scheme;
+
+/* FP64: every stage in FP64.  MIXED: transforms and grid products in FP32,
+ * pencil factorization, right-hand-side assembly and solves in FP64. */
+typedef enum { SP_PREC_FP64 = 0, SP_PREC_MIXED = 1 } sp_precision;
+
+/* Operators in bilinear right-hand-side terms. */
+typedef enum { SP_OP_ID = 0, SP_OP_DX = 1 } sp_op;
+
+/* Create a context on CUDA device `device`, queueing work on `cuda_stream`
+ * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
+ * legacy default stream).  *out receives the handle. */
+sp_status sp_create(sp_ctx** out, int device, void* cuda_stream);
+
+/* Synchronize the stream and release every resource of the context. */
+sp_status sp_destroy(sp_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none).  The
+ * string is owned by the context and valid until its next call. */
+const char* sp_last_error(const sp_ctx* ctx);
+
+/* Declare a problem (Sec. "Domains", Sec. "Problems").  ndim = 2:
+ * bases[0] Fourier (x), bases[1] Chebyshev (z, the coupled axis, last).
+ * nvars = S = number of first-order variables = number of equations.
+ * Sizes supported by the kernels: N_x even with N_gx = N_x * scale of the
+ * form 2^k or 3*2^k (16 <= N_gx <= 4096), N_z with N_gz likewise
+ * (8 <= N_gz <= 1536), S <= 16.  *problem_id receives the handle. */
+sp_status sp_add_problem(sp_ctx* ctx, int ndim, const sp_basis* bases, int nvars,
+                         int scheme, int precision, int* problem_id);
+
+/* Pencil layout and preconditioners (Sec. "Matrix construction",
+ * Sec. "Linear boundary value solver", Appendix "Dirichlet recombination
+ * matrices"):
+ *  col_map[v*N_z + m]  column of variable v, mode m in the pencil system;
+ *  row_map[e*N_z + m]  row that receives mode m of equation e's
+ *                      left-preconditioned right-hand side, or -1 for a
+ *                      dropped tau row;
+ *  var_recombine[v]    1: the solved coefficients are in the Dirichlet
+ *                      basis D_n = T_n - T_{n-2}, so x_m = x~_m - x~_{m+2};
+ *  var_phase[v]        q: true coefficient = i^q x solved coefficient;
+ *  eq_differential[e]  1: equation rows are T-to-U converted,
+ *                      (P^L f)_m = f_m/(2 - delta_m0) - f_{m+2}/2;
+ *  eq_phase[e]         q: equation rows are multiplied by i^(-q);
+ *  bc_rows[q], q < nbc rows holding boundary conditions;
+ *  bc_values[(p*nbc + q)*2 + {0,1}]  complex value of boundary row q on
+ *                      pencil p (already multiplied by its row phase).
+ * Row and column indices are in [0, n) and must form a permutation. */
+sp_status sp_set_layout(sp_ctx* ctx, int problem, const int32_t* col_map,
+                        const int32_t* row_map, const int32_t* var_recombine,
+                        const int32_t* var_phase, const int32_t* eq_differential,
+                        const int32_t* eq_phase, int nbc, const int32_t* bc_rows,
+                        const double* bc_values);
+
+/* Preconditioned pencil matrices M~_p = P^L M_p P^R and L~_p = P^L L_p P^R
+ * (Sec. "Linear boundary value solver"), real, for pencils
+ * [first_pencil, first_pencil + count), on one CSR pattern shared by all
+ * pencils (the union of the M and L patterns, Sec. "Matrix construction"):
+ * indptr[n+1], indices[nnz] (sorted, unique per row), M_values and L_values
+ * [count][nnz].  Every pencil must be set, with the same pattern, before
+ * sp_factor.  The band widths kl, ku are taken from the pattern. */
+sp_status sp_set_pencils(sp_ctx* ctx, int problem, int64_t first_pencil, int64_t count,
+                         int n, int64_t nnz, const int32_t* indptr, const int32_t* indices,
+                         const double* M_values, const double* L_values);
+
+/* Quadratic right-hand side as a sum of terms (Sec. "Arithmetic
+ * operators", products evaluated on the dealiased grid):
+ *   F[eq[t]] += coef[t] * op_a[t](var_a[t]) * op_b[t](var_b[t]),
+ * op in sp_op (DX = i k_x on the true coefficients). */
+sp_status sp_set_bilinear_rhs(sp_ctx* ctx, int problem, int nterms, const int32_t* eq,
+                              const double* coef, const int32_t* op_a, const int32_t* var_a,
+                              const int32_t* op_b, const int32_t* var_b);
+
+/* Factor every pencil for step size dt with banded LU and partial pivoting in
+ * FP64 (Sec. "Matrix solvers": factorize once, reuse while dt is fixed):
+ * RK schemes: M~ + dt H_ii L~ (one matrix, H_ii equal for all stages);
+ * SBDF2: (M~ + dt L~) for its first step and (3/2 M~ + dt L~) afterwards;
+ * SBDF1: M~ + dt L~.  A zero pivot latches SP_ERR_SINGULAR (read it with
+ * sp_sync_status, which also reports the first failing pencil). */
+sp_status sp_factor(sp_ctx* ctx, int problem, double dt);
+
+/* Set / get one variable of the state (Sec. "Initial conditions").
+ * layout 'c': P*N_z complex (re, im) doubles [p][m], true coefficients;
+ * layout 'g': N_z*N_x real doubles [iz][ix] on the scale-1 grid
+ * (forward-transformed on the device).  Setting a variable restarts
+ * multistep history (the next SBDF2 step is an SBDF1 step). */
+sp_status sp_set_field(sp_ctx* ctx, int problem, int var, const void* data, int on_device,
+                       char layout);
+sp_status sp_get_field(sp_ctx* ctx, int problem, int var, void* data, int on_device,
+                       char layout);
+
+/* dst_var := d/dz src_var in coefficient space, with the O(N) Chebyshev
+ * recurrence (Appendix "Differentiation and conversion matrices"; used to
+ * make first-order initial conditions consistent, Sec. "Initial
+ * conditions"). */
+sp_status sp_dz(sp_ctx* ctx, int problem, int src_var, int dst_var);
+
+/* Advance nsteps steps of size dt (Sec. "Time evolution").  dt must equal
+ * the dt of the last sp_factor (else SP_ERR_NOT_FACTORED).  Asynchronous. */
+sp_status sp_step(sp_ctx* ctx, int problem, double dt, int nsteps);
+
+/* Same as sp_step, but the stream work for the nsteps steps is recorded once
+ * into a CUDA graph and replayed; the graph is cached per (problem, dt,
+ * nsteps) and rebuilt when any of them changes. */
+sp_status sp_step_graph(sp_ctx* ctx, int problem, double dt, int nsteps);
+
+/* Wait for the stream and return the latched device status (SP_OK,
+ * SP_ERR_SINGULAR, SP_ERR_NONFINITE or SP_ERR_TIMEOUT); the latch is
+ * cleared.  *pencil (may be NULL) receives the first failing pencil or -1. */
+sp_status sp_sync_status(sp_ctx* ctx, int64_t* pencil);
+
+/* Transform nfields fields between coefficient and grid space at scale
+ * scale_num/scale_den along both axes (Sec. "Scaled transforms &
+ * dealiasing"): direction -1 = backward (in: 'c' layout [f][p][m] complex,
+ * out: grid [f][iz][ix] real, N_g = scale * N_c with zero padding),
+ * direction +1 = forward (in: grid, out: 'c', truncation to N_c).
+ * Arithmetic in the problem's transform precision; in/out are host
+ * (on_device = 0) or device (on_device = 1) FP64 arrays. */
+sp_status sp_transform(sp_ctx* ctx, int problem, const void* in, void* out, int nfields,
+                       int direction, int scale_num, int scale_den, int on_device);
+
+/* Evaluate the bilinear right-hand side of the current state and return its
+ * T coefficients per equation with nonlinear terms, [e][p][m] complex, in
+ * the order of first appearance in sp_set_bilinear_rhs (for testing). */
+sp_status sp_eval_rhs(sp_ctx* ctx, int problem, void* out_host, int* n_eq);
+
+/* Band widths of the pencil pattern: n, kl, ku (U holds kl + ku
+ * superdiagonals after pivoting). */
+sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku);
+
+/* Launch timing of the pencil-solve kernel (the step's dominant kernel):
+ * sp_set_timing reserves CUDA-event pairs for up to max_launches solve
+ * launches of sp_step (not of graph replays) and restarts the count
+ * (max_launches = 0 disables it); sp_last_solve_time waits for the stream and
+ * returns the mean duration in milliseconds of the recorded launches and
+ * their number.  Events are recorded on the context stream around each
+ * launch. */
+sp_status sp_set_timing(sp_ctx* ctx, int problem, int max_launches);
+sp_status sp_last_solve_time(sp_ctx* ctx, int problem, double* ms_per_launch, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPECTAU_H */

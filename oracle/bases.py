@@ -115,6 +115,37 @@ def chebyshev_backward(c, n_grid, axis=-1):
     return np.moveaxis(g, -1, axis)
 
 
+def chebyshev_forward_dct(g, n_coeff, axis=-1):
+    """Same definition as chebyshev_forward, computed with scipy's DCT-II.
+
+    With T_n(x_i) = (-1)^n cos(pi n (2i+1) / (2 N_g)) and scipy's
+    DCT-II y_n = 2 sum_i g_i cos(pi n (2i+1) / (2 N_g)):
+    c_n = (-1)^n (2 - delta_n0) / (2 N_g) y_n.  A second summation order,
+    used only to measure the rounding floor between two FP64 evaluations.
+    """
+    import scipy.fft as sf
+    g = np.moveaxis(np.asarray(g), axis, -1)
+    n_grid = g.shape[-1]
+    y = sf.dct(g, type=2, axis=-1)
+    w = np.full(n_grid, 1.0 / n_grid)
+    w[0] = 0.5 / n_grid
+    c = (y * w * (-1.0) ** np.arange(n_grid))[..., :n_coeff]
+    return np.moveaxis(c, -1, axis)
+
+
+def chebyshev_backward_dct(c, n_grid, axis=-1):
+    """Same definition as chebyshev_backward, computed with scipy's DCT-III
+    (y_k = d_0 + 2 sum_{n>=1} d_n cos(pi n (2k+1) / (2 N_g)), d_n = (-1)^n c_n)."""
+    import scipy.fft as sf
+    c = np.moveaxis(np.asarray(c), axis, -1)
+    n_c = c.shape[-1]
+    d = np.zeros(c.shape[:-1] + (n_grid,), dtype=np.result_type(c, np.float64))
+    d[..., :n_c] = c * (-1.0) ** np.arange(n_c)
+    d[..., 0] *= 2.0
+    g = sf.dct(d, type=3, axis=-1) / 2.0
+    return np.moveaxis(g, -1, axis)
+
+
 def cheb_D_TT(n):
     """T-to-T derivative matrix on [-1, 1] (dense upper triangular)."""
     D = np.zeros((n, n))

@@ -69,7 +69,7 @@ class RB2D:
     Chebyshev mode.
     """
 
-    def __init__(self, n_x, n_z, Ra, Pr=1.0, L_x=4.0, dealias=1.5):
+    def __init__(self, n_x, n_z, Ra, Pr=1.0, L_x=4.0, dealias=1.5, cheb_method="mmt"):
         self.Nx, self.Nz, self.Lx = int(n_x), int(n_z), float(L_x)
         self.Ra, self.Pr = float(Ra), float(Pr)
         self.problem, self.kappa, self.nu = rb_problem(self.Nz, self.Ra, self.Pr)
@@ -80,6 +80,12 @@ class RB2D:
         self.Ngz = int(round(dealias * self.Nz))
         self.var = {v: i for i, v in enumerate(RB_VARIABLES)}
         self._mats = None
+        # "mmt": explicit T_n(x_i) quadrature (default); "dct": scipy DCT, the
+        # same definition summed in another order (rounding-floor estimates)
+        if cheb_method == "dct":
+            self._cf, self._cb = bases.chebyshev_forward_dct, bases.chebyshev_backward_dct
+        else:
+            self._cf, self._cb = bases.chebyshev_forward, bases.chebyshev_backward
 
     # -- pencils ------------------------------------------------------------
     def matrices(self):
@@ -101,14 +107,14 @@ class RB2D:
         """Coefficients c[p, n] -> real grid g[z, x] (z backward first, then x)."""
         n_gx = self.Ngx if n_gx is None else n_gx
         n_gz = self.Ngz if n_gz is None else n_gz
-        gz = bases.chebyshev_backward(c, n_gz, axis=1)        # [p, zg]
+        gz = self._cb(c, n_gz, axis=1)                        # [p, zg]
         g = bases.fourier_backward(gz, n_gx, axis=0)          # [xg, zg]
         return g.T.copy()
 
     def to_coeff(self, g):
         """Real grid g[z, x] -> coefficients c[p, n] (x forward first, then z)."""
         fx = bases.fourier_forward(g, self.Nx, axis=1)        # [zg, p]
-        c = bases.chebyshev_forward(fx, self.Nz, axis=0)      # [n, p]
+        c = self._cf(fx, self.Nz, axis=0)                     # [n, p]
         return c.T.copy()
 
     def dx(self, c):
@@ -145,7 +151,7 @@ class RB2D:
         z = bases.chebyshev_grid(self.Nz)[:, None]
         b_grid = 1.0 - z + amplitude * noise * z * (1.0 - z)
         fx = bases.fourier_forward(b_grid, self.Nx, axis=1)          # [z, p]
-        cb = bases.chebyshev_forward(fx, self.Nz, axis=0).T          # [p, n]
+        cb = self._cf(fx, self.Nz, axis=0).T                         # [p, n]
         X = np.zeros((self.S, self.P, self.Nz), dtype=np.complex128)
         X[self.var["b"]] = cb
         X[self.var["bz"]] = bases.chebyshev_derivative(cb, 0.0, 1.0, axis=1)

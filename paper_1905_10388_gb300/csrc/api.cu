@@ -1,0 +1,942 @@
+// Host runtime behind the C ABI (include/spectau.h): problem objects,
+// validation, device tables, transform plans, factor/step orchestration,
+// CUDA-graph replay and launch timing.  No computation of the step happens
+// on the host; every stage is one of the kernels in band.cu / transforms.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+using namespace spectau;
+
+namespace {
+
+// ARS(2,2,2) of Ascher, Ruuth & Spiteri (1997), and RK111 (IMEX Euler):
+// implicit H and explicit A tableaux with an explicit first stage.
+struct Tableau {
+  int s;
+  double H[4][4];
+  double A[4][4];
+};
+
+Tableau make_tableau(int scheme) {
+  Tableau t{};
+  if (scheme == SP_RK222) {
+    const double g = 1.0 - 1.0 / std::sqrt(2.0), d = 1.0 - 1.0 / (2.0 * g);
+    t.s = 2;
+    t.H[1][1] = g;
+    t.H[2][1] = 1.0 - g;
+    t.H[2][2] = g;
+    t.A[1][0] = g;
+    t.A[2][0] = d;
+    t.A[2][1] = 1.0 - d;
+  } else {  // RK111
+    t.s = 1;
+    t.H[1][1] = 1.0;
+    t.A[1][0] = 1.0;
+  }
+  return t;
+}
+
+bool is_smooth_length(int N) {  // 2^k or 3 * 2^k
+  if (N <= 0) return false;
+  if (N % 3 == 0) N /= 3;
+  return (N & (N - 1)) == 0;
+}
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace
+
+struct Problem {
+  int ndim = 2, S = 0, scheme = 0, prec = 0;
+  sp_basis bx{}, bz{};
+  int Nx = 0, Nz = 0, P = 0, Ngx = 0, Ngz = 0;
+  double Lx = 0, za = 0, zb = 1;
+  // layout
+  bool has_layout = false;
+  std::vector<int32_t> col_map, row_map, var_rec, var_ph, eq_diff, eq_ph, bc_rows;
+  int nbc = 0;
+  std::vector<double> bc_values;
+  // pencils
+  int n = 0;
+  int64_t nnz = -1;
+  std::vector<int32_t> indptr, indices;
+  std::vector<double> Mv, Lv;
+  std::vector<uint8_t> pset;
+  int kl = 0, ku = 0;
+  // bilinear rhs
+  std::vector<int32_t> t_slot, t_fa, t_fb;
+  std::vector<double> t_coef;
+  std::vector<GridField> gfields;
+  std::vector<int32_t> nl_eqs;
+  // device
+  bool uploaded = false;
+  int32_t *d_indptr = nullptr, *d_indices = nullptr;
+  double *d_Mv = nullptr, *d_Lv = nullptr;
+  int32_t *d_col_map = nullptr, *d_row_map = nullptr, *d_var_rec = nullptr, *d_var_ph = nullptr;
+  int32_t *d_eq_diff = nullptr, *d_eq_ph = nullptr, *d_bc_rows = nullptr, *d_nl_eq = nullptr;
+  double2* d_bc_values = nullptr;
+  double* d_kx = nullptr;
+  int32_t *d_gvar = nullptr, *d_gop = nullptr, *d_tslot = nullptr, *d_tfa = nullptr, *d_tfb = nullptr;
+  double* d_tcoef = nullptr;
+  int32_t *d_ident = nullptr, *d_zero = nullptr;
+  double2 *d_Xt = nullptr, *d_Xc = nullptr;
+  double2* d_MX[2] = {nullptr, nullptr};
+  double2* d_LX[3] = {nullptr, nullptr, nullptr};
+  double2* d_Fc[3] = {nullptr, nullptr, nullptr};
+  void* d_gz = nullptr;
+  void* d_h = nullptr;
+  BandFactor fac[2];
+  int nfac = 0;
+  double fac_dt = 0;
+  bool factored = false;
+  int npad = 0, lpad = 0, upad = 0;
+  std::map<std::pair<int, int>, TransformPlan> plans;
+  // stepping state
+  int iteration = 0;
+  bool xt_valid = false, mx_valid = false;
+  // graphs
+  std::map<std::tuple<int, int, int, double>, cudaGraphExec_t> graphs;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+};
+
+struct sp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;
+  std::string err;
+  std::vector<std::unique_ptr<Problem>> probs;
+  DevStatus* d_status = nullptr;
+};
+
+namespace {
+
+sp_status fail(sp_ctx* c, sp_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? SP_ERR_OOM : SP_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+template <typename T>
+cudaError_t upload(T** p, const std::vector<T>& v, cudaStream_t s) {
+  cudaError_t e = dalloc(p, v.size());
+  if (e != cudaSuccess) return e;
+  if (v.empty()) return cudaSuccess;
+  e = cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+Problem* get(sp_ctx* ctx, int id) {
+  if (!ctx || id < 0 || id >= (int)ctx->probs.size()) return nullptr;
+  return ctx->probs[id].get();
+}
+
+// exp(-2 pi i t / N) and exp(-i pi k / (2N)) from libm in FP64
+sp_status make_plan(sp_ctx* ctx, Problem* pr, int Nc, int Ng, TransformPlan** out) {
+  auto key = std::make_pair(Nc, Ng);
+  auto it = pr->plans.find(key);
+  if (it != pr->plans.end()) {
+    *out = &it->second;
+    return SP_OK;
+  }
+  if (!is_smooth_length(Ng) || Ng < 4 || Ng % 2) return fail(ctx, SP_ERR_ARG, "unsupported grid size %d", Ng);
+  TransformPlan pl;
+  pl.Nc = Nc;
+  pl.Ng = Ng;
+  pl.radix3 = (Ng % 3 == 0);
+  std::vector<double2> tw(Ng), dq(Ng);
+  std::vector<float2> tw32(Ng), dq32(Ng);
+  const double pi = 3.14159265358979323846;
+  for (int t = 0; t < Ng; ++t) {
+    tw[t] = make_double2(std::cos(2.0 * pi * t / Ng), -std::sin(2.0 * pi * t / Ng));
+    dq[t] = make_double2(std::cos(pi * t / (2.0 * Ng)), -std::sin(pi * t / (2.0 * Ng)));
+    tw32[t] = make_float2((float)tw[t].x, (float)tw[t].y);
+    dq32[t] = make_float2((float)dq[t].x, (float)dq[t].y);
+  }
+  double2 *a, *b;
+  float2 *c, *d;
+  CK(upload(&a, tw, ctx->stream));
+  CK(upload(&b, dq, ctx->stream));
+  CK(upload(&c, tw32, ctx->stream));
+  CK(upload(&d, dq32, ctx->stream));
+  pl.tw64 = a;
+  pl.dct64 = b;
+  pl.tw32 = c;
+  pl.dct32 = d;
+  pr->plans[key] = pl;
+  *out = &pr->plans[key];
+  return SP_OK;
+}
+
+sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
+  if (pr->uploaded) return SP_OK;
+  if (!pr->has_layout) return fail(ctx, SP_ERR_STATE, "sp_set_layout has not been called");
+  if (pr->nnz < 0) return fail(ctx, SP_ERR_STATE, "sp_set_pencils has not been called");
+  for (int p = 0; p < pr->P; ++p)
+    if (!pr->pset[p]) return fail(ctx, SP_ERR_STATE, "pencil %d has no matrices", p);
+  cudaStream_t s = ctx->stream;
+  CK(upload(&pr->d_indptr, pr->indptr, s));
+  CK(upload(&pr->d_indices, pr->indices, s));
+  CK(upload(&pr->d_Mv, pr->Mv, s));
+  CK(upload(&pr->d_Lv, pr->Lv, s));
+  CK(upload(&pr->d_col_map, pr->col_map, s));
+  CK(upload(&pr->d_row_map, pr->row_map, s));
+  CK(upload(&pr->d_var_rec, pr->var_rec, s));
+  CK(upload(&pr->d_var_ph, pr->var_ph, s));
+  CK(upload(&pr->d_eq_diff, pr->eq_diff, s));
+  CK(upload(&pr->d_eq_ph, pr->eq_ph, s));
+  CK(upload(&pr->d_bc_rows, pr->bc_rows, s));
+  std::vector<double2> bcv(pr->bc_values.size() / 2);
+  for (size_t i = 0; i < bcv.size(); ++i) bcv[i] = make_double2(pr->bc_values[2 * i], pr->bc_values[2 * i + 1]);
+  CK(upload(&pr->d_bc_values, bcv, s));
+  std::vector<double> kx(pr->P);
+  for (int p = 0; p < pr->P; ++p) kx[p] = 2.0 * 3.14159265358979323846 * p / pr->Lx;
+  CK(upload(&pr->d_kx, kx, s));
+  std::vector<int32_t> gv, go;
+  for (auto& g : pr->gfields) { gv.push_back(g.var); go.push_back(g.op); }
+  CK(upload(&pr->d_gvar, gv, s));
+  CK(upload(&pr->d_gop, go, s));
+  CK(upload(&pr->d_tslot, pr->t_slot, s));
+  CK(upload(&pr->d_tfa, pr->t_fa, s));
+  CK(upload(&pr->d_tfb, pr->t_fb, s));
+  CK(upload(&pr->d_tcoef, pr->t_coef, s));
+  CK(upload(&pr->d_nl_eq, pr->nl_eqs, s));
+  std::vector<int32_t> ident(64), zero(64, 0);
+  for (int i = 0; i < 64; ++i) ident[i] = i;
+  CK(upload(&pr->d_ident, ident, s));
+  CK(upload(&pr->d_zero, zero, s));
+  const size_t nvec = (size_t)pr->P * pr->n;
+  CK(dalloc(&pr->d_Xt, nvec));
+  CK(dalloc(&pr->d_Xc, nvec));
+  CK(cudaMemsetAsync(pr->d_Xc, 0, nvec * sizeof(double2), s));
+  for (auto& b : pr->d_MX) CK(dalloc(&b, nvec));
+  for (auto& b : pr->d_LX) CK(dalloc(&b, nvec));
+  const int nl = std::max<int>(1, (int)pr->nl_eqs.size());
+  for (auto& b : pr->d_Fc) CK(dalloc(&b, (size_t)nl * pr->P * pr->Nz));
+  const size_t esz = pr->prec ? sizeof(float2) : sizeof(double2);
+  const int nf = std::max<int>(1, (int)pr->gfields.size());
+  CK(cudaMalloc(&pr->d_gz, (size_t)nf * pr->Ngz * pr->P * esz));
+  CK(cudaMalloc(&pr->d_h, (size_t)nl * pr->Ngz * pr->P * esz));
+  TransformPlan* tp;
+  sp_status st;
+  if ((st = make_plan(ctx, pr, pr->Nz, pr->Ngz, &tp)) != SP_OK) return st;
+  if ((st = make_plan(ctx, pr, pr->Nx, pr->Ngx, &tp)) != SP_OK) return st;
+  // band storage
+  const int kuu = pr->kl + pr->ku;
+  pr->npad = (pr->n + SOLVE_CHUNK - 1) / SOLVE_CHUNK * SOLVE_CHUNK;
+  pr->lpad = std::max(2, (pr->kl + 1) / 2 * 2);
+  pr->upad = kuu <= 31 ? 32 : 64;
+  for (auto& f : pr->fac) {
+    CK(dalloc(&f.L, (size_t)pr->P * pr->npad * pr->lpad));
+    CK(dalloc(&f.piv, (size_t)pr->P * pr->npad));
+    CK(dalloc(&f.U, (size_t)pr->P * pr->npad * pr->upad));
+  }
+  CK(cudaStreamSynchronize(s));
+  pr->uploaded = true;
+  return SP_OK;
+}
+
+void free_problem(Problem* pr) {
+  auto F = [](void* p) { if (p) cudaFree(p); };
+  F(pr->d_indptr); F(pr->d_indices); F(pr->d_Mv); F(pr->d_Lv); F(pr->d_col_map); F(pr->d_row_map);
+  F(pr->d_var_rec); F(pr->d_var_ph); F(pr->d_eq_diff); F(pr->d_eq_ph); F(pr->d_bc_rows); F(pr->d_nl_eq);
+  F(pr->d_bc_values); F(pr->d_kx); F(pr->d_gvar); F(pr->d_gop); F(pr->d_tslot); F(pr->d_tfa); F(pr->d_tfb);
+  F(pr->d_tcoef); F(pr->d_ident); F(pr->d_zero); F(pr->d_Xt); F(pr->d_Xc);
+  for (auto b : pr->d_MX) F(b);
+  for (auto b : pr->d_LX) F(b);
+  for (auto b : pr->d_Fc) F(b);
+  F(pr->d_gz); F(pr->d_h);
+  for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); }
+  for (auto& kv : pr->plans) { F(kv.second.tw64); F(kv.second.tw32); F(kv.second.dct64); F(kv.second.dct32); }
+  for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto e : pr->ev) cudaEventDestroy(e);
+}
+
+// F(X) for the current coefficient state: z backward -> x rows (products) -> z forward
+sp_status eval_rhs(sp_ctx* ctx, Problem* pr, cudaStream_t s, double2* fc_out) {
+  if (pr->nl_eqs.empty()) {
+    CK(cudaMemsetAsync(fc_out, 0, (size_t)pr->P * pr->Nz * sizeof(double2), s));
+    return SP_OK;
+  }
+  TransformPlan& pz = pr->plans.at({pr->Nz, pr->Ngz});
+  TransformPlan& px = pr->plans.at({pr->Nx, pr->Ngx});
+  const int nf = (int)pr->gfields.size(), ne = (int)pr->nl_eqs.size();
+  CK(launch_cheb_backward(s, pr->prec, pz, pr->P, nf, pr->d_gvar, pr->d_gop, pr->d_kx, pr->d_Xc,
+                          pr->P * pr->Nz, pr->d_gz));
+  CK(launch_fourier_rows(s, pr->prec, px, pr->Ngz, pr->P, 7, nf, pr->d_gz, nullptr, nullptr,
+                         (int)pr->t_slot.size(), pr->d_tslot, pr->d_tcoef, pr->d_tfa, pr->d_tfb, ne, pr->d_h));
+  CK(launch_cheb_forward(s, pr->prec, pz, pr->P, ne, pr->d_h, fc_out));
+  return SP_OK;
+}
+
+SolveArgs base_args(Problem* pr, sp_ctx* ctx, int fac) {
+  SolveArgs a{};
+  a.P = pr->P; a.n = pr->n; a.Nz = pr->Nz; a.S = pr->S; a.nbc = pr->nbc; a.nnz = (int)pr->nnz;
+  a.kl = pr->kl; a.kuu = pr->kl + pr->ku; a.npad = pr->npad; a.lpad = pr->lpad; a.upad = pr->upad;
+  a.Lf = pr->fac[fac].L; a.piv = pr->fac[fac].piv; a.Uf = pr->fac[fac].U;
+  a.indptr = pr->d_indptr; a.indices = pr->d_indices;
+  a.row_map = pr->d_row_map; a.col_map = pr->d_col_map;
+  a.var_recombine = pr->d_var_rec; a.var_phase = pr->d_var_ph;
+  a.eq_differential = pr->d_eq_diff; a.eq_phase = pr->d_eq_ph;
+  a.nl_eq = pr->d_nl_eq; a.n_nl = (int)pr->nl_eqs.size();
+  a.bc_rows = pr->d_bc_rows; a.bc_values = pr->d_bc_values;
+  a.status = ctx->d_status;
+  return a;
+}
+
+sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
+  const bool t = pr->timing && pr->ev_used + 2 <= pr->ev.size();
+  if (t) CK(cudaEventRecord(pr->ev[pr->ev_used], s));
+  CK(launch_pencil_solve(s, a));
+  if (t) {
+    CK(cudaEventRecord(pr->ev[pr->ev_used + 1], s));
+    pr->ev_used += 2;
+  }
+  return SP_OK;
+}
+
+// One IMEX step (Sec. "Timesteppers") queued on stream s.
+sp_status one_step(sp_ctx* ctx, Problem* pr, cudaStream_t s, double dt) {
+  sp_status st;
+  if (!pr->xt_valid) {
+    CK(launch_coef_to_solve(s, pr->P, pr->S, pr->Nz, pr->d_Xc, pr->d_Xt, pr->d_col_map, pr->d_var_rec,
+                            pr->d_var_ph));
+    pr->xt_valid = true;
+    pr->mx_valid = false;
+  }
+  if (pr->scheme == SP_RK222 || pr->scheme == SP_RK111) {
+    const Tableau tb = make_tableau(pr->scheme);
+    // F(X^0)
+    if ((st = eval_rhs(ctx, pr, s, pr->d_Fc[0])) != SP_OK) return st;
+    for (int i = 1; i <= tb.s; ++i) {
+      if (i > 1 && (st = eval_rhs(ctx, pr, s, pr->d_Fc[i - 1])) != SP_OK) return st;
+      SolveArgs a = base_args(pr, ctx, 0);
+      // M~ X~^0 (stored, or computed on the first stage of a fresh state)
+      if (i == 1 && !pr->mx_valid) {
+        a.mv_x = pr->d_Xt; a.mv_vals = pr->d_Mv; a.mv_coef = 1.0; a.mv_store = pr->d_MX[0];
+      } else {
+        a.vec[a.nvec] = pr->d_MX[0]; a.vec_coef[a.nvec++] = 1.0;
+      }
+      // - dt sum_{j<i} H_ij L~ X~^j (H_i0 = 0: the first stage is explicit)
+      for (int j = 1; j < i; ++j)
+        if (tb.H[i][j] != 0.0) { a.vec[a.nvec] = pr->d_LX[j]; a.vec_coef[a.nvec++] = -dt * tb.H[i][j]; }
+      // dt sum_{j<i} A_ij F~^j, boundary rows get dt sum_j A_ij g
+      double csum = 0.0;
+      for (int j = 0; j < i; ++j)
+        if (tb.A[i][j] != 0.0) { a.fc[a.nfc] = pr->d_Fc[j]; a.fc_coef[a.nfc++] = dt * tb.A[i][j]; csum += tb.A[i][j]; }
+      a.bc_coef = dt * csum;
+      a.xc_out = pr->d_Xc;
+      if (i < tb.s) {
+        a.ep_mv_vals = pr->d_Lv; a.ep_mv_store = pr->d_LX[i];     // L~ X~^i for later stages
+      } else {
+        a.xt_out = pr->d_Xt;
+        a.ep_mv_vals = pr->d_Mv; a.ep_mv_store = pr->d_MX[0];     // M~ X~^{n+1} for the next step
+      }
+      if ((st = solve(ctx, pr, s, a)) != SP_OK) return st;
+    }
+    pr->mx_valid = true;
+  } else {
+    // SBDF1 / SBDF2 (Wang & Ruuth 2008), constant step, multiplied through by dt:
+    //   SBDF1: (M + dt L) X^n = M X^{n-1} + dt F^{n-1}
+    //   SBDF2: (3/2 M + dt L) X^n = 2 M X^{n-1} - 1/2 M X^{n-2} + dt (2 F^{n-1} - F^{n-2})
+    const int it = pr->iteration;
+    const int cur = it & 1, prv = cur ^ 1;
+    if ((st = eval_rhs(ctx, pr, s, pr->d_Fc[cur])) != SP_OK) return st;
+    const bool first = (pr->scheme == SP_SBDF1) || it == 0;
+    SolveArgs a = base_args(pr, ctx, first ? 0 : 1);
+    if (!pr->mx_valid) {
+      a.mv_x = pr->d_Xt; a.mv_vals = pr->d_Mv; a.mv_store = pr->d_MX[cur];
+      a.mv_coef = first ? 1.0 : 2.0;
+    } else {
+      a.vec[a.nvec] = pr->d_MX[cur]; a.vec_coef[a.nvec++] = first ? 1.0 : 2.0;
+    }
+    if (first) {
+      a.fc[a.nfc] = pr->d_Fc[cur]; a.fc_coef[a.nfc++] = dt;
+    } else {
+      a.vec[a.nvec] = pr->d_MX[prv]; a.vec_coef[a.nvec++] = -0.5;
+      a.fc[a.nfc] = pr->d_Fc[cur]; a.fc_coef[a.nfc++] = 2.0 * dt;
+      a.fc[a.nfc] = pr->d_Fc[prv]; a.fc_coef[a.nfc++] = -dt;
+    }
+    a.bc_coef = dt;
+    a.xt_out = pr->d_Xt;
+    a.xc_out = pr->d_Xc;
+    a.ep_mv_vals = pr->d_Mv; a.ep_mv_store = pr->d_MX[prv];       // M~ X~^n for the next step
+    if ((st = solve(ctx, pr, s, a)) != SP_OK) return st;
+    pr->mx_valid = true;
+    if (pr->scheme == SP_SBDF2) {
+      // after an SBDF1 start the slot parity advances like any other step
+    }
+    pr->iteration = it + 1;
+  }
+  return SP_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// ABI
+// ===========================================================================
+extern "C" {
+
+sp_status sp_create(sp_ctx** out, int device, void* cuda_stream) {
+  if (!out) return SP_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) return SP_ERR_CUDA;
+  if (device < 0 || device >= count) return SP_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return SP_ERR_CUDA;
+  auto* ctx = new sp_ctx();
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&ctx->d_status, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(DevStatus)) != cudaSuccess) {
+    delete ctx;
+    return SP_ERR_CUDA;
+  }
+  *out = ctx;
+  return SP_OK;
+}
+
+sp_status sp_destroy(sp_ctx* ctx) {
+  if (!ctx) return SP_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& p : ctx->probs) free_problem(p.get());
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  delete ctx;
+  return SP_OK;
+}
+
+const char* sp_last_error(const sp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+sp_status sp_add_problem(sp_ctx* ctx, int ndim, const sp_basis* bases, int nvars, int scheme, int precision,
+                         int* problem_id) {
+  if (!ctx) return SP_ERR_ARG;
+  ctx->err.clear();
+  if (ndim != 2) return fail(ctx, SP_ERR_ARG, "only ndim = 2 (Fourier x Chebyshev) is supported");
+  if (!bases || !problem_id) return fail(ctx, SP_ERR_ARG, "null argument");
+  const sp_basis& bx = bases[0];
+  const sp_basis& bz = bases[1];
+  if (bx.kind != SP_FOURIER || bz.kind != SP_CHEBYSHEV)
+    return fail(ctx, SP_ERR_ARG, "bases must be (Fourier, Chebyshev), the Chebyshev axis last");
+  if (nvars < 1 || nvars > 16) return fail(ctx, SP_ERR_ARG, "nvars must be in [1, 16]");
+  if (scheme < SP_RK222 || scheme > SP_RK111) return fail(ctx, SP_ERR_ARG, "unknown scheme %d", scheme);
+  if (precision != SP_PREC_FP64 && precision != SP_PREC_MIXED)
+    return fail(ctx, SP_ERR_ARG, "unknown precision %d", precision);
+  auto pr = std::make_unique<Problem>();
+  pr->S = nvars;
+  pr->scheme = scheme;
+  pr->prec = precision == SP_PREC_MIXED ? 1 : 0;
+  pr->bx = bx;
+  pr->bz = bz;
+  pr->Nx = bx.n_coeff;
+  pr->Nz = bz.n_coeff;
+  if (pr->Nx < 4 || pr->Nx % 2) return fail(ctx, SP_ERR_ARG, "N_x must be even and >= 4");
+  if (pr->Nz < 4) return fail(ctx, SP_ERR_ARG, "N_z must be >= 4");
+  for (const sp_basis* b : {&bx, &bz}) {
+    if (b->dealias_num <= 0 || b->dealias_den <= 0 || (b->n_coeff * b->dealias_num) % b->dealias_den)
+      return fail(ctx, SP_ERR_ARG, "dealias scale must give an integer grid size");
+    if (b->dealias_num < b->dealias_den) return fail(ctx, SP_ERR_ARG, "dealias scale must be >= 1");
+    if (!(b->b > b->a)) return fail(ctx, SP_ERR_ARG, "interval must have b > a");
+  }
+  pr->Ngx = bx.n_coeff * bx.dealias_num / bx.dealias_den;
+  pr->Ngz = bz.n_coeff * bz.dealias_num / bz.dealias_den;
+  if (!is_smooth_length(pr->Ngx) || pr->Ngx < 16 || pr->Ngx > 4096)
+    return fail(ctx, SP_ERR_ARG, "N_gx = %d must be 2^k or 3*2^k in [16, 4096]", pr->Ngx);
+  if (!is_smooth_length(pr->Ngz) || pr->Ngz < 8 || pr->Ngz > 1536)
+    return fail(ctx, SP_ERR_ARG, "N_gz = %d must be 2^k or 3*2^k in [8, 1536]", pr->Ngz);
+  pr->P = pr->Nx / 2;
+  pr->Lx = bx.b - bx.a;
+  pr->za = bz.a;
+  pr->zb = bz.b;
+  pr->n = pr->S * pr->Nz;
+  pr->pset.assign(pr->P, 0);
+  ctx->probs.push_back(std::move(pr));
+  *problem_id = (int)ctx->probs.size() - 1;
+  return SP_OK;
+}
+
+sp_status sp_set_layout(sp_ctx* ctx, int problem, const int32_t* col_map, const int32_t* row_map,
+                        const int32_t* var_recombine, const int32_t* var_phase, const int32_t* eq_differential,
+                        const int32_t* eq_phase, int nbc, const int32_t* bc_rows, const double* bc_values) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (pr->uploaded) return fail(ctx, SP_ERR_STATE, "layout is fixed once the problem is on the device");
+  if (!col_map || !row_map || !var_recombine || !var_phase || !eq_differential || !eq_phase ||
+      (nbc > 0 && (!bc_rows || !bc_values)))
+    return fail(ctx, SP_ERR_ARG, "null argument");
+  const int S = pr->S, Nz = pr->Nz, n = pr->n;
+  if (nbc < 0 || nbc > n) return fail(ctx, SP_ERR_ARG, "bad nbc");
+  std::vector<int> seen_c(n, 0), seen_r(n, 0);
+  for (int i = 0; i < S * Nz; ++i) {
+    if (col_map[i] < 0 || col_map[i] >= n || seen_c[col_map[i]]++)
+      return fail(ctx, SP_ERR_ARG, "col_map is not a permutation of [0, n)");
+    if (row_map[i] >= n || row_map[i] < -1) return fail(ctx, SP_ERR_ARG, "row_map entry out of range");
+    if (row_map[i] >= 0 && seen_r[row_map[i]]++) return fail(ctx, SP_ERR_ARG, "row_map repeats a row");
+  }
+  for (int q = 0; q < nbc; ++q) {
+    if (bc_rows[q] < 0 || bc_rows[q] >= n || seen_r[bc_rows[q]]++)
+      return fail(ctx, SP_ERR_ARG, "bc_rows overlap the equation rows or repeat");
+  }
+  for (int r = 0; r < n; ++r)
+    if (!seen_r[r]) return fail(ctx, SP_ERR_ARG, "row %d receives neither an equation nor a boundary row", r);
+  for (int e = 0; e < S; ++e)
+    if (eq_differential[e]) {
+      // the last row of a differential equation is its tau row
+      if (row_map[e * Nz + Nz - 1] != -1)
+        return fail(ctx, SP_ERR_ARG, "differential equation %d keeps its last (tau) row", e);
+    }
+  pr->col_map.assign(col_map, col_map + S * Nz);
+  pr->row_map.assign(row_map, row_map + S * Nz);
+  pr->var_rec.assign(var_recombine, var_recombine + S);
+  pr->var_ph.assign(var_phase, var_phase + S);
+  pr->eq_diff.assign(eq_differential, eq_differential + S);
+  pr->eq_ph.assign(eq_phase, eq_phase + S);
+  pr->nbc = nbc;
+  pr->bc_rows.assign(bc_rows, bc_rows + nbc);
+  pr->bc_values.assign(bc_values, bc_values + (size_t)2 * nbc * pr->P);
+  pr->has_layout = true;
+  return SP_OK;
+}
+
+sp_status sp_set_pencils(sp_ctx* ctx, int problem, int64_t first_pencil, int64_t count, int n, int64_t nnz,
+                         const int32_t* indptr, const int32_t* indices, const double* M_values,
+                         const double* L_values) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (pr->uploaded) return fail(ctx, SP_ERR_STATE, "pencils are fixed once the problem is on the device");
+  if (n != pr->n) return fail(ctx, SP_ERR_ARG, "n = %d but S * N_z = %d", n, pr->n);
+  if (first_pencil < 0 || count < 1 || first_pencil + count > pr->P)
+    return fail(ctx, SP_ERR_ARG, "pencil range out of [0, P)");
+  if (!indptr || !indices || !M_values || !L_values) return fail(ctx, SP_ERR_ARG, "null argument");
+  if (nnz < 1 || indptr[0] != 0 || indptr[n] != nnz) return fail(ctx, SP_ERR_ARG, "indptr inconsistent with nnz");
+  int kl = 0, ku = 0;
+  for (int r = 0; r < n; ++r) {
+    if (indptr[r + 1] < indptr[r]) return fail(ctx, SP_ERR_ARG, "indptr not monotone");
+    for (int e = indptr[r]; e < indptr[r + 1]; ++e) {
+      const int c = indices[e];
+      if (c < 0 || c >= n) return fail(ctx, SP_ERR_ARG, "column index out of range");
+      if (e > indptr[r] && c <= indices[e - 1]) return fail(ctx, SP_ERR_ARG, "row %d indices not sorted/unique", r);
+      kl = std::max(kl, r - c);
+      ku = std::max(ku, c - r);
+    }
+  }
+  if (kl > 31) return fail(ctx, SP_ERR_ARG, "lower band width %d > 31 is not supported", kl);
+  if (kl + ku > 63) return fail(ctx, SP_ERR_ARG, "kl + ku = %d > 63 is not supported", kl + ku);
+  if (pr->nnz < 0) {
+    pr->nnz = nnz;
+    pr->indptr.assign(indptr, indptr + n + 1);
+    pr->indices.assign(indices, indices + nnz);
+    pr->Mv.assign((size_t)pr->P * nnz, 0.0);
+    pr->Lv.assign((size_t)pr->P * nnz, 0.0);
+    pr->kl = kl;
+    pr->ku = ku;
+  } else {
+    if (nnz != pr->nnz || std::memcmp(indptr, pr->indptr.data(), (n + 1) * sizeof(int32_t)) ||
+        std::memcmp(indices, pr->indices.data(), nnz * sizeof(int32_t)))
+      return fail(ctx, SP_ERR_ARG, "all pencils must share one CSR pattern");
+  }
+  std::memcpy(pr->Mv.data() + first_pencil * nnz, M_values, (size_t)count * nnz * sizeof(double));
+  std::memcpy(pr->Lv.data() + first_pencil * nnz, L_values, (size_t)count * nnz * sizeof(double));
+  for (int64_t p = first_pencil; p < first_pencil + count; ++p) pr->pset[p] = 1;
+  return SP_OK;
+}
+
+sp_status sp_set_bilinear_rhs(sp_ctx* ctx, int problem, int nterms, const int32_t* eq, const double* coef,
+                              const int32_t* op_a, const int32_t* var_a, const int32_t* op_b,
+                              const int32_t* var_b) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (pr->uploaded) return fail(ctx, SP_ERR_STATE, "the right-hand side is fixed once the problem is on the device");
+  if (nterms < 0 || (nterms > 0 && (!eq || !coef || !op_a || !var_a || !op_b || !var_b)))
+    return fail(ctx, SP_ERR_ARG, "null argument");
+  pr->t_slot.clear(); pr->t_fa.clear(); pr->t_fb.clear(); pr->t_coef.clear();
+  pr->gfields.clear(); pr->nl_eqs.clear();
+  auto field = [&](int op, int var) {
+    for (size_t i = 0; i < pr->gfields.size(); ++i)
+      if (pr->gfields[i].op == op && pr->gfields[i].var == var) return (int)i;
+    pr->gfields.push_back(GridField{var, op});
+    return (int)pr->gfields.size() - 1;
+  };
+  for (int t = 0; t < nterms; ++t) {
+    if (eq[t] < 0 || eq[t] >= pr->S || var_a[t] < 0 || var_a[t] >= pr->S || var_b[t] < 0 || var_b[t] >= pr->S)
+      return fail(ctx, SP_ERR_ARG, "term %d: index out of range", t);
+    if ((op_a[t] != SP_OP_ID && op_a[t] != SP_OP_DX) || (op_b[t] != SP_OP_ID && op_b[t] != SP_OP_DX))
+      return fail(ctx, SP_ERR_ARG, "term %d: unknown operator", t);
+    int slot = -1;
+    for (size_t i = 0; i < pr->nl_eqs.size(); ++i)
+      if (pr->nl_eqs[i] == eq[t]) slot = (int)i;
+    if (slot < 0) { pr->nl_eqs.push_back(eq[t]); slot = (int)pr->nl_eqs.size() - 1; }
+    pr->t_slot.push_back(slot);
+    pr->t_coef.push_back(coef[t]);
+    pr->t_fa.push_back(field(op_a[t], var_a[t]));
+    pr->t_fb.push_back(field(op_b[t], var_b[t]));
+  }
+  if (pr->gfields.size() > 16) return fail(ctx, SP_ERR_ARG, "at most 16 distinct grid fields");
+  return SP_OK;
+}
+
+sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, SP_ERR_ARG, "dt must be positive and finite");
+  CK(cudaSetDevice(ctx->device));
+  sp_status st = upload_problem(ctx, pr);
+  if (st != SP_OK) return st;
+  double ab[2][2];
+  int nf = 1;
+  if (pr->scheme == SP_RK222 || pr->scheme == SP_RK111) {
+    const Tableau tb = make_tableau(pr->scheme);
+    ab[0][0] = 1.0; ab[0][1] = dt * tb.H[1][1];
+  } else if (pr->scheme == SP_SBDF1) {
+    ab[0][0] = 1.0; ab[0][1] = dt;
+  } else {
+    ab[0][0] = 1.0; ab[0][1] = dt;
+    ab[1][0] = 1.5; ab[1][1] = dt;
+    nf = 2;
+  }
+  const int ldab = 2 * pr->kl + pr->ku + 1;
+  double* work = nullptr;
+  CK(dalloc(&work, (size_t)pr->P * pr->n * ldab));
+  for (int f = 0; f < nf; ++f) {
+    pr->fac[f].alpha = ab[f][0];
+    pr->fac[f].beta = ab[f][1];
+    cudaError_t e = launch_band_factor(ctx->stream, pr->P, pr->n, (int)pr->nnz, pr->kl, pr->ku, pr->d_indptr,
+                                       pr->d_indices, pr->d_Mv, pr->d_Lv, ab[f][0], ab[f][1], work, pr->fac[f],
+                                       pr->npad, pr->lpad, pr->upad, ctx->d_status);
+    if (e != cudaSuccess) { cudaFree(work); CK(e); }
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(work);
+  CK(e);
+  pr->nfac = nf;
+  pr->fac_dt = dt;
+  pr->factored = true;
+  for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
+  pr->graphs.clear();
+  return SP_OK;
+}
+
+sp_status sp_set_field(sp_ctx* ctx, int problem, int var, const void* data, int on_device, char layout) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (var < 0 || var >= pr->S || !data) return fail(ctx, SP_ERR_ARG, "bad variable or null data");
+  CK(cudaSetDevice(ctx->device));
+  sp_status st = upload_problem(ctx, pr);
+  if (st != SP_OK) return st;
+  cudaStream_t s = ctx->stream;
+  double2* dst = pr->d_Xc + (size_t)var * pr->P * pr->Nz;
+  const size_t ncoef = (size_t)pr->P * pr->Nz;
+  if (layout == 'c') {
+    CK(cudaMemcpyAsync(dst, data, ncoef * sizeof(double2),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  } else if (layout == 'g') {
+    TransformPlan *px, *pz;
+    if ((st = make_plan(ctx, pr, pr->Nx, pr->Nx, &px)) != SP_OK) return st;
+    if ((st = make_plan(ctx, pr, pr->Nz, pr->Nz, &pz)) != SP_OK) return st;
+    const size_t ng = (size_t)pr->Nz * pr->Nx;
+    double* grid = nullptr;
+    void* h = nullptr;
+    CK(dalloc(&grid, ng));
+    // set-up transforms run in FP64 in every precision mode: an initial
+    // state carries small perturbations on an O(1) background
+    CK(cudaMalloc(&h, (size_t)pr->Nz * pr->P * 16));
+    CK(cudaMemcpyAsync(grid, data, ng * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    CK(launch_fourier_rows(s, 0, *px, pr->Nz, pr->P, 4, 1, nullptr, grid, nullptr, 0, nullptr, nullptr,
+                           nullptr, nullptr, 0, h));
+    CK(launch_cheb_forward(s, 0, *pz, pr->P, 1, h, dst));
+    CK(cudaStreamSynchronize(s));
+    cudaFree(grid);
+    cudaFree(h);
+  } else {
+    return fail(ctx, SP_ERR_ARG, "layout must be 'c' or 'g'");
+  }
+  CK(cudaGetLastError());
+  pr->xt_valid = false;
+  pr->mx_valid = false;
+  pr->iteration = 0;
+  return SP_OK;
+}
+
+sp_status sp_get_field(sp_ctx* ctx, int problem, int var, void* data, int on_device, char layout) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (var < 0 || var >= pr->S || !data) return fail(ctx, SP_ERR_ARG, "bad variable or null data");
+  if (!pr->uploaded) return fail(ctx, SP_ERR_STATE, "no state on the device yet");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const double2* src = pr->d_Xc + (size_t)var * pr->P * pr->Nz;
+  const size_t ncoef = (size_t)pr->P * pr->Nz;
+  if (layout == 'c') {
+    CK(cudaMemcpyAsync(data, src, ncoef * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } else if (layout == 'g') {
+    TransformPlan *px, *pz;
+    sp_status st;
+    if ((st = make_plan(ctx, pr, pr->Nx, pr->Nx, &px)) != SP_OK) return st;
+    if ((st = make_plan(ctx, pr, pr->Nz, pr->Nz, &pz)) != SP_OK) return st;
+    const size_t ng = (size_t)pr->Nz * pr->Nx;
+    double* grid = nullptr;
+    void* gz = nullptr;
+    CK(dalloc(&grid, ng));
+    CK(cudaMalloc(&gz, (size_t)pr->Nz * pr->P * 16));
+    CK(launch_cheb_backward(s, 0, *pz, pr->P, 1, pr->d_ident + var, pr->d_zero, pr->d_kx, pr->d_Xc,
+                            pr->P * pr->Nz, gz));
+    CK(launch_fourier_rows(s, 0, *px, pr->Nz, pr->P, 1, 1, gz, nullptr, grid, 0, nullptr, nullptr,
+                           nullptr, nullptr, 0, nullptr));
+    CK(cudaMemcpyAsync(data, grid, ng * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    cudaFree(grid);
+    cudaFree(gz);
+  } else {
+    return fail(ctx, SP_ERR_ARG, "layout must be 'c' or 'g'");
+  }
+  return SP_OK;
+}
+
+sp_status sp_dz(sp_ctx* ctx, int problem, int src_var, int dst_var) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (src_var < 0 || src_var >= pr->S || dst_var < 0 || dst_var >= pr->S || src_var == dst_var)
+    return fail(ctx, SP_ERR_ARG, "bad variables");
+  if (!pr->uploaded) return fail(ctx, SP_ERR_STATE, "no state on the device yet");
+  CK(cudaSetDevice(ctx->device));
+  const size_t f = (size_t)pr->P * pr->Nz;
+  CK(launch_dz(ctx->stream, pr->P, pr->Nz, 2.0 / (pr->zb - pr->za), pr->d_Xc + src_var * f, pr->d_Xc + dst_var * f));
+  pr->xt_valid = false;
+  pr->mx_valid = false;
+  pr->iteration = 0;
+  return SP_OK;
+}
+
+sp_status sp_step(sp_ctx* ctx, int problem, double dt, int nsteps) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (nsteps < 0) return fail(ctx, SP_ERR_ARG, "nsteps < 0");
+  if (!pr->factored || dt != pr->fac_dt)
+    return fail(ctx, SP_ERR_NOT_FACTORED, "dt = %.17g is not the factored step size", dt);
+  CK(cudaSetDevice(ctx->device));
+  for (int k = 0; k < nsteps; ++k) {
+    sp_status st = one_step(ctx, pr, ctx->stream, dt);
+    if (st != SP_OK) return st;
+  }
+  return SP_OK;
+}
+
+sp_status sp_step_graph(sp_ctx* ctx, int problem, double dt, int nsteps) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (nsteps < 0) return fail(ctx, SP_ERR_ARG, "nsteps < 0");
+  if (!pr->factored || dt != pr->fac_dt)
+    return fail(ctx, SP_ERR_NOT_FACTORED, "dt = %.17g is not the factored step size", dt);
+  CK(cudaSetDevice(ctx->device));
+  int left = nsteps;
+  // warm-up steps that change the buffer schedule run eagerly
+  while (left > 0 && (!pr->xt_valid || !pr->mx_valid ||
+                      (pr->scheme == SP_SBDF2 && pr->iteration == 0))) {
+    sp_status st = one_step(ctx, pr, ctx->stream, dt);
+    if (st != SP_OK) return st;
+    --left;
+  }
+  const bool timing = pr->timing;
+  pr->timing = false;  // event nodes are not recorded inside graphs
+  while (left > 0) {
+    const int block = std::min(left, 16);
+    const int parity = (pr->scheme == SP_SBDF2 || pr->scheme == SP_SBDF1) ? (pr->iteration & 1) : 0;
+    auto key = std::make_tuple(block, parity, pr->scheme, dt);
+    cudaGraphExec_t exec = nullptr;
+    auto it = pr->graphs.find(key);
+    const int it0 = pr->iteration;
+    if (it == pr->graphs.end()) {
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+      sp_status st = SP_OK;
+      for (int k = 0; k < block && st == SP_OK; ++k) st = one_step(ctx, pr, ctx->capture, dt);
+      cudaError_t e = cudaStreamEndCapture(ctx->capture, &g);
+      if (st != SP_OK) { pr->timing = timing; return st; }
+      CK(e);
+      CK(cudaGraphInstantiate(&exec, g, 0));
+      cudaGraphDestroy(g);
+      pr->graphs[key] = exec;
+    } else {
+      exec = it->second;
+      pr->iteration = it0 + block;
+    }
+    CK(cudaGraphLaunch(exec, ctx->stream));
+    left -= block;
+  }
+  pr->timing = timing;
+  return SP_OK;
+}
+
+sp_status sp_sync_status(sp_ctx* ctx, int64_t* pencil) {
+  if (!ctx) return SP_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  DevStatus h{};
+  CK(cudaMemcpy(&h, ctx->d_status, sizeof h, cudaMemcpyDeviceToHost));
+  CK(cudaMemset(ctx->d_status, 0, sizeof h));
+  if (pencil) *pencil = h.code ? h.pencil : -1;
+  if (h.code) {
+    ctx->err = "device status " + std::to_string(h.code) + " at pencil " + std::to_string(h.pencil);
+    return (sp_status)h.code;
+  }
+  return SP_OK;
+}
+
+sp_status sp_transform(sp_ctx* ctx, int problem, const void* in, void* out, int nfields, int direction,
+                       int scale_num, int scale_den, int on_device) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (!in || !out || nfields < 1 || nfields > 16 || (direction != 1 && direction != -1))
+    return fail(ctx, SP_ERR_ARG, "bad arguments");
+  if (scale_num <= 0 || scale_den <= 0 || scale_num < scale_den ||
+      (pr->Nx * scale_num) % scale_den || (pr->Nz * scale_num) % scale_den)
+    return fail(ctx, SP_ERR_ARG, "scale must be >= 1 and give integer grid sizes");
+  CK(cudaSetDevice(ctx->device));
+  sp_status st = upload_problem(ctx, pr);
+  if (st != SP_OK) return st;
+  const int Ngx = pr->Nx * scale_num / scale_den, Ngz = pr->Nz * scale_num / scale_den;
+  TransformPlan *px, *pz;
+  if ((st = make_plan(ctx, pr, pr->Nx, Ngx, &px)) != SP_OK) return st;
+  if ((st = make_plan(ctx, pr, pr->Nz, Ngz, &pz)) != SP_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const size_t ncoef = (size_t)nfields * pr->P * pr->Nz, ngrid = (size_t)nfields * Ngz * Ngx;
+  const size_t esz = pr->prec ? 8 : 16;
+  double2* coef = nullptr;
+  double* grid = nullptr;
+  void* mid = nullptr;
+  CK(dalloc(&coef, ncoef));
+  CK(dalloc(&grid, ngrid));
+  CK(cudaMalloc(&mid, (size_t)nfields * Ngz * pr->P * esz));
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e;
+  if (direction < 0) {
+    e = cudaMemcpyAsync(coef, in, ncoef * sizeof(double2), kin, s);
+    if (e == cudaSuccess)
+      e = launch_cheb_backward(s, pr->prec, *pz, pr->P, nfields, pr->d_ident, pr->d_zero, pr->d_kx, coef,
+                               pr->P * pr->Nz, mid);
+    if (e == cudaSuccess)
+      e = launch_fourier_rows(s, pr->prec, *px, Ngz, pr->P, 1, nfields, mid, nullptr, grid, 0, nullptr, nullptr,
+                              nullptr, nullptr, 0, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, grid, ngrid * sizeof(double), kout, s);
+  } else {
+    e = cudaMemcpyAsync(grid, in, ngrid * sizeof(double), kin, s);
+    if (e == cudaSuccess)
+      e = launch_fourier_rows(s, pr->prec, *px, Ngz, pr->P, 4, nfields, nullptr, grid, nullptr, 0, nullptr,
+                              nullptr, nullptr, nullptr, 0, mid);
+    if (e == cudaSuccess) e = launch_cheb_forward(s, pr->prec, *pz, pr->P, nfields, mid, coef);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, coef, ncoef * sizeof(double2), kout, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(coef);
+  cudaFree(grid);
+  cudaFree(mid);
+  CK(e);
+  return SP_OK;
+}
+
+sp_status sp_eval_rhs(sp_ctx* ctx, int problem, void* out_host, int* n_eq) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (!pr->uploaded) return fail(ctx, SP_ERR_STATE, "no state on the device yet");
+  CK(cudaSetDevice(ctx->device));
+  sp_status st = eval_rhs(ctx, pr, ctx->stream, pr->d_Fc[2]);
+  if (st != SP_OK) return st;
+  const size_t cnt = pr->nl_eqs.size() * (size_t)pr->P * pr->Nz;
+  if (out_host && cnt) CK(cudaMemcpyAsync(out_host, pr->d_Fc[2], cnt * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (n_eq) *n_eq = (int)pr->nl_eqs.size();
+  return SP_OK;
+}
+
+sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  if (pr->nnz < 0) return fail(ctx, SP_ERR_STATE, "sp_set_pencils has not been called");
+  if (n) *n = pr->n;
+  if (kl) *kl = pr->kl;
+  if (ku) *ku = pr->ku;
+  return SP_OK;
+}
+
+sp_status sp_set_timing(sp_ctx* ctx, int problem, int max_launches) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->device));
+  while ((int)pr->ev.size() < 2 * max_launches) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    pr->ev.push_back(e);
+  }
+  pr->ev_used = 0;
+  pr->timing = max_launches > 0;
+  return SP_OK;
+}
+
+sp_status sp_last_solve_time(sp_ctx* ctx, int problem, double* ms_per_launch, int* launches) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double tot = 0;
+  const int cnt = (int)(pr->ev_used / 2);
+  for (int i = 0; i < cnt; ++i) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, pr->ev[2 * i], pr->ev[2 * i + 1]));
+    tot += ms;
+  }
+  if (ms_per_launch) *ms_per_launch = cnt ? tot / cnt : 0.0;
+  if (launches) *launches = cnt;
+  return SP_OK;
+}
+
+}  // extern "C"

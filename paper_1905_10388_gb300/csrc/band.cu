@@ -1,0 +1,556 @@
+// Banded pencil factorization and solve (FP64), sm_103a.
+//
+// Sec. "Matrix solvers": factor each pencil matrix once per step size and
+// reuse it; Sec. "Multistep / Runge-Kutta IMEX integrators": B~ is a fixed
+// linear combination of stored M~X~, L~X~ and F~ vectors.  The pencil
+// matrices are banded after interleaving and Dirichlet recombination
+// (Sec. "A general sparse tau method"), so the LU uses banded partial
+// pivoting in the LAPACK gbtrf layout: L keeps kl multipliers per column and
+// the row interchanges are applied interleaved with them; U holds
+// kuu = kl + ku superdiagonals.
+//
+// GB300 FP64 runs at ~1 TFLOP/s with a 64-cycle dependent-FMA latency, so
+// the substitution is a sequential chain per pencil.  One warp owns one
+// pencil: its 32 lanes hold a rotating window of the right-hand side
+// (lane = index mod 32 [mod 64 with two registers per lane]), one lane per
+// band entry, the real and imaginary parts of the complex right-hand side
+// sharing one real factor.  Each step broadcasts the settled entry with one
+// shuffle and updates the window with one FMA per lane.  The factor is
+// streamed through a shared-memory ring by bulk asynchronous copies (TMA,
+// cp.async.bulk) issued by one lane and tracked with mbarriers; every wait
+// is bounded and reports SP_ERR_TIMEOUT instead of hanging.
+#include <cstdio>
+
+#include "internal.h"
+
+namespace spectau {
+
+// ---------------------------------------------------------------------------
+// factorization: one warp per pencil, working in a global band array
+// AB[p][j][t], t = i - j + kuu, holding a*M~ + b*L~
+// ---------------------------------------------------------------------------
+__global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32_t* __restrict__ indptr,
+                              const int32_t* __restrict__ indices, const double* __restrict__ Mv,
+                              const double* __restrict__ Lv, double alpha, double beta,
+                              double* __restrict__ work, double* __restrict__ Lf, uint8_t* __restrict__ piv,
+                              double* __restrict__ Uf, int npad, int lpad, int upad, DevStatus* st) {
+  const int warps = blockDim.x / 32;
+  const int p = blockIdx.x * warps + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (p >= P) return;
+  const int kuu = kl + ku;
+  const int ldab = kl + kuu + 1;
+  double* AB = work + (size_t)p * n * ldab;
+  for (size_t e = lane; e < (size_t)n * ldab; e += 32) AB[e] = 0.0;
+  __syncwarp();
+  const double* M = Mv + (size_t)p * nnz;
+  const double* L = Lv + (size_t)p * nnz;
+  for (int r = lane; r < n; r += 32) {
+    for (int e = indptr[r]; e < indptr[r + 1]; ++e) {
+      const int c = indices[e];
+      AB[(size_t)c * ldab + (r - c + kuu)] = alpha * M[e] + beta * L[e];
+    }
+  }
+  __syncwarp();
+  uint8_t* pv = piv + (size_t)p * npad;
+  bool singular = false;
+  for (int j = 0; j < n; ++j) {
+    const int m = min(kl, n - 1 - j);
+    double* colj = AB + (size_t)j * ldab;
+    // pivot search: first maximum of |a| over rows j .. j+m
+    double a = (lane <= m) ? fabs(colj[kuu + lane]) : -1.0;
+    int ia = lane;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double b = __shfl_xor_sync(0xffffffffu, a, o);
+      const int ib = __shfl_xor_sync(0xffffffffu, ia, o);
+      if (b > a || (b == a && ib < ia)) { a = b; ia = ib; }
+    }
+    const int t = ia;
+    if (lane == 0) pv[j] = (uint8_t)t;
+    if (!(a > 0.0)) { singular = true; break; }
+    // interchange rows j and j+t over columns j .. j+kuu
+    if (t != 0) {
+      for (int c = j + lane; c <= min(n - 1, j + kuu); c += 32) {
+        double* col = AB + (size_t)c * ldab;
+        const int r0 = j - c + kuu, r1 = j + t - c + kuu;
+        const double x0 = col[r0];
+        col[r0] = col[r1];
+        col[r1] = x0;
+      }
+    }
+    __syncwarp();
+    const double pivot = colj[kuu];
+    double lt = 0.0;
+    if (lane >= 1 && lane <= m) {
+      lt = colj[kuu + lane] / pivot;
+      colj[kuu + lane] = lt;
+    }
+    __syncwarp();
+    // rank-1 update of rows j+1..j+m, columns j+1..j+kuu
+    for (int c = j + 1 + lane; c <= min(n - 1, j + kuu); c += 32) {
+      double* col = AB + (size_t)c * ldab;
+      const double u = col[j - c + kuu];
+      for (int tt = 1; tt <= m; ++tt) {
+        const double l = colj[kuu + tt];
+        col[j + tt - c + kuu] = fma(-l, u, col[j + tt - c + kuu]);
+      }
+    }
+    __syncwarp();
+  }
+  if (singular) {
+    if (lane == 0) raise_status(st, SP_ERR_SINGULAR, p);
+    return;
+  }
+  // write the solve layout: L multipliers, scaled U columns
+  double* Lp = Lf + (size_t)p * npad * lpad;
+  double* Up = Uf + (size_t)p * npad * upad;
+  for (int j = lane; j < npad; j += 32) {
+    if (j >= n) {
+      for (int t = 0; t < lpad; ++t) Lp[(size_t)j * lpad + t] = 0.0;
+      for (int t = 0; t < upad; ++t) Up[(size_t)j * upad + t] = 0.0;
+      pv[j] = 0;
+      continue;
+    }
+    const double* col = AB + (size_t)j * ldab;
+    for (int t = 0; t < lpad; ++t)
+      Lp[(size_t)j * lpad + t] = (t < kl && j + 1 + t < n) ? col[kuu + 1 + t] : 0.0;
+    const double rd = 1.0 / col[kuu];
+    Up[(size_t)j * upad] = rd;
+    for (int t = 1; t < upad; ++t)
+      Up[(size_t)j * upad + t] = (t <= kuu && j - t >= 0) ? col[kuu - t] * rd : 0.0;
+  }
+}
+
+cudaError_t launch_band_factor(cudaStream_t s, int P, int n, int nnz, int kl, int ku,
+                               const int32_t* indptr, const int32_t* indices, const double* Mv,
+                               const double* Lv, double alpha, double beta, double* work,
+                               const BandFactor& f, int npad, int lpad, int upad, DevStatus* st) {
+  const int wpb = 4;
+  k_band_factor<<<(P + wpb - 1) / wpb, 32 * wpb, 0, s>>>(P, n, nnz, kl, ku, indptr, indices, Mv, Lv,
+                                                        alpha, beta, work, f.L, f.piv, f.U, npad,
+                                                        lpad, upad, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copy + mbarrier helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// A bulk copy that has not landed after ~1 s of SM clock (2^31 cycles at
+// ~2 GHz) is declared lost.
+constexpr long long WAIT_CYCLES = 1ll << 31;
+
+__device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t phase) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, phase))
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  return true;
+}
+
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+  double2 r;
+  r.x = __shfl_sync(0xffffffffu, v.x, src);
+  r.y = __shfl_sync(0xffffffffu, v.y, src);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// pencil solve: prologue (B~ assembly) -> L pass -> U pass -> epilogue
+// ---------------------------------------------------------------------------
+struct SolveSmem {
+  double2* B;
+  double* Lring;
+  double* Uring;
+  uint8_t* Pring;
+  uint64_t* barL;
+  uint64_t* barU;
+  int* abort_flag;
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// B holds npad + 64 entries: the padded columns plus the forward pass's
+// one-window-ahead prefetch, zero beyond n.
+__host__ __device__ inline size_t solve_smem_bytes(int npad, int lpad, int upad) {
+  size_t off = align_up((size_t)(npad + 64) * 16, 128);
+  off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK * lpad * 8, 128);
+  off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK * upad * 8, 128);
+  off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK, 128);
+  off += align_up((size_t)2 * SOLVE_RING * 8, 128);
+  off += 128;
+  return off;
+}
+
+template <int RU>
+__global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int p = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int n = a.n;
+  SolveSmem sm;
+  {
+    size_t off = 0;
+    sm.B = reinterpret_cast<double2*>(smem_raw + off);
+    off += align_up((size_t)(a.npad + 64) * 16, 128);
+    sm.Lring = reinterpret_cast<double*>(smem_raw + off);
+    off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK * a.lpad * 8, 128);
+    sm.Uring = reinterpret_cast<double*>(smem_raw + off);
+    off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK * a.upad * 8, 128);
+    sm.Pring = reinterpret_cast<uint8_t*>(smem_raw + off);
+    off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK, 128);
+    sm.barL = reinterpret_cast<uint64_t*>(smem_raw + off);
+    sm.barU = sm.barL + SOLVE_RING;
+    off += align_up((size_t)2 * SOLVE_RING * 8, 128);
+    sm.abort_flag = reinterpret_cast<int*>(smem_raw + off);
+  }
+  const int nchunks = a.npad / SOLVE_CHUNK;
+  const double* Lsrc = a.Lf + (size_t)p * a.npad * a.lpad;
+  const double* Usrc = a.Uf + (size_t)p * a.npad * a.upad;
+  const uint8_t* Psrc = a.piv + (size_t)p * a.npad;
+  const uint32_t lbytes = SOLVE_CHUNK * a.lpad * 8, ubytes = SOLVE_CHUNK * a.upad * 8;
+
+  auto issue_L = [&](int c) {  // chunk c (forward order) into slot c % RING
+    const int s = c % SOLVE_RING;
+    mbar_expect_tx(&sm.barL[s], lbytes + SOLVE_CHUNK);
+    bulk_g2s(sm.Lring + (size_t)s * SOLVE_CHUNK * a.lpad, Lsrc + (size_t)c * SOLVE_CHUNK * a.lpad, lbytes,
+             &sm.barL[s]);
+    bulk_g2s(sm.Pring + (size_t)s * SOLVE_CHUNK, Psrc + (size_t)c * SOLVE_CHUNK, SOLVE_CHUNK, &sm.barL[s]);
+  };
+  auto issue_U = [&](int k) {  // k-th chunk of the backward order (chunk nchunks-1-k)
+    const int s = k % SOLVE_RING;
+    const int c = nchunks - 1 - k;
+    mbar_expect_tx(&sm.barU[s], ubytes);
+    bulk_g2s(sm.Uring + (size_t)s * SOLVE_CHUNK * a.upad, Usrc + (size_t)c * SOLVE_CHUNK * a.upad, ubytes,
+             &sm.barU[s]);
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < SOLVE_RING; ++s) {
+      mbar_init(&sm.barL[s], 1);
+      mbar_init(&sm.barU[s], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *sm.abort_flag = 0;
+    // the factor does not depend on the prologue: start streaming now
+    for (int c = 0; c < min(SOLVE_RING, nchunks); ++c) issue_L(c);
+    for (int k = 0; k < min(SOLVE_RING, nchunks); ++k) issue_U(k);
+  }
+
+  // ---- prologue: B~ = linear combination of stored vectors, one matvec,
+  //      left-preconditioned F~ (T-to-U conversion, tau rows dropped) and
+  //      boundary values
+  const size_t prow = (size_t)p * n;
+  for (int r = tid; r < n; r += nt) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < a.nvec; ++k) {
+      const double2 v = a.vec[k][prow + r];
+      acc.x = fma(a.vec_coef[k], v.x, acc.x);
+      acc.y = fma(a.vec_coef[k], v.y, acc.y);
+    }
+    if (a.mv_x != nullptr) {
+      double2 s = make_double2(0.0, 0.0);
+      const double* vals = a.mv_vals + (size_t)p * a.nnz;
+      for (int e = a.indptr[r]; e < a.indptr[r + 1]; ++e) {
+        const double m = vals[e];
+        const double2 x = a.mv_x[prow + a.indices[e]];
+        s.x = fma(m, x.x, s.x);
+        s.y = fma(m, x.y, s.y);
+      }
+      if (a.mv_store != nullptr) a.mv_store[prow + r] = s;
+      acc.x = fma(a.mv_coef, s.x, acc.x);
+      acc.y = fma(a.mv_coef, s.y, acc.y);
+    }
+    sm.B[r] = acc;
+  }
+  for (int r = n + tid; r < a.npad + 64; r += nt) sm.B[r] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const int Nz = a.Nz;
+  for (int idx = tid; idx < a.n_nl * Nz; idx += nt) {
+    const int sl = idx / Nz, m = idx - sl * Nz;
+    const int e = a.nl_eq[sl];
+    const int row = a.row_map[e * Nz + m];
+    if (row < 0) continue;
+    double2 f0 = make_double2(0.0, 0.0), f2 = make_double2(0.0, 0.0);
+    for (int k = 0; k < a.nfc; ++k) {
+      const double2* F = a.fc[k] + ((size_t)sl * a.P + p) * Nz;
+      const double2 v0 = F[m];
+      f0.x = fma(a.fc_coef[k], v0.x, f0.x);
+      f0.y = fma(a.fc_coef[k], v0.y, f0.y);
+      if (m + 2 < Nz) {
+        const double2 v2 = F[m + 2];
+        f2.x = fma(a.fc_coef[k], v2.x, f2.x);
+        f2.y = fma(a.fc_coef[k], v2.y, f2.y);
+      }
+    }
+    double2 u;
+    if (a.eq_differential[e]) {
+      const double c0 = (m == 0) ? 1.0 : 0.5;
+      u.x = fma(c0, f0.x, -0.5 * f2.x);
+      u.y = fma(c0, f0.y, -0.5 * f2.y);
+    } else {
+      u = f0;
+    }
+    u = cipow<double>(u, -a.eq_phase[e]);
+    double2 b = sm.B[row];
+    b.x += u.x;
+    b.y += u.y;
+    sm.B[row] = b;
+  }
+  for (int q = tid; q < a.nbc; q += nt) {
+    const int row = a.bc_rows[q];
+    const double2 g = a.bc_values[(size_t)p * a.nbc + q];
+    double2 b = sm.B[row];
+    b.x = fma(a.bc_coef, g.x, b.x);
+    b.y = fma(a.bc_coef, g.y, b.y);
+    sm.B[row] = b;
+  }
+  __syncthreads();
+
+  // ---- substitution (warp 0), over the padded columns [0, npad): padding
+  //      columns carry zero factors, so they pass zeros through.
+  //      Chunks are SOLVE_CHUNK = 32 columns, aligned with the 32-lane window,
+  //      so within a chunk step jj the owner lane is jj and the offset of lane
+  //      l from the pivot row is (l - jj) mod 32 (forward) or (jj - l) mod 32
+  //      (backward).  The per-step dependency chain is one shuffle + one FMA;
+  //      everything else (coefficients, pivots, the next window element) is
+  //      loaded ahead of use and merged with predicated selects.
+  if (tid < 32) {
+    const int lane = tid;
+    bool ok = true;
+    int doneL = 0, doneU = 0;  // chunks consumed (issued = min(nchunks, done + RING))
+    double2* B = sm.B;
+    // forward: row interchanges and unit-lower multipliers
+    double2 v = B[lane];          // window element b[j + ((lane - j) & 31)]
+    double2 nv = B[lane + 32];    // the element this lane takes next
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int s = c % SOLVE_RING;
+      if (!bounded_wait(&sm.barL[s], (c / SOLVE_RING) & 1)) { ok = false; break; }
+      doneL = c + 1;
+      const double* Lc = sm.Lring + (size_t)s * SOLVE_CHUNK * a.lpad;
+      const uint32_t* Pw = reinterpret_cast<const uint32_t*>(sm.Pring + (size_t)s * SOLVE_CHUNK);
+      const int j0 = c * SOLVE_CHUNK;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int off = (Pw[jj >> 2] >> (8 * (jj & 3))) & 0xff;
+        const int pl = (jj + off) & 31;
+        const int d = (lane - jj) & 31;
+        const double l = (d >= 1 && d <= a.kl) ? Lc[jj * a.lpad + d - 1] : 0.0;
+        const double2 bj = shfl2(v, pl);   // pivot row value = y_j
+        const double2 vo = shfl2(v, jj);   // old b_j moves to the pivot row
+        v = (lane == pl) ? vo : v;
+        v.x = fma(-l, bj.x, v.x);
+        v.y = fma(-l, bj.y, v.y);
+        if (lane == jj) {
+          B[j0 + jj] = bj;
+          v = nv;
+          nv = B[j0 + jj + 64];
+        }
+      }
+      __syncwarp();
+      if (lane == 0 && c + SOLVE_RING < nchunks) {
+        fence_proxy_async();
+        issue_L(c + SOLVE_RING);
+      }
+    }
+    __syncwarp();
+    // backward: scaled U columns, window of 32*RU entries
+    constexpr int W = 32 * RU;
+    const int npad = a.npad;
+    double2 w[RU], nw[RU];
+#pragma unroll
+    for (int r = 0; r < RU; ++r) {
+      // index congruent to lane + 32 r (mod W) in [npad - W, npad - 1]
+      const int i = npad - W + lane + 32 * r;
+      w[r] = (ok && i >= 0) ? B[i] : make_double2(0.0, 0.0);
+      nw[r] = (ok && i - W >= 0) ? B[i - W] : make_double2(0.0, 0.0);
+    }
+    for (int k = 0; k < nchunks && ok; ++k) {
+      const int s = k % SOLVE_RING;
+      if (!bounded_wait(&sm.barU[s], (k / SOLVE_RING) & 1)) { ok = false; break; }
+      doneU = k + 1;
+      const double* Uc = sm.Uring + (size_t)s * SOLVE_CHUNK * a.upad;
+      const int j0 = (nchunks - 1 - k) * SOLVE_CHUNK;
+#pragma unroll
+      for (int jj = 31; jj >= 0; --jj) {
+        const int j = j0 + jj;
+        const double* Ucol = Uc + jj * a.upad;
+        const int oreg = (RU == 1) ? 0 : ((j & (W - 1)) >> 5);
+        double2 src = w[0];
+#pragma unroll
+        for (int r = 1; r < RU; ++r) src = (oreg == r) ? w[r] : src;
+        const double2 bj = shfl2(src, jj);
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          const int t = (j - lane - 32 * r) & (W - 1);
+          const double u = (t >= 1) ? Ucol[t] : 0.0;   // U_{j-t,j}/U_jj, zero beyond kuu
+          w[r].x = fma(-u, bj.x, w[r].x);
+          w[r].y = fma(-u, bj.y, w[r].y);
+        }
+        if (lane == jj) {
+          const double rd = Ucol[0];
+          B[j] = make_double2(bj.x * rd, bj.y * rd);
+          const double2 nxt = (j - 2 * W >= 0) ? B[j - 2 * W] : make_double2(0.0, 0.0);
+#pragma unroll
+          for (int r = 0; r < RU; ++r) {
+            if (oreg == r) {
+              w[r] = nw[r];
+              nw[r] = nxt;
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0 && k + SOLVE_RING < nchunks) {
+        fence_proxy_async();
+        issue_U(k + SOLVE_RING);
+      }
+    }
+    if (!ok) {
+      // report, then let every copy in flight land before the CTA exits
+      if (lane == 0) {
+        raise_status(a.status, SP_ERR_TIMEOUT, p);
+        *sm.abort_flag = 1;
+        const int issL = min(nchunks, doneL + SOLVE_RING), issU = min(nchunks, doneU + SOLVE_RING);
+        for (int q = doneL; q < issL; ++q)
+          bounded_wait(&sm.barL[q % SOLVE_RING], (q / SOLVE_RING) & 1);
+        for (int q = doneU; q < issU; ++q)
+          bounded_wait(&sm.barU[q % SOLVE_RING], (q / SOLVE_RING) & 1);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (*sm.abort_flag) return;
+
+  // ---- epilogue: store X~, recombine to T coefficients, optional M~ X~
+  bool finite = true;
+  for (int r = tid; r < n; r += nt) {
+    const double2 x = sm.B[r];
+    finite = finite && isfinite(x.x) && isfinite(x.y);
+    if (a.xt_out) a.xt_out[prow + r] = x;
+  }
+  if (a.xc_out) {
+    for (int idx = tid; idx < a.S * Nz; idx += nt) {
+      const int v = idx / Nz, m = idx - v * Nz;
+      double2 x = sm.B[a.col_map[idx]];
+      if (a.var_recombine[v] && m + 2 < Nz) {
+        const double2 x2 = sm.B[a.col_map[idx + 2]];
+        x.x -= x2.x;
+        x.y -= x2.y;
+      }
+      a.xc_out[((size_t)v * a.P + p) * Nz + m] = cipow<double>(x, a.var_phase[v]);
+    }
+  }
+  if (a.ep_mv_vals) {
+    const double* vals = a.ep_mv_vals + (size_t)p * a.nnz;
+    for (int r = tid; r < n; r += nt) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int e = a.indptr[r]; e < a.indptr[r + 1]; ++e) {
+        const double m = vals[e];
+        const double2 x = sm.B[a.indices[e]];
+        s.x = fma(m, x.x, s.x);
+        s.y = fma(m, x.y, s.y);
+      }
+      a.ep_mv_store[prow + r] = s;
+    }
+  }
+  if (!finite) raise_status(a.status, SP_ERR_NONFINITE, p);
+}
+
+cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a) {
+  const size_t smem = solve_smem_bytes(a.npad, a.lpad, a.upad);
+  if (a.kuu <= 31) {
+    cudaFuncSetAttribute(k_pencil_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_pencil_solve<1><<<a.P, 128, smem, s>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_pencil_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_pencil_solve<2><<<a.P, 128, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// state conversion and Chebyshev derivative (set-up kernels)
+// ---------------------------------------------------------------------------
+// x~ = i^{-q_v} (P^R)^{-1} x : recombined variables invert x_m = x~_m - x~_{m+2}
+__global__ void k_coef_to_solve(int P, int S, int Nz, const double2* __restrict__ xc, double2* __restrict__ xt,
+                                const int32_t* __restrict__ col_map, const int32_t* __restrict__ rec,
+                                const int32_t* __restrict__ ph) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P * S) return;
+  const int v = idx / P, p = idx - v * P;
+  const double2* x = xc + ((size_t)v * P + p) * Nz;
+  double2* out = xt + (size_t)p * S * Nz;
+  double2 t1 = make_double2(0.0, 0.0), t2 = make_double2(0.0, 0.0);  // x~_{m+1}, x~_{m+2}
+  for (int m = Nz - 1; m >= 0; --m) {
+    double2 y = cipow<double>(x[m], -ph[v]);
+    if (rec[v]) { y.x += t2.x; y.y += t2.y; }
+    out[col_map[v * Nz + m]] = y;
+    t2 = t1;
+    t1 = y;
+  }
+}
+
+cudaError_t launch_coef_to_solve(cudaStream_t s, int P, int S, int Nz, const double2* xc, double2* xt,
+                                 const int32_t* col_map, const int32_t* var_recombine,
+                                 const int32_t* var_phase) {
+  const int total = P * S;
+  k_coef_to_solve<<<(total + 127) / 128, 128, 0, s>>>(P, S, Nz, xc, xt, col_map, var_recombine, var_phase);
+  return cudaGetLastError();
+}
+
+// c'_{m} = c'_{m+2} + 2 (m+1) c_{m+1}, c'_0 halved, times 2/(b-a)
+__global__ void k_dz(int P, int Nz, double scale, const double2* __restrict__ src, double2* __restrict__ dst) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const double2* c = src + (size_t)p * Nz;
+  double2* d = dst + (size_t)p * Nz;
+  double2 d1 = make_double2(0.0, 0.0), d2 = make_double2(0.0, 0.0);  // d_{m+1}, d_{m+2}
+  for (int m = Nz - 1; m >= 0; --m) {
+    double2 dm = d2;
+    if (m + 1 < Nz) {
+      dm.x += 2.0 * (m + 1) * c[m + 1].x;
+      dm.y += 2.0 * (m + 1) * c[m + 1].y;
+    }
+    const double h = (m == 0) ? 0.5 : 1.0;
+    d[m] = make_double2(dm.x * h * scale, dm.y * h * scale);
+    d2 = d1;
+    d1 = dm;
+  }
+}
+
+cudaError_t launch_dz(cudaStream_t s, int P, int Nz, double scale, const double2* src, double2* dst) {
+  k_dz<<<(P + 127) / 128, 128, 0, s>>>(P, Nz, scale, src, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace spectau

@@ -1,0 +1,55 @@
+// Device helpers shared by the spectau kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/spectau.h"
+
+namespace spectau {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on float2 / double2
+// ---------------------------------------------------------------------------
+template <typename T> struct cplx;
+template <> struct cplx<float> { using t = float2; };
+template <> struct cplx<double> { using t = double2; };
+template <typename T> using C = typename cplx<T>::t;
+
+template <typename T> __host__ __device__ __forceinline__ C<T> mk(T re, T im) {
+  C<T> z; z.x = re; z.y = im; return z;
+}
+template <typename T> __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T> __device__ __forceinline__ C<T> cmulc(C<T> a, C<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T> __device__ __forceinline__ C<T> cconj(C<T> a) { return mk<T>(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// multiply by i^q, q taken mod 4
+template <typename T> __device__ __forceinline__ C<T> cipow(C<T> a, int q) {
+  switch (q & 3) {
+    case 0: return a;
+    case 1: return mk<T>(-a.y, a.x);
+    case 2: return mk<T>(-a.x, -a.y);
+    default: return mk<T>(a.y, -a.x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// device status word: first error wins; bad pencil recorded alongside
+// ---------------------------------------------------------------------------
+struct DevStatus {
+  int code;            // 0 or a negative sp_status
+  int pad;
+  long long pencil;    // first failing pencil (or -1)
+};
+
+__device__ __forceinline__ void raise_status(DevStatus* st, int code, long long pencil) {
+  if (atomicCAS(&st->code, 0, code) == 0) st->pencil = pencil;
+}
+
+}  // namespace spectau

@@ -1,0 +1,89 @@
+// Internal declarations shared by the spectau translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace spectau {
+
+// Column chunk streamed per bulk copy by the pencil-solve kernel, and the
+// ring depth.  Factor arrays are padded to a multiple of SOLVE_CHUNK columns.
+constexpr int SOLVE_CHUNK = 32;
+constexpr int SOLVE_RING = 4;
+
+// Banded LU factors of one matrix a*M~ + b*L~ for all pencils.
+struct BandFactor {
+  double alpha = 0, beta = 0;   // A = alpha M~ + beta L~
+  double* L = nullptr;          // [P][npad][lpad]  multipliers of column j (rows j+1..j+kl)
+  uint8_t* piv = nullptr;       // [P][npad]        pivot row offset (piv - j) in [0, kl]
+  double* U = nullptr;          // [P][npad][upad]  t=0: 1/U_jj, t>=1: U_{j-t,j}/U_jj
+};
+
+// Arguments of the pencil right-hand-side assembly + solve + epilogue kernel.
+struct SolveArgs {
+  int P, n, Nz, S, nbc, nnz;
+  int kl, kuu, npad, lpad, upad;
+  const double* Lf; const uint8_t* piv; const double* Uf;
+  // prologue: B = sum_k vec_coef[k] vec[k] + mv_coef (Mat x) + sum_k fc_coef[k] P^L Fc_k + bc_coef g
+  int nvec; const double2* vec[3]; double vec_coef[3];
+  const double2* mv_x; const double* mv_vals; double mv_coef; double2* mv_store;
+  int nfc; const double2* fc[3]; double fc_coef[3];
+  double bc_coef;
+  // epilogue
+  double2* xt_out; double2* xc_out;
+  const double* ep_mv_vals; double2* ep_mv_store;
+  // tables (device)
+  const int32_t* indptr; const int32_t* indices;
+  const int32_t* row_map; const int32_t* col_map;
+  const int32_t* var_recombine; const int32_t* var_phase;
+  const int32_t* eq_differential; const int32_t* eq_phase;
+  const int32_t* nl_eq; int n_nl;        // equation index of each nonlinear slot
+  const int32_t* bc_rows; const double2* bc_values;
+  DevStatus* status;
+};
+
+// Transform arguments.
+struct GridField { int var; int op; };
+
+struct TransformPlan {
+  int Nc, Ng;                   // coefficients and grid points along one axis
+  int radix3;
+  void* tw64 = nullptr;         // double2[Ng]  exp(-2 pi i t / Ng)
+  void* tw32 = nullptr;         // float2[Ng]
+  void* dct64 = nullptr;        // double2[Ng]  exp(-i pi k / (2 Ng))
+  void* dct32 = nullptr;
+};
+
+// --- launchers (band.cu) ---------------------------------------------------
+cudaError_t launch_band_factor(cudaStream_t s, int P, int n, int nnz, int kl, int ku,
+                               const int32_t* indptr, const int32_t* indices,
+                               const double* Mv, const double* Lv, double alpha, double beta,
+                               double* work, const BandFactor& f, int npad, int lpad, int upad,
+                               DevStatus* st);
+cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a);
+cudaError_t launch_coef_to_solve(cudaStream_t s, int P, int S, int Nz, const double2* xc,
+                                 double2* xt, const int32_t* col_map, const int32_t* var_recombine,
+                                 const int32_t* var_phase);
+cudaError_t launch_dz(cudaStream_t s, int P, int Nz, double scale, const double2* src, double2* dst);
+
+// --- launchers (transforms.cu) ---------------------------------------------
+// precision: 0 = double, 1 = float.  Buffers of the grid stages are typed by
+// the precision; coefficient-space inputs/outputs are always double2.
+cudaError_t launch_cheb_backward(cudaStream_t s, int prec, const TransformPlan& pz, int P,
+                                 int nf, const int32_t* f_var, const int32_t* f_op,
+                                 const double* kx, const double2* xc, int xc_field_stride,
+                                 void* gz);
+cudaError_t launch_fourier_rows(cudaStream_t s, int prec, const TransformPlan& px, int rows,
+                                int P, int mode, int nf, const void* gz, double* grid_in,
+                                double* grid_out, int nterms, const int32_t* t_eq,
+                                const double* t_coef, const int32_t* t_fa, const int32_t* t_fb,
+                                int ne, void* h);
+cudaError_t launch_cheb_forward(cudaStream_t s, int prec, const TransformPlan& pz, int P, int ne,
+                                const void* h, double2* fc);
+
+}  // namespace spectau

@@ -1,0 +1,220 @@
+"""Thin Python front end over the C ABI: a pencil problem on one GPU.
+
+``TauSolver`` hands an assembled :class:`~.tau.PencilProblem` to the library
+(``sp_add_problem``, ``sp_set_layout``, ``sp_set_pencils``,
+``sp_set_bilinear_rhs``) and exposes factor / step / state access.  Every
+step of the method runs in the CUDA kernels behind the ABI; this module only
+marshals arguments.  ``RBSolver`` builds the Rayleigh-Benard workload.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+from . import rb as rbmod
+
+
+class Context:
+    """A library context on one CUDA device and stream."""
+
+    def __init__(self, device=0, stream=None):
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = 0
+        self._h = ctypes.c_void_p()
+        st = L.lib().sp_create(ctypes.byref(self._h), int(device), ctypes.c_void_p(stream))
+        if st != L.SP_OK:
+            raise L.SpectauError(st, "sp_create failed (is a CUDA device visible?)")
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            L.lib().sp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync_status(self):
+        pen = ctypes.c_int64(-1)
+        st = L.lib().sp_sync_status(self._h, ctypes.byref(pen))
+        return st, pen.value
+
+
+class TauSolver:
+    """One Fourier(x) x Chebyshev(z) first-order problem in the library."""
+
+    def __init__(self, ctx, problem, n_x, n_z, L_x, kx_scale=None, scheme="RK222",
+                 precision="fp64", dealias=(3, 2), z_interval=(0.0, 1.0), bilinear=()):
+        self.ctx = ctx
+        self.problem = problem
+        self.Nx, self.Nz, self.Lx = int(n_x), int(n_z), float(L_x)
+        self.P = self.Nx // 2
+        self.S = problem.S
+        self.var = {v: i for i, v in enumerate(problem.variables)}
+        self.state_order = tuple(problem.variables)   # order of get_state / set_state
+        self.eq = {e.name: i for i, e in enumerate(problem.equations)}
+        lib, h = L.lib(), ctx.handle
+        bases = (L.sp_basis * 2)()
+        bases[0] = L.sp_basis(L.SP_FOURIER, self.Nx, 0.0, self.Lx, dealias[0], dealias[1])
+        bases[1] = L.sp_basis(L.SP_CHEBYSHEV, self.Nz, z_interval[0], z_interval[1], dealias[0], dealias[1])
+        pid = ctypes.c_int()
+        prec = L.SP_PREC_MIXED if precision == "mixed" else L.SP_PREC_FP64
+        L.check(h, lib.sp_add_problem(h, 2, bases, self.S, L.SCHEMES[scheme], prec, ctypes.byref(pid)))
+        self.pid = pid.value
+        self.scheme, self.precision = scheme, precision
+        kx = 2 * np.pi * np.arange(self.P) / self.Lx
+        asm = problem.build(self.Nz, kx)
+        self.assembly = asm
+        c = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+        bcv = np.ascontiguousarray(np.stack([asm["bc_values"].real, asm["bc_values"].imag], -1), dtype=np.float64)
+        L.check(h, lib.sp_set_layout(h, self.pid, L.i32(c(asm["col_map"])), L.i32(c(asm["row_map"])),
+                                     L.i32(c(asm["var_recombine"])), L.i32(c(asm["var_phase"])),
+                                     L.i32(c(asm["eq_differential"])), L.i32(c(asm["eq_phase"])),
+                                     len(asm["bc_rows"]), L.i32(c(asm["bc_rows"])), L.f64(bcv)))
+        Mv = np.ascontiguousarray(asm["M"], dtype=np.float64)
+        Lv = np.ascontiguousarray(asm["L"], dtype=np.float64)
+        L.check(h, lib.sp_set_pencils(h, self.pid, 0, self.P, asm["n"], len(asm["indices"]),
+                                      L.i32(c(asm["indptr"])), L.i32(c(asm["indices"])), L.f64(Mv), L.f64(Lv)))
+        self.set_bilinear(bilinear)
+        self.dt = None
+
+    def set_bilinear(self, terms):
+        ops = {"ID": L.SP_OP_ID, "DX": L.SP_OP_DX}
+        eq = np.array([self.eq[t[0]] for t in terms], np.int32)
+        coef = np.array([t[1] for t in terms], np.float64)
+        oa = np.array([ops[t[2]] for t in terms], np.int32)
+        va = np.array([self.var[t[3]] for t in terms], np.int32)
+        ob = np.array([ops[t[4]] for t in terms], np.int32)
+        vb = np.array([self.var[t[5]] for t in terms], np.int32)
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_set_bilinear_rhs(h, self.pid, len(terms), L.i32(eq), L.f64(coef), L.i32(oa),
+                                               L.i32(va), L.i32(ob), L.i32(vb)))
+        self.nl_eqs = []
+        for t in terms:
+            if t[0] not in self.nl_eqs:
+                self.nl_eqs.append(t[0])
+
+    # -- numerics ------------------------------------------------------------
+    def factor(self, dt):
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_factor(h, self.pid, float(dt)))
+        self.dt = float(dt)
+
+    def step(self, nsteps=1, dt=None, graph=False):
+        dt = self.dt if dt is None else float(dt)
+        h = self.ctx.handle
+        f = L.lib().sp_step_graph if graph else L.lib().sp_step
+        L.check(h, f(h, self.pid, dt, int(nsteps)))
+
+    def sync(self):
+        st, pen = self.ctx.sync_status()
+        if st != L.SP_OK:
+            raise L.SpectauError(st, f"device status at pencil {pen}")
+
+    def band(self):
+        n, kl, ku = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_get_band(h, self.pid, ctypes.byref(n), ctypes.byref(kl), ctypes.byref(ku)))
+        return n.value, kl.value, ku.value
+
+    # -- state -----------------------------------------------------------------
+    def set_field(self, name, data, layout="c"):
+        h = self.ctx.handle
+        if hasattr(data, "data_ptr"):        # a torch CUDA tensor
+            L.check(h, L.lib().sp_set_field(h, self.pid, self.var[name], ctypes.c_void_p(data.data_ptr()), 1,
+                                            layout.encode()))
+            return
+        arr = np.ascontiguousarray(data, dtype=np.complex128 if layout == "c" else np.float64)
+        L.check(h, L.lib().sp_set_field(h, self.pid, self.var[name], arr.ctypes.data_as(ctypes.c_void_p), 0,
+                                        layout.encode()))
+
+    def get_field(self, name, layout="c"):
+        h = self.ctx.handle
+        if layout == "c":
+            out = np.zeros((self.P, self.Nz), np.complex128)
+        else:
+            out = np.zeros((self.Nz, self.Nx), np.float64)
+        L.check(h, L.lib().sp_get_field(h, self.pid, self.var[name], out.ctypes.data_as(ctypes.c_void_p), 0,
+                                        layout.encode()))
+        return out
+
+    def get_state(self):
+        """State coefficients [var][p][m] in ``state_order``."""
+        return np.stack([self.get_field(v) for v in self.state_order])
+
+    def set_state(self, X):
+        """Set every variable from X[var] (``state_order``)."""
+        for i, v in enumerate(self.state_order):
+            self.set_field(v, X[i])
+
+    def dz(self, src, dst):
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_dz(h, self.pid, self.var[src], self.var[dst]))
+
+    def transform(self, data, direction, scale=(1, 1)):
+        """direction -1: coefficients [f][p][m] -> grid [f][iz][ix]; +1: back."""
+        h = self.ctx.handle
+        if direction < 0:
+            inp = np.ascontiguousarray(data, np.complex128)
+            nf = inp.shape[0]
+            ngx, ngz = self.Nx * scale[0] // scale[1], self.Nz * scale[0] // scale[1]
+            out = np.zeros((nf, ngz, ngx), np.float64)
+        else:
+            inp = np.ascontiguousarray(data, np.float64)
+            nf = inp.shape[0]
+            out = np.zeros((nf, self.P, self.Nz), np.complex128)
+        L.check(h, L.lib().sp_transform(h, self.pid, inp.ctypes.data_as(ctypes.c_void_p),
+                                        out.ctypes.data_as(ctypes.c_void_p), nf, int(direction),
+                                        scale[0], scale[1], 0))
+        return out
+
+    def eval_rhs(self):
+        out = np.zeros((max(1, len(self.nl_eqs)), self.P, self.Nz), np.complex128)
+        ne = ctypes.c_int()
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_eval_rhs(h, self.pid, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ne)))
+        return {e: out[i] for i, e in enumerate(self.nl_eqs)}
+
+    def set_timing(self, max_launches):
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_set_timing(h, self.pid, int(max_launches)))
+
+    def solve_time(self):
+        ms, cnt = ctypes.c_double(), ctypes.c_int()
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_last_solve_time(h, self.pid, ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value
+
+
+class RBSolver(TauSolver):
+    """2D Rayleigh-Benard convection (b, p, u, w, bz, uz, wz) in the library."""
+
+    def __init__(self, ctx, n_x, n_z, Ra, Pr=1.0, L_x=4.0, scheme="RK222", precision="fp64",
+                 dealias=(3, 2)):
+        problem = rbmod.rb_pencil_problem(Ra, Pr)
+        super().__init__(ctx, problem, n_x, n_z, L_x, scheme=scheme, precision=precision,
+                         dealias=dealias, bilinear=rbmod.BILINEAR_TERMS)
+        self.state_order = rbmod.VARIABLES
+        self.Ra, self.Pr = Ra, Pr
+
+    def set_initial_state(self, noise, amplitude=1e-3):
+        """b = 1 - z + A xi z (1 - z) on the scale-1 grid (transformed on the
+        device), bz = dz b (device recurrence), all other fields zero."""
+        z = rbmod.chebyshev_nodes(self.Nz)[:, None]
+        b_grid = 1.0 - z + amplitude * noise * z * (1.0 - z)
+        zero = np.zeros((self.P, self.Nz), np.complex128)
+        for v in self.problem.variables:
+            self.set_field(v, zero)
+        self.set_field("b", b_grid, layout="g")
+        self.dz("b", "bz")

@@ -197,3 +197,12 @@ def test_derivative_on_problem_interval():
     c = bases.chebyshev_forward(z ** 4 - 2 * z, N)
     d = bases.chebyshev_derivative(c, 0.0, 1.0)
     assert np.abs(bases.chebyshev_backward(d, N) - (4 * z ** 3 - 2)).max() < 1e-12
+
+
+@pytest.mark.parametrize("Nc,Ng", [(16, 24), (32, 48), (12, 12)])
+def test_dct_variant_equals_quadrature(Nc, Ng):
+    # the floor-estimate variant computes the same definition (scipy DCT)
+    c = RNG.standard_normal((3, Nc)) + 1j * RNG.standard_normal((3, Nc))
+    g = bases.chebyshev_backward(c, Ng)
+    assert np.abs(bases.chebyshev_backward_dct(c, Ng) - g).max() < 1e-12   # O(N eps) sums
+    assert np.abs(bases.chebyshev_forward_dct(g, Nc) - bases.chebyshev_forward(g, Nc)).max() < 1e-12
