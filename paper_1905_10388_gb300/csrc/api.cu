@@ -85,6 +85,10 @@ struct Problem {
   bool uploaded = false;
   int32_t *d_indptr = nullptr, *d_indices = nullptr;
   double *d_Mv = nullptr, *d_Lv = nullptr;
+  // M~ on its own compact pattern (entries nonzero in at least one pencil)
+  int64_t nnzM = 0;
+  int32_t *d_indptrM = nullptr, *d_indicesM = nullptr;
+  double* d_MvC = nullptr;
   int32_t *d_col_map = nullptr, *d_row_map = nullptr, *d_var_rec = nullptr, *d_var_ph = nullptr;
   int32_t *d_eq_diff = nullptr, *d_eq_ph = nullptr, *d_bc_rows = nullptr, *d_nl_eq = nullptr;
   double2* d_bc_values = nullptr;
@@ -212,6 +216,26 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
   CK(upload(&pr->d_indices, pr->indices, s));
   CK(upload(&pr->d_Mv, pr->Mv, s));
   CK(upload(&pr->d_Lv, pr->Lv, s));
+  {
+    std::vector<char> keep(pr->nnz, 0);
+    for (int p = 0; p < pr->P; ++p)
+      for (int64_t e = 0; e < pr->nnz; ++e)
+        if (pr->Mv[(size_t)p * pr->nnz + e] != 0.0) keep[e] = 1;
+    std::vector<int32_t> ip(pr->n + 1, 0), ix;
+    std::vector<int64_t> src;
+    for (int r = 0; r < pr->n; ++r) {
+      for (int e = pr->indptr[r]; e < pr->indptr[r + 1]; ++e)
+        if (keep[e]) { ix.push_back(pr->indices[e]); src.push_back(e); }
+      ip[r + 1] = (int32_t)ix.size();
+    }
+    pr->nnzM = (int64_t)ix.size();
+    std::vector<double> mv((size_t)pr->P * std::max<int64_t>(pr->nnzM, 1), 0.0);
+    for (int p = 0; p < pr->P; ++p)
+      for (int64_t k = 0; k < pr->nnzM; ++k) mv[(size_t)p * pr->nnzM + k] = pr->Mv[(size_t)p * pr->nnz + src[k]];
+    CK(upload(&pr->d_indptrM, ip, s));
+    CK(upload(&pr->d_indicesM, ix, s));
+    CK(upload(&pr->d_MvC, mv, s));
+  }
   CK(upload(&pr->d_col_map, pr->col_map, s));
   CK(upload(&pr->d_row_map, pr->row_map, s));
   CK(upload(&pr->d_var_rec, pr->var_rec, s));
@@ -263,6 +287,7 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
     CK(dalloc(&f.L, (size_t)pr->P * pr->npad * pr->lpad));
     CK(dalloc(&f.piv, (size_t)pr->P * pr->npad));
     CK(dalloc(&f.U, (size_t)pr->P * pr->npad * pr->upad));
+    CK(dalloc(&f.rd, (size_t)pr->P * pr->npad));
   }
   CK(cudaStreamSynchronize(s));
   pr->uploaded = true;
@@ -271,7 +296,7 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
 
 void free_problem(Problem* pr) {
   auto F = [](void* p) { if (p) cudaFree(p); };
-  F(pr->d_indptr); F(pr->d_indices); F(pr->d_Mv); F(pr->d_Lv); F(pr->d_col_map); F(pr->d_row_map);
+  F(pr->d_indptr); F(pr->d_indices); F(pr->d_Mv); F(pr->d_Lv); F(pr->d_indptrM); F(pr->d_indicesM); F(pr->d_MvC); F(pr->d_col_map); F(pr->d_row_map);
   F(pr->d_var_rec); F(pr->d_var_ph); F(pr->d_eq_diff); F(pr->d_eq_ph); F(pr->d_bc_rows); F(pr->d_nl_eq);
   F(pr->d_bc_values); F(pr->d_kx); F(pr->d_gvar); F(pr->d_gop); F(pr->d_tslot); F(pr->d_tfa); F(pr->d_tfb);
   F(pr->d_tcoef); F(pr->d_ident); F(pr->d_zero); F(pr->d_Xt); F(pr->d_Xc);
@@ -279,7 +304,7 @@ void free_problem(Problem* pr) {
   for (auto b : pr->d_LX) F(b);
   for (auto b : pr->d_Fc) F(b);
   F(pr->d_gz); F(pr->d_h);
-  for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); }
+  for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); F(f.rd); }
   for (auto& kv : pr->plans) { F(kv.second.tw64); F(kv.second.tw32); F(kv.second.dct64); F(kv.second.dct32); }
   for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
   for (auto e : pr->ev) cudaEventDestroy(e);
@@ -306,7 +331,7 @@ SolveArgs base_args(Problem* pr, sp_ctx* ctx, int fac) {
   SolveArgs a{};
   a.P = pr->P; a.n = pr->n; a.Nz = pr->Nz; a.S = pr->S; a.nbc = pr->nbc; a.nnz = (int)pr->nnz;
   a.kl = pr->kl; a.kuu = pr->kl + pr->ku; a.npad = pr->npad; a.lpad = pr->lpad; a.upad = pr->upad;
-  a.Lf = pr->fac[fac].L; a.piv = pr->fac[fac].piv; a.Uf = pr->fac[fac].U;
+  a.Lf = pr->fac[fac].L; a.piv = pr->fac[fac].piv; a.Uf = pr->fac[fac].U; a.rd = pr->fac[fac].rd;
   a.indptr = pr->d_indptr; a.indices = pr->d_indices;
   a.row_map = pr->d_row_map; a.col_map = pr->d_col_map;
   a.var_recombine = pr->d_var_rec; a.var_phase = pr->d_var_ph;
@@ -315,6 +340,16 @@ SolveArgs base_args(Problem* pr, sp_ctx* ctx, int fac) {
   a.bc_rows = pr->d_bc_rows; a.bc_values = pr->d_bc_values;
   a.status = ctx->d_status;
   return a;
+}
+
+void set_mv_M(Problem* pr, SolveArgs& a) {
+  a.mv_vals = pr->d_MvC; a.mv_indptr = pr->d_indptrM; a.mv_indices = pr->d_indicesM; a.mv_nnz = (int)pr->nnzM;
+}
+void set_ep_M(Problem* pr, SolveArgs& a) {
+  a.ep_mv_vals = pr->d_MvC; a.ep_indptr = pr->d_indptrM; a.ep_indices = pr->d_indicesM; a.ep_nnz = (int)pr->nnzM;
+}
+void set_ep_L(Problem* pr, SolveArgs& a) {
+  a.ep_mv_vals = pr->d_Lv; a.ep_indptr = pr->d_indptr; a.ep_indices = pr->d_indices; a.ep_nnz = (int)pr->nnz;
 }
 
 sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
@@ -346,7 +381,8 @@ sp_status one_step(sp_ctx* ctx, Problem* pr, cudaStream_t s, double dt) {
       SolveArgs a = base_args(pr, ctx, 0);
       // M~ X~^0 (stored, or computed on the first stage of a fresh state)
       if (i == 1 && !pr->mx_valid) {
-        a.mv_x = pr->d_Xt; a.mv_vals = pr->d_Mv; a.mv_coef = 1.0; a.mv_store = pr->d_MX[0];
+        a.mv_x = pr->d_Xt; a.mv_coef = 1.0; a.mv_store = pr->d_MX[0];
+        set_mv_M(pr, a);
       } else {
         a.vec[a.nvec] = pr->d_MX[0]; a.vec_coef[a.nvec++] = 1.0;
       }
@@ -360,10 +396,10 @@ sp_status one_step(sp_ctx* ctx, Problem* pr, cudaStream_t s, double dt) {
       a.bc_coef = dt * csum;
       a.xc_out = pr->d_Xc;
       if (i < tb.s) {
-        a.ep_mv_vals = pr->d_Lv; a.ep_mv_store = pr->d_LX[i];     // L~ X~^i for later stages
+        set_ep_L(pr, a); a.ep_mv_store = pr->d_LX[i];             // L~ X~^i for later stages
       } else {
         a.xt_out = pr->d_Xt;
-        a.ep_mv_vals = pr->d_Mv; a.ep_mv_store = pr->d_MX[0];     // M~ X~^{n+1} for the next step
+        set_ep_M(pr, a); a.ep_mv_store = pr->d_MX[0];             // M~ X~^{n+1} for the next step
       }
       if ((st = solve(ctx, pr, s, a)) != SP_OK) return st;
     }
@@ -378,7 +414,8 @@ sp_status one_step(sp_ctx* ctx, Problem* pr, cudaStream_t s, double dt) {
     const bool first = (pr->scheme == SP_SBDF1) || it == 0;
     SolveArgs a = base_args(pr, ctx, first ? 0 : 1);
     if (!pr->mx_valid) {
-      a.mv_x = pr->d_Xt; a.mv_vals = pr->d_Mv; a.mv_store = pr->d_MX[cur];
+      a.mv_x = pr->d_Xt; a.mv_store = pr->d_MX[cur];
+      set_mv_M(pr, a);
       a.mv_coef = first ? 1.0 : 2.0;
     } else {
       a.vec[a.nvec] = pr->d_MX[cur]; a.vec_coef[a.nvec++] = first ? 1.0 : 2.0;
@@ -393,7 +430,7 @@ sp_status one_step(sp_ctx* ctx, Problem* pr, cudaStream_t s, double dt) {
     a.bc_coef = dt;
     a.xt_out = pr->d_Xt;
     a.xc_out = pr->d_Xc;
-    a.ep_mv_vals = pr->d_Mv; a.ep_mv_store = pr->d_MX[prv];       // M~ X~^n for the next step
+    set_ep_M(pr, a); a.ep_mv_store = pr->d_MX[prv];               // M~ X~^n for the next step
     if ((st = solve(ctx, pr, s, a)) != SP_OK) return st;
     pr->mx_valid = true;
     if (pr->scheme == SP_SBDF2) {

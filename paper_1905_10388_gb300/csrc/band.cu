@@ -33,7 +33,8 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
                               const int32_t* __restrict__ indices, const double* __restrict__ Mv,
                               const double* __restrict__ Lv, double alpha, double beta,
                               double* __restrict__ work, double* __restrict__ Lf, uint8_t* __restrict__ piv,
-                              double* __restrict__ Uf, int npad, int lpad, int upad, DevStatus* st) {
+                              double* __restrict__ Uf, double* __restrict__ Rd, int npad, int lpad, int upad,
+                              DevStatus* st) {
   const int warps = blockDim.x / 32;
   const int p = blockIdx.x * warps + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
@@ -104,11 +105,13 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
   // write the solve layout: L multipliers, scaled U columns
   double* Lp = Lf + (size_t)p * npad * lpad;
   double* Up = Uf + (size_t)p * npad * upad;
+  double* Rp = Rd + (size_t)p * npad;
   for (int j = lane; j < npad; j += 32) {
     if (j >= n) {
       for (int t = 0; t < lpad; ++t) Lp[(size_t)j * lpad + t] = 0.0;
       for (int t = 0; t < upad; ++t) Up[(size_t)j * upad + t] = 0.0;
       pv[j] = 0;
+      Rp[j] = 0.0;
       continue;
     }
     const double* col = AB + (size_t)j * ldab;
@@ -116,6 +119,7 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
       Lp[(size_t)j * lpad + t] = (t < kl && j + 1 + t < n) ? col[kuu + 1 + t] : 0.0;
     const double rd = 1.0 / col[kuu];
     Up[(size_t)j * upad] = rd;
+    Rp[j] = rd;
     for (int t = 1; t < upad; ++t)
       Up[(size_t)j * upad + t] = (t <= kuu && j - t >= 0) ? col[kuu - t] * rd : 0.0;
   }
@@ -127,7 +131,7 @@ cudaError_t launch_band_factor(cudaStream_t s, int P, int n, int nnz, int kl, in
                                const BandFactor& f, int npad, int lpad, int upad, DevStatus* st) {
   const int wpb = 4;
   k_band_factor<<<(P + wpb - 1) / wpb, 32 * wpb, 0, s>>>(P, n, nnz, kl, ku, indptr, indices, Mv, Lv,
-                                                        alpha, beta, work, f.L, f.piv, f.U, npad,
+                                                        alpha, beta, work, f.L, f.piv, f.U, f.rd, npad,
                                                         lpad, upad, st);
   return cudaGetLastError();
 }
@@ -210,15 +214,21 @@ __host__ __device__ inline size_t solve_smem_bytes(int npad, int lpad, int upad)
   return off;
 }
 
-template <int RU>
+// PPC pencils per CTA of 128 threads (1 or 2); with PPC = 2 threads
+// [0, 64) serve pencil 2b and [64, 128) pencil 2b + 1, each half with its own
+// shared-memory region.
+template <int RU, int PPC>
 __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int p = blockIdx.x;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int half = (PPC == 2) ? (threadIdx.x >> 6) : 0;
+  const int p = blockIdx.x * PPC + half;
+  const bool active = p < a.P;
+  const int tid = (PPC == 2) ? (threadIdx.x & 63) : threadIdx.x;
+  const int nt = 128 / PPC;
   const int n = a.n;
   SolveSmem sm;
   {
-    size_t off = 0;
+    size_t off = (size_t)half * solve_smem_bytes(a.npad, a.lpad, a.upad);
     sm.B = reinterpret_cast<double2*>(smem_raw + off);
     off += align_up((size_t)(a.npad + 64) * 16, 128);
     sm.Lring = reinterpret_cast<double*>(smem_raw + off);
@@ -233,9 +243,10 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
     sm.abort_flag = reinterpret_cast<int*>(smem_raw + off);
   }
   const int nchunks = a.npad / SOLVE_CHUNK;
-  const double* Lsrc = a.Lf + (size_t)p * a.npad * a.lpad;
-  const double* Usrc = a.Uf + (size_t)p * a.npad * a.upad;
-  const uint8_t* Psrc = a.piv + (size_t)p * a.npad;
+  const int pp = active ? p : 0;             // keeps addresses valid on an idle half
+  const double* Lsrc = a.Lf + (size_t)pp * a.npad * a.lpad;
+  const double* Usrc = a.Uf + (size_t)pp * a.npad * a.upad;
+  const uint8_t* Psrc = a.piv + (size_t)pp * a.npad;
   const uint32_t lbytes = SOLVE_CHUNK * a.lpad * 8, ubytes = SOLVE_CHUNK * a.upad * 8;
 
   auto issue_L = [&](int c) {  // chunk c (forward order) into slot c % RING
@@ -253,7 +264,7 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
              &sm.barU[s]);
   };
 
-  if (tid == 0) {
+  if (tid == 0 && active) {
     for (int s = 0; s < SOLVE_RING; ++s) {
       mbar_init(&sm.barL[s], 1);
       mbar_init(&sm.barU[s], 1);
@@ -268,8 +279,8 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
   // ---- prologue: B~ = linear combination of stored vectors, one matvec,
   //      left-preconditioned F~ (T-to-U conversion, tau rows dropped) and
   //      boundary values
-  const size_t prow = (size_t)p * n;
-  for (int r = tid; r < n; r += nt) {
+  const size_t prow = (size_t)pp * n;
+  for (int r = tid; active && r < n; r += nt) {
     double2 acc = make_double2(0.0, 0.0);
     for (int k = 0; k < a.nvec; ++k) {
       const double2 v = a.vec[k][prow + r];
@@ -278,10 +289,10 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
     }
     if (a.mv_x != nullptr) {
       double2 s = make_double2(0.0, 0.0);
-      const double* vals = a.mv_vals + (size_t)p * a.nnz;
-      for (int e = a.indptr[r]; e < a.indptr[r + 1]; ++e) {
+      const double* vals = a.mv_vals + (size_t)p * a.mv_nnz;
+      for (int e = a.mv_indptr[r]; e < a.mv_indptr[r + 1]; ++e) {
         const double m = vals[e];
-        const double2 x = a.mv_x[prow + a.indices[e]];
+        const double2 x = a.mv_x[prow + a.mv_indices[e]];
         s.x = fma(m, x.x, s.x);
         s.y = fma(m, x.y, s.y);
       }
@@ -291,10 +302,10 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
     }
     sm.B[r] = acc;
   }
-  for (int r = n + tid; r < a.npad + 64; r += nt) sm.B[r] = make_double2(0.0, 0.0);
+  for (int r = n + tid; active && r < a.npad + 64; r += nt) sm.B[r] = make_double2(0.0, 0.0);
   __syncthreads();
   const int Nz = a.Nz;
-  for (int idx = tid; idx < a.n_nl * Nz; idx += nt) {
+  for (int idx = tid; active && idx < a.n_nl * Nz; idx += nt) {
     const int sl = idx / Nz, m = idx - sl * Nz;
     const int e = a.nl_eq[sl];
     const int row = a.row_map[e * Nz + m];
@@ -319,13 +330,13 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
     } else {
       u = f0;
     }
-    u = cipow<double>(u, -a.eq_phase[e]);
+    u = cipow_d(u, -a.eq_phase[e]);
     double2 b = sm.B[row];
     b.x += u.x;
     b.y += u.y;
     sm.B[row] = b;
   }
-  for (int q = tid; q < a.nbc; q += nt) {
+  for (int q = tid; active && q < a.nbc; q += nt) {
     const int row = a.bc_rows[q];
     const double2 g = a.bc_values[(size_t)p * a.nbc + q];
     double2 b = sm.B[row];
@@ -335,26 +346,48 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
   }
   __syncthreads();
 
-  // ---- substitution (warp 0), over the padded columns [0, npad): padding
-  //      columns carry zero factors, so they pass zeros through.
-  //      Chunks are SOLVE_CHUNK = 32 columns, aligned with the 32-lane window,
-  //      so within a chunk step jj the owner lane is jj and the offset of lane
-  //      l from the pivot row is (l - jj) mod 32 (forward) or (jj - l) mod 32
-  //      (backward).  The per-step dependency chain is one shuffle + one FMA;
-  //      everything else (coefficients, pivots, the next window element) is
-  //      loaded ahead of use and merged with predicated selects.
-  if (tid < 32) {
-    const int lane = tid;
+  // ---- substitution, over the padded columns [0, npad): padding columns
+  //      carry zero factors, so they pass zeros through.  Warp 0 solves the
+  //      real part and warp 1 the imaginary part of the right-hand side with
+  //      the same real factor: on GB300 each SM sub-partition retires about
+  //      one FP64 warp instruction per 64 cycles, so the two components run
+  //      on two sub-partitions with one DFMA per step each.
+  //      Chunks are SOLVE_CHUNK = 32 columns, aligned with the 32-lane window:
+  //      within a chunk, step jj is owned by lane jj and lane l sits
+  //      (l - jj) mod 32 rows below the pivot row (forward) or (jj - l) mod 32
+  //      rows above the diagonal (backward).  The per-step dependency chain
+  //      is one shuffle + one FMA; coefficients, pivots and the next window
+  //      element are loaded ahead of use and merged with predicated selects.
+  //      Both warps read each ring slot; named barrier 1 (64 threads) at the
+  //      top of every chunk both agrees on a timed-out wait and frees the
+  //      previous slot for refilling.
+  if (active && tid < 64) {
+    const int lane = tid & 31;
+    const int comp = tid >> 5;                 // 0: real part, 1: imaginary part
+    double* Bd = reinterpret_cast<double*>(sm.B) + comp;   // element j at Bd[2 j]
+    int doneL = 0, doneU = 0;                  // chunks consumed
     bool ok = true;
-    int doneL = 0, doneU = 0;  // chunks consumed (issued = min(nchunks, done + RING))
-    double2* B = sm.B;
+    auto chunk_sync = [&](uint64_t* bar, int k, int& done) -> bool {
+      const bool got = bounded_wait(bar, (k / SOLVE_RING) & 1);
+      if (!got) atomicOr(sm.abort_flag, 1);
+      if (half == 0)
+        asm volatile("bar.sync 1, 64;" ::: "memory");
+      else
+        asm volatile("bar.sync 2, 64;" ::: "memory");
+      if (*sm.abort_flag) return false;
+      done = k + 1;
+      return true;
+    };
     // forward: row interchanges and unit-lower multipliers
-    double2 v = B[lane];          // window element b[j + ((lane - j) & 31)]
-    double2 nv = B[lane + 32];    // the element this lane takes next
-    for (int c = 0; c < nchunks && ok; ++c) {
+    double v = Bd[2 * lane];          // window element b[j + ((lane - j) & 31)]
+    double nv = Bd[2 * (lane + 32)];  // the element this lane takes next
+    for (int c = 0; c < nchunks; ++c) {
       const int s = c % SOLVE_RING;
-      if (!bounded_wait(&sm.barL[s], (c / SOLVE_RING) & 1)) { ok = false; break; }
-      doneL = c + 1;
+      if (!chunk_sync(&sm.barL[s], c, doneL)) { ok = false; break; }
+      if (tid == 0 && c >= 1 && c - 1 + SOLVE_RING < nchunks) {
+        fence_proxy_async();
+        issue_L(c - 1 + SOLVE_RING);   // both warps are past chunk c - 1
+      }
       const double* Lc = sm.Lring + (size_t)s * SOLVE_CHUNK * a.lpad;
       const uint32_t* Pw = reinterpret_cast<const uint32_t*>(sm.Pring + (size_t)s * SOLVE_CHUNK);
       const int j0 = c * SOLVE_CHUNK;
@@ -364,39 +397,35 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
         const int pl = (jj + off) & 31;
         const int d = (lane - jj) & 31;
         const double l = (d >= 1 && d <= a.kl) ? Lc[jj * a.lpad + d - 1] : 0.0;
-        const double2 bj = shfl2(v, pl);   // pivot row value = y_j
-        const double2 vo = shfl2(v, jj);   // old b_j moves to the pivot row
+        const double bj = __shfl_sync(0xffffffffu, v, pl);   // pivot row value = y_j
+        const double vo = __shfl_sync(0xffffffffu, v, jj);   // old b_j moves to the pivot row
+        const double nxt = Bd[2 * (j0 + jj + 64)];   // same address in every lane
         v = (lane == pl) ? vo : v;
-        v.x = fma(-l, bj.x, v.x);
-        v.y = fma(-l, bj.y, v.y);
-        if (lane == jj) {
-          B[j0 + jj] = bj;
-          v = nv;
-          nv = B[j0 + jj + 64];
-        }
-      }
-      __syncwarp();
-      if (lane == 0 && c + SOLVE_RING < nchunks) {
-        fence_proxy_async();
-        issue_L(c + SOLVE_RING);
+        v = fma(-l, bj, v);
+        const bool own = (lane == jj);
+        if (own) Bd[2 * (j0 + jj)] = bj;
+        v = own ? nv : v;
+        nv = own ? nxt : nv;
       }
     }
-    __syncwarp();
-    // backward: scaled U columns, window of 32*RU entries
+    // backward: scaled U columns (U_{j-t,j}/U_jj), window of 32*RU entries;
+    // x_j = b_j / U_jj is applied in the epilogue
     constexpr int W = 32 * RU;
     const int npad = a.npad;
-    double2 w[RU], nw[RU];
+    double w[RU], nw[RU];
 #pragma unroll
     for (int r = 0; r < RU; ++r) {
-      // index congruent to lane + 32 r (mod W) in [npad - W, npad - 1]
-      const int i = npad - W + lane + 32 * r;
-      w[r] = (ok && i >= 0) ? B[i] : make_double2(0.0, 0.0);
-      nw[r] = (ok && i - W >= 0) ? B[i - W] : make_double2(0.0, 0.0);
+      const int i = npad - W + lane + 32 * r;      // congruent to lane + 32 r (mod W)
+      w[r] = (ok && i >= 0) ? Bd[2 * i] : 0.0;
+      nw[r] = (ok && i - W >= 0) ? Bd[2 * (i - W)] : 0.0;
     }
-    for (int k = 0; k < nchunks && ok; ++k) {
+    for (int k = 0; ok && k < nchunks; ++k) {
       const int s = k % SOLVE_RING;
-      if (!bounded_wait(&sm.barU[s], (k / SOLVE_RING) & 1)) { ok = false; break; }
-      doneU = k + 1;
+      if (!chunk_sync(&sm.barU[s], k, doneU)) { ok = false; break; }
+      if (tid == 0 && k >= 1 && k - 1 + SOLVE_RING < nchunks) {
+        fence_proxy_async();
+        issue_U(k - 1 + SOLVE_RING);
+      }
       const double* Uc = sm.Uring + (size_t)s * SOLVE_CHUNK * a.upad;
       const int j0 = (nchunks - 1 - k) * SOLVE_CHUNK;
 #pragma unroll
@@ -404,62 +433,59 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
         const int j = j0 + jj;
         const double* Ucol = Uc + jj * a.upad;
         const int oreg = (RU == 1) ? 0 : ((j & (W - 1)) >> 5);
-        double2 src = w[0];
+        double src = w[0];
 #pragma unroll
         for (int r = 1; r < RU; ++r) src = (oreg == r) ? w[r] : src;
-        const double2 bj = shfl2(src, jj);
+        const double bj = __shfl_sync(0xffffffffu, src, jj);
 #pragma unroll
         for (int r = 0; r < RU; ++r) {
           const int t = (j - lane - 32 * r) & (W - 1);
-          const double u = (t >= 1) ? Ucol[t] : 0.0;   // U_{j-t,j}/U_jj, zero beyond kuu
-          w[r].x = fma(-u, bj.x, w[r].x);
-          w[r].y = fma(-u, bj.y, w[r].y);
+          const double u = (t >= 1) ? Ucol[t] : 0.0;
+          w[r] = fma(-u, bj, w[r]);
         }
-        if (lane == jj) {
-          const double rd = Ucol[0];
-          B[j] = make_double2(bj.x * rd, bj.y * rd);
-          const double2 nxt = (j - 2 * W >= 0) ? B[j - 2 * W] : make_double2(0.0, 0.0);
+        const double nxt = (j - 2 * W >= 0) ? Bd[2 * (j - 2 * W)] : 0.0;   // same address in every lane
+        const bool own = (lane == jj);
+        if (own) Bd[2 * j] = bj;
 #pragma unroll
-          for (int r = 0; r < RU; ++r) {
-            if (oreg == r) {
-              w[r] = nw[r];
-              nw[r] = nxt;
-            }
-          }
+        for (int r = 0; r < RU; ++r) {
+          const bool take = own && (oreg == r);
+          w[r] = take ? nw[r] : w[r];
+          nw[r] = take ? nxt : nw[r];
         }
-      }
-      __syncwarp();
-      if (lane == 0 && k + SOLVE_RING < nchunks) {
-        fence_proxy_async();
-        issue_U(k + SOLVE_RING);
       }
     }
-    if (!ok) {
+    if (!ok && tid == 0) {
       // report, then let every copy in flight land before the CTA exits
-      if (lane == 0) {
-        raise_status(a.status, SP_ERR_TIMEOUT, p);
-        *sm.abort_flag = 1;
-        const int issL = min(nchunks, doneL + SOLVE_RING), issU = min(nchunks, doneU + SOLVE_RING);
-        for (int q = doneL; q < issL; ++q)
-          bounded_wait(&sm.barL[q % SOLVE_RING], (q / SOLVE_RING) & 1);
-        for (int q = doneU; q < issU; ++q)
-          bounded_wait(&sm.barU[q % SOLVE_RING], (q / SOLVE_RING) & 1);
-      }
-      __syncwarp();
+      raise_status(a.status, SP_ERR_TIMEOUT, p);
+      // chunks issued: RING up front, then chunk q - 1 + RING at the top of chunk q
+      const int issL = min(nchunks, doneL == 0 ? SOLVE_RING : doneL - 1 + SOLVE_RING);
+      const int issU = min(nchunks, doneU == 0 ? SOLVE_RING : doneU - 1 + SOLVE_RING);
+      for (int q = doneL; q < issL; ++q) bounded_wait(&sm.barL[q % SOLVE_RING], (q / SOLVE_RING) & 1);
+      for (int q = doneU; q < issU; ++q) bounded_wait(&sm.barU[q % SOLVE_RING], (q / SOLVE_RING) & 1);
     }
   }
   __syncthreads();
-  if (*sm.abort_flag) return;
+  const bool work = active && !*sm.abort_flag;
 
-  // ---- epilogue: store X~, recombine to T coefficients, optional M~ X~
+  // ---- epilogue: x_j = b_j / U_jj, store X~, recombine to T
+  //      coefficients, optional M~ X~
+  {
+    const double* rdp = a.rd + (size_t)pp * a.npad;
+    for (int r = tid; work && r < n; r += nt) {
+      const double q = rdp[r];
+      const double2 b = sm.B[r];
+      sm.B[r] = make_double2(b.x * q, b.y * q);
+    }
+    __syncthreads();
+  }
   bool finite = true;
-  for (int r = tid; r < n; r += nt) {
+  for (int r = tid; work && r < n; r += nt) {
     const double2 x = sm.B[r];
-    finite = finite && isfinite(x.x) && isfinite(x.y);
+    finite = finite && dfinite(x.x) && dfinite(x.y);
     if (a.xt_out) a.xt_out[prow + r] = x;
   }
   if (a.xc_out) {
-    for (int idx = tid; idx < a.S * Nz; idx += nt) {
+    for (int idx = tid; work && idx < a.S * Nz; idx += nt) {
       const int v = idx / Nz, m = idx - v * Nz;
       double2 x = sm.B[a.col_map[idx]];
       if (a.var_recombine[v] && m + 2 < Nz) {
@@ -467,16 +493,16 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
         x.x -= x2.x;
         x.y -= x2.y;
       }
-      a.xc_out[((size_t)v * a.P + p) * Nz + m] = cipow<double>(x, a.var_phase[v]);
+      a.xc_out[((size_t)v * a.P + p) * Nz + m] = cipow_d(x, a.var_phase[v]);
     }
   }
   if (a.ep_mv_vals) {
-    const double* vals = a.ep_mv_vals + (size_t)p * a.nnz;
-    for (int r = tid; r < n; r += nt) {
+    const double* vals = a.ep_mv_vals + (size_t)p * a.ep_nnz;
+    for (int r = tid; work && r < n; r += nt) {
       double2 s = make_double2(0.0, 0.0);
-      for (int e = a.indptr[r]; e < a.indptr[r + 1]; ++e) {
+      for (int e = a.ep_indptr[r]; e < a.ep_indptr[r + 1]; ++e) {
         const double m = vals[e];
-        const double2 x = sm.B[a.indices[e]];
+        const double2 x = sm.B[a.ep_indices[e]];
         s.x = fma(m, x.x, s.x);
         s.y = fma(m, x.y, s.y);
       }
@@ -487,13 +513,16 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
 }
 
 cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a) {
-  const size_t smem = solve_smem_bytes(a.npad, a.lpad, a.upad);
+  constexpr int PPC = 1;
+  const size_t smem = PPC * solve_smem_bytes(a.npad, a.lpad, a.upad);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  const int grid = (a.P + PPC - 1) / PPC;
   if (a.kuu <= 31) {
-    cudaFuncSetAttribute(k_pencil_solve<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_pencil_solve<1><<<a.P, 128, smem, s>>>(a);
+    cudaFuncSetAttribute(k_pencil_solve<1, PPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_pencil_solve<1, PPC><<<grid, 128, smem, s>>>(a);
   } else {
-    cudaFuncSetAttribute(k_pencil_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_pencil_solve<2><<<a.P, 128, smem, s>>>(a);
+    cudaFuncSetAttribute(k_pencil_solve<2, PPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_pencil_solve<2, PPC><<<grid, 128, smem, s>>>(a);
   }
   return cudaGetLastError();
 }

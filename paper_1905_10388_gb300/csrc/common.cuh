@@ -39,6 +39,25 @@ template <typename T> __device__ __forceinline__ C<T> cipow(C<T> a, int q) {
   }
 }
 
+// FP64 helpers that stay off the FP64 pipe (integer operations on the bit
+// pattern): on GB300 each SM sub-partition retires only ~one FP64 warp
+// instruction per 64 cycles, so sign flips and finiteness tests use the ALU.
+__device__ __forceinline__ double dneg(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+__device__ __forceinline__ bool dfinite(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+// i^q * a for double2 without FP64 instructions
+__device__ __forceinline__ double2 cipow_d(double2 a, int q) {
+  switch (q & 3) {
+    case 0: return a;
+    case 1: return make_double2(dneg(a.y), a.x);
+    case 2: return make_double2(dneg(a.x), dneg(a.y));
+    default: return make_double2(a.y, dneg(a.x));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // device status word: first error wins; bad pencil recorded alongside
 // ---------------------------------------------------------------------------

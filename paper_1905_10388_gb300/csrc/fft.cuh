@@ -6,8 +6,8 @@
 // N/R-long input stream has position k = j mod Ns inside its sub-transform,
 // is twiddled by W_N^{t k N/(R Ns)} for input t, combined by a length-R DFT,
 // and written to (j / Ns) R Ns + k + t Ns.  A radix-3 pass runs first when
-// N has the factor 3, then radix-2 passes until Ns = N.  The result is in
-// natural order; no bit reversal.
+// N has the factor 3, then at most one radix-2 pass, then radix-4 passes
+// until Ns = N.  The result is in natural order; no bit reversal.
 //
 // `tw` holds W_N^t = exp(-2 pi i t / N), t < N, computed on the host in FP64
 // (libm) and rounded to T.  sign = -1: forward DFT (exp(-i...)); sign = +1:
@@ -24,44 +24,74 @@ __device__ __forceinline__ C<T> tw_get(const C<T>* tw, int idx, int sign) {
   return w;
 }
 
-// Returns the buffer holding the result (x or y).  Ends with __syncthreads.
+// Copy the twiddle table to shared memory (every FFT pass reads it).
+template <typename T>
+__device__ __forceinline__ void load_twiddles(C<T>* dst, const C<T>* __restrict__ src, int N) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = src[i];
+}
+
+// One radix-R Stockham pass (R = 2, 3 or 4) over nb sequences.
+template <typename T, int R>
+__device__ __forceinline__ void stockham_pass(const C<T>* __restrict__ x, C<T>* __restrict__ y, int N, int Ns,
+                                              const C<T>* __restrict__ tw, int sign, int nb) {
+  const int Q = N / R;
+  const int step = N / (R * Ns);
+  for (int idx = threadIdx.x; idx < nb * Q; idx += blockDim.x) {
+    const int b = idx / Q, j = idx - b * Q;
+    const int k = j % Ns;
+    const C<T>* xb = x + b * N;
+    C<T>* yb = y + b * N;
+    C<T> a[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      a[t] = xb[j + t * Q];
+      if (t > 0) a[t] = cmul<T>(a[t], tw_get<T>(tw, t * k * step, sign));
+    }
+    const int o = (j / Ns) * R * Ns + k;
+    if (R == 2) {
+      yb[o] = cadd<T>(a[0], a[1]);
+      yb[o + Ns] = csub<T>(a[0], a[1]);
+    } else if (R == 3) {
+      const C<T> w1 = tw_get<T>(tw, N / 3, sign), w2 = tw_get<T>(tw, 2 * (N / 3), sign);
+      yb[o] = cadd<T>(a[0], cadd<T>(a[1], a[2]));
+      yb[o + Ns] = cadd<T>(a[0], cadd<T>(cmul<T>(w1, a[1]), cmul<T>(w2, a[2])));
+      yb[o + 2 * Ns] = cadd<T>(a[0], cadd<T>(cmul<T>(w2, a[1]), cmul<T>(w1, a[2])));
+    } else {
+      const C<T> b0 = cadd<T>(a[0], a[2]), b1 = csub<T>(a[0], a[2]), b2 = cadd<T>(a[1], a[3]);
+      const C<T> d = csub<T>(a[1], a[3]);
+      // (a1 - a3) times -i (forward) or +i (inverse)
+      const C<T> b3 = (sign < 0) ? mk<T>(d.y, -d.x) : mk<T>(-d.y, d.x);
+      yb[o] = cadd<T>(b0, b2);
+      yb[o + Ns] = cadd<T>(b1, b3);
+      yb[o + 2 * Ns] = csub<T>(b0, b2);
+      yb[o + 3 * Ns] = csub<T>(b1, b3);
+    }
+  }
+  __syncthreads();
+}
+
+// Batched FFT of nb contiguous length-N sequences: a radix-3 pass when 3 | N,
+// one radix-2 pass when N/3^{0,1} is an odd power of two, then radix-4
+// passes.  `tw` should point to shared memory.  Returns the buffer holding
+// the result (x or y).  Ends with __syncthreads.
 template <typename T>
 __device__ C<T>* fft_batched(C<T>* x, C<T>* y, int N, int radix3, const C<T>* __restrict__ tw,
                              int sign, int nb) {
-  const int tid = threadIdx.x, nt = blockDim.x;
   int Ns = 1;
   if (radix3) {
-    const int Q = N / 3;
-    const C<T> w1 = tw_get<T>(tw, Q, sign), w2 = tw_get<T>(tw, 2 * Q, sign);
-    for (int idx = tid; idx < nb * Q; idx += nt) {
-      const int b = idx / Q, j = idx - b * Q;
-      const C<T>* xb = x + b * N;
-      C<T>* yb = y + b * N;
-      const C<T> a0 = xb[j], a1 = xb[j + Q], a2 = xb[j + 2 * Q];
-      // length-3 DFT, Ns = 1 (no twiddle)
-      yb[3 * j] = cadd<T>(a0, cadd<T>(a1, a2));
-      yb[3 * j + 1] = cadd<T>(a0, cadd<T>(cmul<T>(w1, a1), cmul<T>(w2, a2)));
-      yb[3 * j + 2] = cadd<T>(a0, cadd<T>(cmul<T>(w2, a1), cmul<T>(w1, a2)));
-    }
-    __syncthreads();
+    stockham_pass<T, 3>(x, y, N, Ns, tw, sign, nb);
     C<T>* t = x; x = y; y = t;
     Ns = 3;
   }
-  const int H = N / 2;
-  for (; Ns < N; Ns *= 2) {
-    const int step = N / (2 * Ns);
-    for (int idx = tid; idx < nb * H; idx += nt) {
-      const int b = idx / H, j = idx - b * H;
-      const int k = j % Ns;
-      const C<T>* xb = x + b * N;
-      C<T>* yb = y + b * N;
-      const C<T> a0 = xb[j];
-      const C<T> a1 = cmul<T>(xb[j + H], tw_get<T>(tw, k * step, sign));
-      const int o = (j / Ns) * 2 * Ns + k;
-      yb[o] = cadd<T>(a0, a1);
-      yb[o + Ns] = csub<T>(a0, a1);
-    }
-    __syncthreads();
+  const int M = N / Ns;                 // a power of two
+  const int m = 31 - __clz(M);
+  if (m & 1) {
+    stockham_pass<T, 2>(x, y, N, Ns, tw, sign, nb);
+    C<T>* t = x; x = y; y = t;
+    Ns *= 2;
+  }
+  for (; Ns < N; Ns *= 4) {
+    stockham_pass<T, 4>(x, y, N, Ns, tw, sign, nb);
     C<T>* t = x; x = y; y = t;
   }
   return x;

@@ -22,21 +22,24 @@ struct BandFactor {
   double* L = nullptr;          // [P][npad][lpad]  multipliers of column j (rows j+1..j+kl)
   uint8_t* piv = nullptr;       // [P][npad]        pivot row offset (piv - j) in [0, kl]
   double* U = nullptr;          // [P][npad][upad]  t=0: 1/U_jj, t>=1: U_{j-t,j}/U_jj
+  double* rd = nullptr;         // [P][npad]        1/U_jj (0 on padding columns)
 };
 
 // Arguments of the pencil right-hand-side assembly + solve + epilogue kernel.
 struct SolveArgs {
   int P, n, Nz, S, nbc, nnz;
   int kl, kuu, npad, lpad, upad;
-  const double* Lf; const uint8_t* piv; const double* Uf;
+  const double* Lf; const uint8_t* piv; const double* Uf; const double* rd;
   // prologue: B = sum_k vec_coef[k] vec[k] + mv_coef (Mat x) + sum_k fc_coef[k] P^L Fc_k + bc_coef g
   int nvec; const double2* vec[3]; double vec_coef[3];
   const double2* mv_x; const double* mv_vals; double mv_coef; double2* mv_store;
+  const int32_t* mv_indptr; const int32_t* mv_indices; int mv_nnz;   // pattern of mv_vals
   int nfc; const double2* fc[3]; double fc_coef[3];
   double bc_coef;
   // epilogue
   double2* xt_out; double2* xc_out;
   const double* ep_mv_vals; double2* ep_mv_store;
+  const int32_t* ep_indptr; const int32_t* ep_indices; int ep_nnz;    // pattern of ep_mv_vals
   // tables (device)
   const int32_t* indptr; const int32_t* indices;
   const int32_t* row_map; const int32_t* col_map;

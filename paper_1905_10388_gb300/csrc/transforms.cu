@@ -46,6 +46,8 @@ k_cheb_backward(int Nc, int Ng, int radix3, const C<T>* __restrict__ tw, const C
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* b1 = b0 + Z_TILE * Ng;
+  C<T>* tws = b1 + Z_TILE * Ng;
+  load_twiddles<T>(tws, tw, Ng);
   const int f = blockIdx.y;
   const int p0 = blockIdx.x * Z_TILE;
   const int var = f_var[f], op = f_op[f];
@@ -67,7 +69,7 @@ k_cheb_backward(int Nc, int Ng, int radix3, const C<T>* __restrict__ tw, const C
     b0[idx] = cmulc<T>(d, wq[k]);
   }
   __syncthreads();
-  C<T>* res = fft_batched<T>(b0, b1, Ng, radix3, tw, +1, Z_TILE);
+  C<T>* res = fft_batched<T>(b0, b1, Ng, radix3, tws, +1, Z_TILE);
   for (int idx = threadIdx.x; idx < Z_TILE * Ng; idx += blockDim.x) {
     const int zg = idx / Z_TILE, c = idx - zg * Z_TILE;
     const int p = p0 + c;
@@ -87,6 +89,8 @@ k_cheb_forward(int Nc, int Ng, int radix3, const C<T>* __restrict__ tw, const C<
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* b1 = b0 + Z_TILE * Ng;
+  C<T>* tws = b1 + Z_TILE * Ng;
+  load_twiddles<T>(tws, tw, Ng);
   const int e = blockIdx.y;
   const int p0 = blockIdx.x * Z_TILE;
   for (int idx = threadIdx.x; idx < Z_TILE * Ng; idx += blockDim.x) {
@@ -96,7 +100,7 @@ k_cheb_forward(int Nc, int Ng, int radix3, const C<T>* __restrict__ tw, const C<
     b0[c * Ng + j] = (p < P) ? h[((size_t)e * Ng + zg) * P + p] : mk<T>(0, 0);
   }
   __syncthreads();
-  C<T>* res = fft_batched<T>(b0, b1, Ng, radix3, tw, -1, Z_TILE);
+  C<T>* res = fft_batched<T>(b0, b1, Ng, radix3, tws, -1, Z_TILE);
   const T inv = (T)1 / (T)Ng;
   for (int idx = threadIdx.x; idx < Z_TILE * Nc; idx += blockDim.x) {
     const int c = idx / Nc, k = idx - c * Nc;
@@ -133,8 +137,10 @@ k_fourier_rows(int N, int radix3, const C<T>* __restrict__ tw, int rows, int K, 
   const int nbmax = max(nbi, nbo);
   C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* b1 = b0 + (size_t)nbmax * N;
-  T* G = reinterpret_cast<T*>(b1 + (size_t)nbmax * N);
+  C<T>* tws = b1 + (size_t)nbmax * N;
+  T* G = reinterpret_cast<T*>(tws + N);
   T* O = G + (size_t)nf * N;
+  load_twiddles<T>(tws, tw, N);
   const int row = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
 
@@ -160,7 +166,7 @@ k_fourier_rows(int N, int radix3, const C<T>* __restrict__ tw, int rows, int K, 
       b0[idx] = z;
     }
     __syncthreads();
-    C<T>* res = fft_batched<T>(b0, b1, N, radix3, tw, +1, nbi);
+    C<T>* res = fft_batched<T>(b0, b1, N, radix3, tws, +1, nbi);
     for (int idx = tid; idx < nbi * N; idx += nt) {
       const int q = idx / N, i = idx - q * N;
       G[(size_t)(2 * q) * N + i] = res[idx].x;
@@ -197,7 +203,7 @@ k_fourier_rows(int N, int radix3, const C<T>* __restrict__ tw, int rows, int K, 
       b0[idx] = mk<T>(a, b);
     }
     __syncthreads();
-    C<T>* res = fft_batched<T>(b0, b1, N, radix3, tw, -1, nbo);
+    C<T>* res = fft_batched<T>(b0, b1, N, radix3, tws, -1, nbo);
     const T s = (T)1 / (T)(2 * N);
     for (int idx = tid; idx < nbo * K; idx += nt) {
       const int q = idx / K, k = idx - q * K;
@@ -231,7 +237,7 @@ template <typename T>
 static cudaError_t cheb_bwd_t(cudaStream_t s, const TransformPlan& pz, int P, int nf, const int32_t* f_var,
                               const int32_t* f_op, const double* kx, const double2* xc, int stride,
                               void* gz) {
-  const size_t smem = 2ull * Z_TILE * pz.Ng * sizeof(C<T>);
+  const size_t smem = (2ull * Z_TILE + 1) * pz.Ng * sizeof(C<T>);
   cudaFuncSetAttribute(k_cheb_backward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((P + Z_TILE - 1) / Z_TILE, nf);
   k_cheb_backward<T><<<grid, Z_THREADS, smem, s>>>(pz.Nc, pz.Ng, pz.radix3, tw_of<T>(pz), dct_of<T>(pz), P,
@@ -250,7 +256,7 @@ cudaError_t launch_cheb_backward(cudaStream_t s, int prec, const TransformPlan& 
 template <typename T>
 static cudaError_t cheb_fwd_t(cudaStream_t s, const TransformPlan& pz, int P, int ne, const void* h,
                               double2* fc) {
-  const size_t smem = 2ull * Z_TILE * pz.Ng * sizeof(C<T>);
+  const size_t smem = (2ull * Z_TILE + 1) * pz.Ng * sizeof(C<T>);
   cudaFuncSetAttribute(k_cheb_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((P + Z_TILE - 1) / Z_TILE, ne);
   k_cheb_forward<T><<<grid, Z_THREADS, smem, s>>>(pz.Nc, pz.Ng, pz.radix3, tw_of<T>(pz), dct_of<T>(pz), P,
@@ -271,7 +277,7 @@ static cudaError_t fourier_rows_t(cudaStream_t s, const TransformPlan& px, int r
   const int N = px.Ng;
   const int nout = (mode & 2) ? ne : nf;
   const int nbmax = std::max((nf + 1) / 2, (nout + 1) / 2);
-  size_t smem = 2ull * nbmax * N * sizeof(C<T>) + (size_t)nf * N * sizeof(T);
+  size_t smem = (2ull * nbmax + 1) * N * sizeof(C<T>) + (size_t)nf * N * sizeof(T);
   if (mode & 2) smem += (size_t)ne * N * sizeof(T);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   cudaFuncSetAttribute(k_fourier_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
