@@ -208,6 +208,33 @@ sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku);
 sp_status sp_set_timing(sp_ctx* ctx, int problem, int max_launches);
 sp_status sp_last_solve_time(sp_ctx* ctx, int problem, double* ms_per_launch, int* launches);
 
+/* Backward transform without any device allocation.  The paper has no
+ * counterpart; this entry point is for callers that cannot call cudaMalloc
+ * when they need a transform: code running while a stream is captured into a
+ * CUDA graph (allocation is not capturable and may synchronize the device),
+ * programs whose device memory all belongs to another allocator, and hosts
+ * that must not block on an implicit device synchronization.  It computes
+ * the same thing as sp_transform with direction -1 in FP64, with no context:
+ *   coef_dev  device, nfields * (n_x/2) * n_z complex FP64 ('c' layout
+ *             [f][p][m]), read only;
+ *   grid_dev  device, nfields * N_gz * N_gx FP64 ([f][iz][ix]) on the grid of
+ *             scale scale_num/scale_den, written;
+ *   cuda_stream  stream to queue on (NULL = legacy default stream);
+ *   errbuf/errlen  optional caller buffer for a message on failure.
+ * Its intermediate data and twiddle tables live in fixed static device
+ * arrays that every GPU loading the library keeps until exit: at most
+ * nfields * N_gz * (n_x/2) <= 524288 complex values (8 MiB), N_gx <= 4096,
+ * N_gz <= 1536, nfields <= 16; larger requests return SP_ERR_ARG with the
+ * reason in errbuf.  The first call on a device (with that device current)
+ * looks up the device addresses of those arrays; make it before any stream
+ * capture.  All calls share the arrays: calls that may overlap on the GPU
+ * (other streams or threads without ordering) race and must be serialized.
+ * Each call rewrites everything it reads, so nothing carries over between
+ * calls.  Asynchronous: the result is ready when the stream reaches it. */
+sp_status sp_transform_backward_static(const double* coef_dev, double* grid_dev, int nfields,
+                                       int n_x, int n_z, int scale_num, int scale_den,
+                                       void* cuda_stream, char* errbuf, int errlen);
+
 #ifdef __cplusplus
 }
 #endif

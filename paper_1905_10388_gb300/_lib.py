@@ -26,7 +26,7 @@ EXPORTS = (
     "sp_create", "sp_destroy", "sp_last_error", "sp_add_problem", "sp_set_layout",
     "sp_set_pencils", "sp_set_bilinear_rhs", "sp_factor", "sp_set_field", "sp_get_field",
     "sp_dz", "sp_step", "sp_step_graph", "sp_sync_status", "sp_transform", "sp_eval_rhs",
-    "sp_get_band", "sp_set_timing", "sp_last_solve_time",
+    "sp_get_band", "sp_set_timing", "sp_last_solve_time", "sp_transform_backward_static",
 )
 
 
@@ -70,6 +70,7 @@ _SIGS = {
     "sp_get_band": [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)],
     "sp_set_timing": [P, I, I],
     "sp_last_solve_time": [P, I, ctypes.POINTER(D), ctypes.POINTER(I)],
+    "sp_transform_backward_static": [P, P, I, I, I, I, I, P, ctypes.c_char_p, I],
 }
 
 
