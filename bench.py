@@ -212,6 +212,51 @@ def run_ours(args):
     return result
 
 
+def run_batch(args):
+    """64 independent uneven 2D RB instances advanced together (RK222)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1905_10388_gb300.solver import Context, RBSolver, batch_tile, step_batched
+    ws = si.batched_workloads()
+    ctx = Context(0, torch.cuda.current_stream(0).cuda_stream)
+    solvers = []
+    for w in ws:
+        s = RBSolver(ctx, w.n_x, w.n_z, w.Ra, w.Pr, w.L_x, scheme="RK222", precision=args.precision)
+        s.factor(w.dt)
+        s.set_initial_state(si.rb_noise(w.seed, w.n_z, w.n_x))
+        solvers.append(s)
+    step_batched(solvers, args.warmup, graph=True)
+    ctx.sync_status()
+    stream = torch.cuda.current_stream(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    step_batched(solvers, args.steps, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st, pen = ctx.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} at pencil {pen}")
+    ms = e0.elapsed_time(e1)
+    dof = sum(w.dof for w in ws)
+    res = {"metric": METRIC, "value": dof * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "data": "synthetic (seeded Rayleigh-Benard initial states)",
+           "config": {"workload": "rb2d_batch64_rk222", "instances": len(ws), "dof_total": dof,
+                      "n_x": sorted({w.n_x for w in ws}), "n_z": sorted({w.n_z for w in ws}),
+                      "precision": args.precision, "z_tile": batch_tile(solvers),
+                      "launch": "one batched launch per kernel type per stage, CUDA graph",
+                      "l2": "working set > L2"},
+           "roofline": None, "gpu_launches": 8 * args.steps, "clocks": clk}
+    ctx.close()
+    return res
+
+
 def oracle_rate(workload, steps_timed, warm):
     """The FP64 CPU oracle on the same workload: returns (DOF*steps/s, seconds)."""
     from oracle import rb as orb
@@ -267,6 +312,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         res = run_reference(args)
+    elif args.workload == "rb2d_batch64_rk222":
+        res = run_batch(args)
     else:
         res = run_ours(args)
         if res is not None and not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:

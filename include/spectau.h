@@ -174,6 +174,21 @@ sp_status sp_step(sp_ctx* ctx, int problem, double dt, int nsteps);
  * nsteps) and rebuilt when any of them changes. */
 sp_status sp_step_graph(sp_ctx* ctx, int problem, double dt, int nsteps);
 
+/* Advance a batch of independent problems together (uneven sizes, Rayleigh
+ * numbers and step sizes; one scheme and precision for all).  Each stage
+ * launches each kernel type once for the whole batch: the work of every
+ * problem is listed (largest items first) in one grid, so small problems
+ * fill the SMs left idle by large ones.  dts[q] must equal problem q's
+ * factored dt.  Problems not yet in their steady schedule (fresh state,
+ * SBDF2 first step) are first stepped one by one.  On the first call for a
+ * set of ids the pencil tile of the z-transform kernels is autotuned (4, 8
+ * or 16 columns per CTA, fastest kept; sp_batch_tile reports it).
+ * use_graph = 1 records blocks of up to 16 batch steps in CUDA graphs and
+ * replays them.  Asynchronous. */
+sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, const double* dts,
+                          int nsteps, int use_graph);
+sp_status sp_batch_tile(sp_ctx* ctx, int nproblems, const int* problem_ids, int* tile);
+
 /* Wait for the stream and return the latched device status (SP_OK,
  * SP_ERR_SINGULAR, SP_ERR_NONFINITE or SP_ERR_TIMEOUT); the latch is
  * cleared.  *pencil (may be NULL) receives the first failing pencil or -1. */

@@ -2,6 +2,7 @@
 // validation, device tables, transform plans, factor/step orchestration,
 // CUDA-graph replay and launch timing.  No computation of the step happens
 // on the host; every stage is one of the kernels in band.cu / transforms.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -97,6 +98,10 @@ struct Problem {
   double* d_tcoef = nullptr;
   int32_t *d_ident = nullptr, *d_zero = nullptr;
   double2 *d_Xt = nullptr, *d_Xc = nullptr;
+  float2* d_Xc32 = nullptr;        // FP32 copy of the T coefficients (mixed precision)
+  float* d_kx32 = nullptr;
+  float* d_tcoef32 = nullptr;
+  bool xc32_valid = false;
   double2* d_MX[2] = {nullptr, nullptr};
   double2* d_LX[3] = {nullptr, nullptr, nullptr};
   double2* d_Fc[3] = {nullptr, nullptr, nullptr};
@@ -119,6 +124,7 @@ struct Problem {
   size_t ev_used = 0;
 };
 
+struct Batch;
 struct sp_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -126,6 +132,9 @@ struct sp_ctx {
   std::string err;
   std::vector<std::unique_ptr<Problem>> probs;
   DevStatus* d_status = nullptr;
+  // batches keyed by (problem ids, schedule parity); tile chosen per ids
+  std::map<std::pair<std::vector<int>, int>, Batch*> batches;
+  std::map<std::vector<int>, int> batch_tile;
 };
 
 namespace {
@@ -265,6 +274,12 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
   const size_t nvec = (size_t)pr->P * pr->n;
   CK(dalloc(&pr->d_Xt, nvec));
   CK(dalloc(&pr->d_Xc, nvec));
+  if (pr->prec) {
+    CK(dalloc(&pr->d_Xc32, nvec));
+    std::vector<float> kx32(kx.begin(), kx.end()), tc32(pr->t_coef.begin(), pr->t_coef.end());
+    CK(upload(&pr->d_kx32, kx32, s));
+    CK(upload(&pr->d_tcoef32, tc32, s));
+  }
   CK(cudaMemsetAsync(pr->d_Xc, 0, nvec * sizeof(double2), s));
   for (auto& b : pr->d_MX) CK(dalloc(&b, nvec));
   for (auto& b : pr->d_LX) CK(dalloc(&b, nvec));
@@ -299,7 +314,8 @@ void free_problem(Problem* pr) {
   F(pr->d_indptr); F(pr->d_indices); F(pr->d_Mv); F(pr->d_Lv); F(pr->d_indptrM); F(pr->d_indicesM); F(pr->d_MvC); F(pr->d_col_map); F(pr->d_row_map);
   F(pr->d_var_rec); F(pr->d_var_ph); F(pr->d_eq_diff); F(pr->d_eq_ph); F(pr->d_bc_rows); F(pr->d_nl_eq);
   F(pr->d_bc_values); F(pr->d_kx); F(pr->d_gvar); F(pr->d_gop); F(pr->d_tslot); F(pr->d_tfa); F(pr->d_tfb);
-  F(pr->d_tcoef); F(pr->d_ident); F(pr->d_zero); F(pr->d_Xt); F(pr->d_Xc);
+  F(pr->d_tcoef); F(pr->d_ident); F(pr->d_zero); F(pr->d_Xt); F(pr->d_Xc); F(pr->d_Xc32); F(pr->d_kx32);
+  F(pr->d_tcoef32);
   for (auto b : pr->d_MX) F(b);
   for (auto b : pr->d_LX) F(b);
   for (auto b : pr->d_Fc) F(b);
@@ -319,10 +335,15 @@ sp_status eval_rhs(sp_ctx* ctx, Problem* pr, cudaStream_t s, double2* fc_out) {
   TransformPlan& pz = pr->plans.at({pr->Nz, pr->Ngz});
   TransformPlan& px = pr->plans.at({pr->Nx, pr->Ngx});
   const int nf = (int)pr->gfields.size(), ne = (int)pr->nl_eqs.size();
+  if (pr->prec && !pr->xc32_valid) {
+    CK(launch_to_f32(s, pr->d_Xc, pr->d_Xc32, (size_t)pr->S * pr->P * pr->Nz));
+    pr->xc32_valid = true;
+  }
   CK(launch_cheb_backward(s, pr->prec, pz, pr->P, nf, pr->d_gvar, pr->d_gop, pr->d_kx, pr->d_Xc,
-                          pr->P * pr->Nz, pr->d_gz));
+                          pr->P * pr->Nz, pr->d_gz, pr->d_kx32, pr->d_Xc32));
   CK(launch_fourier_rows(s, pr->prec, px, pr->Ngz, pr->P, 7, nf, pr->d_gz, nullptr, nullptr,
-                         (int)pr->t_slot.size(), pr->d_tslot, pr->d_tcoef, pr->d_tfa, pr->d_tfb, ne, pr->d_h));
+                         (int)pr->t_slot.size(), pr->d_tslot, pr->d_tcoef, pr->d_tfa, pr->d_tfb, ne, pr->d_h,
+                         pr->d_tcoef32));
   CK(launch_cheb_forward(s, pr->prec, pz, pr->P, ne, pr->d_h, fc_out));
   return SP_OK;
 }
@@ -339,6 +360,7 @@ SolveArgs base_args(Problem* pr, sp_ctx* ctx, int fac) {
   a.nl_eq = pr->d_nl_eq; a.n_nl = (int)pr->nl_eqs.size();
   a.bc_rows = pr->d_bc_rows; a.bc_values = pr->d_bc_values;
   a.status = ctx->d_status;
+  a.xc32_out = pr->d_Xc32;   // null unless mixed precision
   return a;
 }
 
@@ -363,21 +385,20 @@ sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
   return SP_OK;
 }
 
-// One IMEX step (Sec. "Timesteppers") queued on stream s.
-sp_status one_step(sp_ctx* ctx, Problem* pr, cudaStream_t s, double dt) {
-  sp_status st;
-  if (!pr->xt_valid) {
-    CK(launch_coef_to_solve(s, pr->P, pr->S, pr->Nz, pr->d_Xc, pr->d_Xt, pr->d_col_map, pr->d_var_rec,
-                            pr->d_var_ph));
-    pr->xt_valid = true;
-    pr->mx_valid = false;
-  }
+// One stage of a step: evaluate F of the current state into fc_out (if
+// set), then one pencil solve with `args`.
+struct StagePlan {
+  double2* fc_out;
+  SolveArgs args;
+};
+
+// The stages of one IMEX step (Sec. "Timesteppers") for the problem's
+// current state, without touching that state.  Valid when xt_valid.
+std::vector<StagePlan> plan_step(sp_ctx* ctx, Problem* pr, double dt) {
+  std::vector<StagePlan> plan;
   if (pr->scheme == SP_RK222 || pr->scheme == SP_RK111) {
     const Tableau tb = make_tableau(pr->scheme);
-    // F(X^0)
-    if ((st = eval_rhs(ctx, pr, s, pr->d_Fc[0])) != SP_OK) return st;
     for (int i = 1; i <= tb.s; ++i) {
-      if (i > 1 && (st = eval_rhs(ctx, pr, s, pr->d_Fc[i - 1])) != SP_OK) return st;
       SolveArgs a = base_args(pr, ctx, 0);
       // M~ X~^0 (stored, or computed on the first stage of a fresh state)
       if (i == 1 && !pr->mx_valid) {
@@ -401,16 +422,14 @@ sp_status one_step(sp_ctx* ctx, Problem* pr, cudaStream_t s, double dt) {
         a.xt_out = pr->d_Xt;
         set_ep_M(pr, a); a.ep_mv_store = pr->d_MX[0];             // M~ X~^{n+1} for the next step
       }
-      if ((st = solve(ctx, pr, s, a)) != SP_OK) return st;
+      plan.push_back(StagePlan{pr->d_Fc[i - 1], a});               // F(X^{i-1}) before stage i
     }
-    pr->mx_valid = true;
   } else {
     // SBDF1 / SBDF2 (Wang & Ruuth 2008), constant step, multiplied through by dt:
     //   SBDF1: (M + dt L) X^n = M X^{n-1} + dt F^{n-1}
     //   SBDF2: (3/2 M + dt L) X^n = 2 M X^{n-1} - 1/2 M X^{n-2} + dt (2 F^{n-1} - F^{n-2})
     const int it = pr->iteration;
     const int cur = it & 1, prv = cur ^ 1;
-    if ((st = eval_rhs(ctx, pr, s, pr->d_Fc[cur])) != SP_OK) return st;
     const bool first = (pr->scheme == SP_SBDF1) || it == 0;
     SolveArgs a = base_args(pr, ctx, first ? 0 : 1);
     if (!pr->mx_valid) {
@@ -431,12 +450,175 @@ sp_status one_step(sp_ctx* ctx, Problem* pr, cudaStream_t s, double dt) {
     a.xt_out = pr->d_Xt;
     a.xc_out = pr->d_Xc;
     set_ep_M(pr, a); a.ep_mv_store = pr->d_MX[prv];               // M~ X~^n for the next step
-    if ((st = solve(ctx, pr, s, a)) != SP_OK) return st;
-    pr->mx_valid = true;
-    if (pr->scheme == SP_SBDF2) {
-      // after an SBDF1 start the slot parity advances like any other step
+    plan.push_back(StagePlan{pr->d_Fc[cur], a});
+  }
+  return plan;
+}
+
+// state after a planned step has been queued
+void commit_step(Problem* pr) {
+  pr->mx_valid = true;
+  if (pr->scheme == SP_SBDF1 || pr->scheme == SP_SBDF2) pr->iteration += 1;
+}
+
+sp_status ensure_solve_vars(sp_ctx* ctx, Problem* pr, cudaStream_t s) {
+  if (!pr->xt_valid) {
+    CK(launch_coef_to_solve(s, pr->P, pr->S, pr->Nz, pr->d_Xc, pr->d_Xt, pr->d_col_map, pr->d_var_rec,
+                            pr->d_var_ph));
+    pr->xt_valid = true;
+    pr->mx_valid = false;
+  }
+  return SP_OK;
+}
+
+// One IMEX step (Sec. "Timesteppers") queued on stream s.
+sp_status one_step(sp_ctx* ctx, Problem* pr, cudaStream_t s, double dt) {
+  sp_status st;
+  if ((st = ensure_solve_vars(ctx, pr, s)) != SP_OK) return st;
+  for (const StagePlan& sp : plan_step(ctx, pr, dt)) {
+    if ((st = eval_rhs(ctx, pr, s, sp.fc_out)) != SP_OK) return st;
+    if ((st = solve(ctx, pr, s, sp.args)) != SP_OK) return st;
+  }
+  commit_step(pr);
+  return SP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches: every kernel type launched once per stage over all problems
+// ---------------------------------------------------------------------------
+ZDesc zdesc_backward(Problem* pr) {
+  TransformPlan& pz = pr->plans.at({pr->Nz, pr->Ngz});
+  ZDesc d{};
+  d.Nc = pz.Nc; d.Ng = pz.Ng; d.radix3 = pz.radix3; d.P = pr->P;
+  d.tw = pr->prec ? pz.tw32 : pz.tw64; d.wq = pr->prec ? pz.dct32 : pz.dct64;
+  d.f_var = pr->d_gvar; d.f_op = pr->d_gop; d.kx = pr->d_kx; d.xc = pr->d_Xc; d.xc_stride = pr->P * pr->Nz;
+  d.gz = pr->d_gz;
+  d.kx32 = pr->d_kx32; d.xc32 = pr->d_Xc32;
+  return d;
+}
+ZDesc zdesc_forward(Problem* pr, double2* fc) {
+  ZDesc d = zdesc_backward(pr);
+  d.h = pr->d_h; d.fc = fc;
+  return d;
+}
+XDesc xdesc_rows(Problem* pr) {
+  TransformPlan& px = pr->plans.at({pr->Nx, pr->Ngx});
+  XDesc d{};
+  d.N = px.Ng; d.radix3 = px.radix3; d.rows = pr->Ngz; d.K = pr->P; d.mode = 7; d.nf = (int)pr->gfields.size();
+  d.tw = pr->prec ? px.tw32 : px.tw64;
+  d.gz = pr->d_gz;
+  d.nterms = (int)pr->t_slot.size(); d.t_eq = pr->d_tslot; d.t_coef = pr->d_tcoef; d.t_fa = pr->d_tfa;
+  d.t_fb = pr->d_tfb; d.ne = (int)pr->nl_eqs.size(); d.h = pr->d_h;
+  d.t_coef32 = pr->d_tcoef32;
+  return d;
+}
+
+}  // namespace
+
+struct BatchStage {
+  ZDesc* d_zb = nullptr; ZDesc* d_zf = nullptr; XDesc* d_x = nullptr; SolveArgs* d_args = nullptr;
+};
+struct Batch {
+  std::vector<int> ids;
+  int prec = 0, scheme = 0, nstage = 0, parity = 0;
+  int tile = 8;
+  int max_ngz = 0, max_kuu = 0;
+  size_t x_smem = 0, s_smem = 0;
+  int4 *d_wzb = nullptr, *d_wx = nullptr, *d_wzf = nullptr, *d_ws = nullptr;
+  int nzb = 0, nx = 0, nzf = 0, ns = 0;
+  std::vector<BatchStage> stages;
+  std::map<int, cudaGraphExec_t> graphs;     // by block length
+};
+
+namespace {
+
+void free_batch(Batch* b) {
+  auto F = [](void* p) { if (p) cudaFree(p); };
+  F(b->d_wzb); F(b->d_wx); F(b->d_wzf); F(b->d_ws);
+  for (auto& st : b->stages) { F(st.d_zb); F(st.d_zf); F(st.d_x); F(st.d_args); }
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+}
+
+template <typename T>
+cudaError_t upload_vec(T** d, const std::vector<T>& v) {
+  cudaError_t e = cudaMalloc((void**)d, std::max<size_t>(v.size(), 1) * sizeof(T));
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Work lists in descending cost order (largest items first).
+sp_status build_batch(sp_ctx* ctx, const std::vector<Problem*>& ps, const std::vector<int>& ids, int tile,
+                      int parity, Batch* b) {
+  b->ids = ids;
+  b->prec = ps[0]->prec;
+  b->scheme = ps[0]->scheme;
+  b->tile = tile;
+  b->parity = parity;
+  std::vector<std::pair<long long, int4>> zb, xr, zf, sv;
+  for (size_t q = 0; q < ps.size(); ++q) {
+    Problem* pr = ps[q];
+    const int nt = (pr->P + tile - 1) / tile;
+    const long long zc = (long long)pr->Ngz * 100 + pr->Nz;
+    for (int f = 0; f < (int)pr->gfields.size(); ++f)
+      for (int t = 0; t < nt; ++t) zb.push_back({zc, make_int4((int)q, t, f, 0)});
+    for (int e = 0; e < (int)pr->nl_eqs.size(); ++e)
+      for (int t = 0; t < nt; ++t) zf.push_back({zc, make_int4((int)q, t, e, 0)});
+    for (int r = 0; r < pr->Ngz; ++r) xr.push_back({(long long)pr->Ngx, make_int4((int)q, r, 0, 0)});
+    for (int p = 0; p < pr->P; ++p) sv.push_back({(long long)pr->n, make_int4((int)q, p, 0, 0)});
+    b->max_ngz = std::max(b->max_ngz, pr->Ngz);
+    b->max_kuu = std::max(b->max_kuu, pr->kl + pr->ku);
+    b->x_smem = std::max(b->x_smem, x_smem_bytes(pr->prec, pr->Ngx, 7, (int)pr->gfields.size(),
+                                                 (int)pr->nl_eqs.size()));
+    b->s_smem = std::max(b->s_smem, pencil_solve_smem(pr->npad, pr->lpad, pr->upad));
+  }
+  auto finish = [](std::vector<std::pair<long long, int4>>& v) {
+    std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
+    std::vector<int4> out;
+    for (auto& x : v) out.push_back(x.second);
+    return out;
+  };
+  auto wzb = finish(zb), wx = finish(xr), wzf = finish(zf), ws = finish(sv);
+  b->nzb = (int)wzb.size(); b->nx = (int)wx.size(); b->nzf = (int)wzf.size(); b->ns = (int)ws.size();
+  CK(upload_vec(&b->d_wzb, wzb));
+  CK(upload_vec(&b->d_wx, wx));
+  CK(upload_vec(&b->d_wzf, wzf));
+  CK(upload_vec(&b->d_ws, ws));
+  // per-stage descriptor tables from the single-problem plans, planned at
+  // the requested schedule parity (multistep schemes alternate buffers)
+  std::vector<std::vector<StagePlan>> plans;
+  for (Problem* pr : ps) {
+    const int saved = pr->iteration;
+    if ((b->scheme == SP_SBDF2 || b->scheme == SP_SBDF1) && (pr->iteration & 1) != parity) pr->iteration += 1;
+    plans.push_back(plan_step(ctx, pr, pr->fac_dt));
+    pr->iteration = saved;
+  }
+  b->nstage = (int)plans[0].size();
+  for (int i = 0; i < b->nstage; ++i) {
+    std::vector<ZDesc> zbv, zfv;
+    std::vector<XDesc> xv;
+    std::vector<SolveArgs> av;
+    for (size_t q = 0; q < ps.size(); ++q) {
+      zbv.push_back(zdesc_backward(ps[q]));
+      xv.push_back(xdesc_rows(ps[q]));
+      zfv.push_back(zdesc_forward(ps[q], plans[q][i].fc_out));
+      av.push_back(plans[q][i].args);
     }
-    pr->iteration = it + 1;
+    BatchStage st;
+    CK(upload_vec(&st.d_zb, zbv));
+    CK(upload_vec(&st.d_x, xv));
+    CK(upload_vec(&st.d_zf, zfv));
+    CK(upload_vec(&st.d_args, av));
+    b->stages.push_back(st);
+  }
+  return SP_OK;
+}
+
+sp_status batch_step(sp_ctx* ctx, Batch* b, cudaStream_t s) {
+  for (const BatchStage& st : b->stages) {
+    CK(launch_cheb_backward_batched(s, b->prec, b->tile, st.d_zb, b->d_wzb, b->nzb, b->max_ngz));
+    CK(launch_fourier_rows_batched(s, b->prec, st.d_x, b->d_wx, b->nx, b->x_smem));
+    CK(launch_cheb_forward_batched(s, b->prec, b->tile, st.d_zf, b->d_wzf, b->nzf, b->max_ngz));
+    CK(launch_pencil_solve_batched(s, st.d_args, b->d_ws, b->ns, b->max_kuu, b->s_smem));
   }
   return SP_OK;
 }
@@ -472,6 +654,7 @@ sp_status sp_destroy(sp_ctx* ctx) {
   if (!ctx) return SP_ERR_ARG;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->batches) { free_batch(kv.second); delete kv.second; }
   for (auto& p : ctx->probs) free_problem(p.get());
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
@@ -648,6 +831,7 @@ sp_status sp_set_bilinear_rhs(sp_ctx* ctx, int problem, int nterms, const int32_
     pr->t_fb.push_back(field(op_b[t], var_b[t]));
   }
   if (pr->gfields.size() > 16) return fail(ctx, SP_ERR_ARG, "at most 16 distinct grid fields");
+  if (nterms > 16) return fail(ctx, SP_ERR_ARG, "at most 16 bilinear terms");
   return SP_OK;
 }
 
@@ -731,6 +915,7 @@ sp_status sp_set_field(sp_ctx* ctx, int problem, int var, const void* data, int 
   CK(cudaGetLastError());
   pr->xt_valid = false;
   pr->mx_valid = false;
+  pr->xc32_valid = false;
   pr->iteration = 0;
   return SP_OK;
 }
@@ -783,6 +968,7 @@ sp_status sp_dz(sp_ctx* ctx, int problem, int src_var, int dst_var) {
   const size_t f = (size_t)pr->P * pr->Nz;
   CK(launch_dz(ctx->stream, pr->P, pr->Nz, 2.0 / (pr->zb - pr->za), pr->d_Xc + src_var * f, pr->d_Xc + dst_var * f));
   pr->xt_valid = false;
+  pr->xc32_valid = false;
   pr->mx_valid = false;
   pr->iteration = 0;
   return SP_OK;
@@ -850,6 +1036,129 @@ sp_status sp_step_graph(sp_ctx* ctx, int problem, double dt, int nsteps) {
   return SP_OK;
 }
 
+sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, const double* dts, int nsteps,
+                          int use_graph) {
+  if (!ctx) return SP_ERR_ARG;
+  ctx->err.clear();
+  if (nproblems < 1 || !problem_ids || !dts || nsteps < 0) return fail(ctx, SP_ERR_ARG, "bad arguments");
+  std::vector<int> ids(problem_ids, problem_ids + nproblems);
+  std::vector<Problem*> ps;
+  for (int q = 0; q < nproblems; ++q) {
+    Problem* pr = get(ctx, ids[q]);
+    if (!pr) return fail(ctx, SP_ERR_ARG, "bad problem id %d", ids[q]);
+    for (int r = 0; r < q; ++r)
+      if (ids[r] == ids[q]) return fail(ctx, SP_ERR_ARG, "problem %d listed twice", ids[q]);
+    if (!pr->factored || dts[q] != pr->fac_dt)
+      return fail(ctx, SP_ERR_NOT_FACTORED, "problem %d: dt = %.17g is not its factored step size", ids[q], dts[q]);
+    if (pr->nl_eqs.empty()) return fail(ctx, SP_ERR_ARG, "problem %d has no bilinear right-hand side", ids[q]);
+    ps.push_back(pr);
+  }
+  for (Problem* pr : ps)
+    if (pr->scheme != ps[0]->scheme || pr->prec != ps[0]->prec)
+      return fail(ctx, SP_ERR_ARG, "all problems of a batch need the same scheme and precision");
+  CK(cudaSetDevice(ctx->device));
+  sp_status st;
+  // eager steps until every problem is in its steady schedule
+  auto steady = [&](Problem* pr) {
+    return pr->xt_valid && pr->mx_valid && !(pr->scheme == SP_SBDF2 && pr->iteration == 0);
+  };
+  while (nsteps > 0 && !std::all_of(ps.begin(), ps.end(), steady)) {
+    for (Problem* pr : ps)
+      if ((st = one_step(ctx, pr, ctx->stream, pr->fac_dt)) != SP_OK) return st;
+    --nsteps;
+  }
+  if (nsteps == 0) return SP_OK;
+  const bool multistep = (ps[0]->scheme == SP_SBDF1 || ps[0]->scheme == SP_SBDF2);
+  for (Problem* pr : ps)
+    if (multistep && (pr->iteration & 1) != (ps[0]->iteration & 1))
+      return fail(ctx, SP_ERR_STATE, "problems of a batch must be at the same step parity");
+  // tile autotuning of the z-transform kernels (first call for these ids)
+  auto get_batch = [&](int parity, int tile) -> Batch* {
+    auto key = std::make_pair(ids, parity);
+    auto it = ctx->batches.find(key);
+    if (it != ctx->batches.end() && it->second->tile == tile) return it->second;
+    if (it != ctx->batches.end()) { free_batch(it->second); delete it->second; ctx->batches.erase(it); }
+    Batch* b = new Batch();
+    if (build_batch(ctx, ps, ids, tile, parity, b) != SP_OK) { free_batch(b); delete b; return nullptr; }
+    ctx->batches[key] = b;
+    return b;
+  };
+  if (!ctx->batch_tile.count(ids)) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = 8;
+    float best_ms = 1e30f;
+    for (int tile : {4, 8, 16}) {
+      Batch* b = get_batch(multistep ? (ps[0]->iteration & 1) : 0, tile);
+      if (!b) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
+      // the transform kernels write only scratch buffers that the next step overwrites
+      const BatchStage& sg = b->stages[0];
+      float tot = 0;
+      for (int rep = 0; rep < 4; ++rep) {
+        CK(cudaEventRecord(e0, ctx->stream));
+        CK(launch_cheb_backward_batched(ctx->stream, b->prec, tile, sg.d_zb, b->d_wzb, b->nzb, b->max_ngz));
+        CK(launch_cheb_forward_batched(ctx->stream, b->prec, tile, sg.d_zf, b->d_wzf, b->nzf, b->max_ngz));
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) tot += ms;
+      }
+      if (tot < best_ms) { best_ms = tot; best = tile; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->batch_tile[ids] = best;
+  }
+  const int tile = ctx->batch_tile[ids];
+  while (nsteps > 0) {
+    const int parity = multistep ? (ps[0]->iteration & 1) : 0;
+    Batch* b = get_batch(parity, tile);
+    if (!b) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
+    if (!use_graph) {
+      if ((st = batch_step(ctx, b, ctx->stream)) != SP_OK) return st;
+      for (Problem* pr : ps) commit_step(pr);
+      --nsteps;
+      continue;
+    }
+    // a graph of `block` steps starting at this parity (parities alternate)
+    const int block = std::min(nsteps, 16);
+    auto git = b->graphs.find(block);
+    cudaGraphExec_t exec = nullptr;
+    if (git == b->graphs.end()) {
+      Batch* other = multistep ? get_batch(parity ^ 1, tile) : b;
+      if (!other) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+      st = SP_OK;
+      for (int k = 0; k < block && st == SP_OK; ++k) st = batch_step(ctx, (k & 1) ? other : b, ctx->capture);
+      cudaError_t e = cudaStreamEndCapture(ctx->capture, &g);
+      if (st != SP_OK) return st;
+      CK(e);
+      CK(cudaGraphInstantiate(&exec, g, 0));
+      cudaGraphDestroy(g);
+      b->graphs[block] = exec;
+    } else {
+      exec = git->second;
+    }
+    CK(cudaGraphLaunch(exec, ctx->stream));
+    for (int k = 0; k < block; ++k)
+      for (Problem* pr : ps) commit_step(pr);
+    nsteps -= block;
+  }
+  return SP_OK;
+}
+
+sp_status sp_batch_tile(sp_ctx* ctx, int nproblems, const int* problem_ids, int* tile) {
+  if (!ctx || nproblems < 1 || !problem_ids || !tile) return SP_ERR_ARG;
+  std::vector<int> ids(problem_ids, problem_ids + nproblems);
+  auto it = ctx->batch_tile.find(ids);
+  if (it == ctx->batch_tile.end()) return fail(ctx, SP_ERR_STATE, "no batch step has run for these problems");
+  *tile = it->second;
+  return SP_OK;
+}
+
 sp_status sp_sync_status(sp_ctx* ctx, int64_t* pencil) {
   if (!ctx) return SP_ERR_ARG;
   CK(cudaSetDevice(ctx->device));
@@ -894,11 +1203,16 @@ sp_status sp_transform(sp_ctx* ctx, int problem, const void* in, void* out, int 
   const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   cudaError_t e;
+  float2* coef32 = nullptr;
   if (direction < 0) {
     e = cudaMemcpyAsync(coef, in, ncoef * sizeof(double2), kin, s);
+    if (e == cudaSuccess && pr->prec) {
+      e = cudaMalloc(&coef32, ncoef * sizeof(float2));
+      if (e == cudaSuccess) e = launch_to_f32(s, coef, coef32, ncoef);
+    }
     if (e == cudaSuccess)
       e = launch_cheb_backward(s, pr->prec, *pz, pr->P, nfields, pr->d_ident, pr->d_zero, pr->d_kx, coef,
-                               pr->P * pr->Nz, mid);
+                               pr->P * pr->Nz, mid, pr->d_kx32, coef32);
     if (e == cudaSuccess)
       e = launch_fourier_rows(s, pr->prec, *px, Ngz, pr->P, 1, nfields, mid, nullptr, grid, 0, nullptr, nullptr,
                               nullptr, nullptr, 0, nullptr);
@@ -915,6 +1229,7 @@ sp_status sp_transform(sp_ctx* ctx, int problem, const void* in, void* out, int 
   cudaFree(coef);
   cudaFree(grid);
   cudaFree(mid);
+  if (coef32) cudaFree(coef32);
   CK(e);
   return SP_OK;
 }

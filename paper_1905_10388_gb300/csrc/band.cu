@@ -19,6 +19,7 @@
 // streamed through a shared-memory ring by bulk asynchronous copies (TMA,
 // cp.async.bulk) issued by one lane and tracked with mbarriers; every wait
 // is bounded and reports SP_ERR_TIMEOUT instead of hanging.
+#include <algorithm>
 #include <cstdio>
 
 #include "internal.h"
@@ -218,10 +219,9 @@ __host__ __device__ inline size_t solve_smem_bytes(int npad, int lpad, int upad)
 // [0, 64) serve pencil 2b and [64, 128) pencil 2b + 1, each half with its own
 // shared-memory region.
 template <int RU, int PPC>
-__global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block, unsigned char* smem_raw) {
   const int half = (PPC == 2) ? (threadIdx.x >> 6) : 0;
-  const int p = blockIdx.x * PPC + half;
+  const int p = block * PPC + half;
   const bool active = p < a.P;
   const int tid = (PPC == 2) ? (threadIdx.x & 63) : threadIdx.x;
   const int nt = 128 / PPC;
@@ -493,7 +493,9 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
         x.x -= x2.x;
         x.y -= x2.y;
       }
-      a.xc_out[((size_t)v * a.P + p) * Nz + m] = cipow_d(x, a.var_phase[v]);
+      const double2 xv = cipow_d(x, a.var_phase[v]);
+      a.xc_out[((size_t)v * a.P + p) * Nz + m] = xv;
+      if (a.xc32_out) a.xc32_out[((size_t)v * a.P + p) * Nz + m] = make_float2((float)xv.x, (float)xv.y);
     }
   }
   if (a.ep_mv_vals) {
@@ -510,6 +512,36 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
     }
   }
   if (!finite) raise_status(a.status, SP_ERR_NONFINITE, p);
+}
+
+template <int RU, int PPC>
+__global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  pencil_solve_body<RU, PPC>(a, blockIdx.x, smem_raw);
+}
+
+// a batch of problems: work item (problem, pencil) per CTA
+template <int RU>
+__global__ void __launch_bounds__(128, 1) k_pencil_solve_batched(const SolveArgs* __restrict__ args,
+                                                                 const int4* __restrict__ work) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int4 w = work[blockIdx.x];
+  pencil_solve_body<RU, 1>(args[w.x], w.y, smem_raw);
+}
+
+size_t pencil_solve_smem(int npad, int lpad, int upad) { return solve_smem_bytes(npad, lpad, upad); }
+
+cudaError_t launch_pencil_solve_batched(cudaStream_t s, const SolveArgs* args, const int4* work, int nwork,
+                                        int max_kuu, size_t smem) {
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  if (max_kuu <= 31) {
+    cudaFuncSetAttribute(k_pencil_solve_batched<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_pencil_solve_batched<1><<<nwork, 128, smem, s>>>(args, work);
+  } else {
+    cudaFuncSetAttribute(k_pencil_solve_batched<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_pencil_solve_batched<2><<<nwork, 128, smem, s>>>(args, work);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a) {
@@ -575,6 +607,16 @@ __global__ void k_dz(int P, int Nz, double scale, const double2* __restrict__ sr
     d2 = d1;
     d1 = dm;
   }
+}
+
+__global__ void k_to_f32(const double2* __restrict__ src, float2* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = make_float2((float)src[i].x, (float)src[i].y);
+}
+
+cudaError_t launch_to_f32(cudaStream_t s, const double2* src, float2* dst, size_t n) {
+  k_to_f32<<<(int)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dz(cudaStream_t s, int P, int Nz, double scale, const double2* src, double2* dst) {

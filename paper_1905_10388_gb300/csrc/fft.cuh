@@ -30,41 +30,52 @@ __device__ __forceinline__ void load_twiddles(C<T>* dst, const C<T>* __restrict_
   for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = src[i];
 }
 
-// One radix-R Stockham pass (R = 2, 3 or 4) over nb sequences.
+// One radix-R Stockham pass (R = 2, 3 or 4) over nb sequences.  Ns is
+// 2^ns_log2 or 3 * 2^ns_log2 (ns_has3); Q = N / R.  Index arithmetic avoids
+// run-time integer division: the sequence loop is outermost and j / Ns,
+// j mod Ns use shifts and a division by the constant 3.
 template <typename T, int R>
 __device__ __forceinline__ void stockham_pass(const C<T>* __restrict__ x, C<T>* __restrict__ y, int N, int Ns,
-                                              const C<T>* __restrict__ tw, int sign, int nb) {
+                                              int ns_log2, bool ns_has3, const C<T>* __restrict__ tw, int sign,
+                                              int nb) {
   const int Q = N / R;
   const int step = N / (R * Ns);
-  for (int idx = threadIdx.x; idx < nb * Q; idx += blockDim.x) {
-    const int b = idx / Q, j = idx - b * Q;
-    const int k = j % Ns;
+  C<T> w1 = mk<T>(0, 0), w2 = mk<T>(0, 0);
+  if (R == 3) {
+    w1 = tw_get<T>(tw, N / 3, sign);
+    w2 = tw_get<T>(tw, 2 * (N / 3), sign);
+  }
+  for (int b = 0; b < nb; ++b) {
     const C<T>* xb = x + b * N;
     C<T>* yb = y + b * N;
-    C<T> a[R];
+    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+      int jq = j >> ns_log2;                       // j / Ns
+      if (ns_has3) jq /= 3;
+      const int k = j - jq * Ns;                   // j mod Ns
+      C<T> a[R];
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      a[t] = xb[j + t * Q];
-      if (t > 0) a[t] = cmul<T>(a[t], tw_get<T>(tw, t * k * step, sign));
-    }
-    const int o = (j / Ns) * R * Ns + k;
-    if (R == 2) {
-      yb[o] = cadd<T>(a[0], a[1]);
-      yb[o + Ns] = csub<T>(a[0], a[1]);
-    } else if (R == 3) {
-      const C<T> w1 = tw_get<T>(tw, N / 3, sign), w2 = tw_get<T>(tw, 2 * (N / 3), sign);
-      yb[o] = cadd<T>(a[0], cadd<T>(a[1], a[2]));
-      yb[o + Ns] = cadd<T>(a[0], cadd<T>(cmul<T>(w1, a[1]), cmul<T>(w2, a[2])));
-      yb[o + 2 * Ns] = cadd<T>(a[0], cadd<T>(cmul<T>(w2, a[1]), cmul<T>(w1, a[2])));
-    } else {
-      const C<T> b0 = cadd<T>(a[0], a[2]), b1 = csub<T>(a[0], a[2]), b2 = cadd<T>(a[1], a[3]);
-      const C<T> d = csub<T>(a[1], a[3]);
-      // (a1 - a3) times -i (forward) or +i (inverse)
-      const C<T> b3 = (sign < 0) ? mk<T>(d.y, -d.x) : mk<T>(-d.y, d.x);
-      yb[o] = cadd<T>(b0, b2);
-      yb[o + Ns] = cadd<T>(b1, b3);
-      yb[o + 2 * Ns] = csub<T>(b0, b2);
-      yb[o + 3 * Ns] = csub<T>(b1, b3);
+      for (int t = 0; t < R; ++t) {
+        a[t] = xb[j + t * Q];
+        if (t > 0) a[t] = cmul<T>(a[t], tw_get<T>(tw, t * k * step, sign));
+      }
+      const int o = jq * R * Ns + k;
+      if (R == 2) {
+        yb[o] = cadd<T>(a[0], a[1]);
+        yb[o + Ns] = csub<T>(a[0], a[1]);
+      } else if (R == 3) {
+        yb[o] = cadd<T>(a[0], cadd<T>(a[1], a[2]));
+        yb[o + Ns] = cadd<T>(a[0], cadd<T>(cmul<T>(w1, a[1]), cmul<T>(w2, a[2])));
+        yb[o + 2 * Ns] = cadd<T>(a[0], cadd<T>(cmul<T>(w2, a[1]), cmul<T>(w1, a[2])));
+      } else {
+        const C<T> b0 = cadd<T>(a[0], a[2]), b1 = csub<T>(a[0], a[2]), b2 = cadd<T>(a[1], a[3]);
+        const C<T> d = csub<T>(a[1], a[3]);
+        // (a1 - a3) times -i (forward) or +i (inverse)
+        const C<T> b3 = (sign < 0) ? mk<T>(d.y, -d.x) : mk<T>(-d.y, d.x);
+        yb[o] = cadd<T>(b0, b2);
+        yb[o + Ns] = cadd<T>(b1, b3);
+        yb[o + 2 * Ns] = csub<T>(b0, b2);
+        yb[o + 3 * Ns] = csub<T>(b1, b3);
+      }
     }
   }
   __syncthreads();
@@ -77,21 +88,24 @@ __device__ __forceinline__ void stockham_pass(const C<T>* __restrict__ x, C<T>* 
 template <typename T>
 __device__ C<T>* fft_batched(C<T>* x, C<T>* y, int N, int radix3, const C<T>* __restrict__ tw,
                              int sign, int nb) {
-  int Ns = 1;
+  int Ns = 1, lg = 0;
+  bool has3 = false;
   if (radix3) {
-    stockham_pass<T, 3>(x, y, N, Ns, tw, sign, nb);
+    stockham_pass<T, 3>(x, y, N, Ns, lg, has3, tw, sign, nb);
     C<T>* t = x; x = y; y = t;
     Ns = 3;
+    has3 = true;
   }
   const int M = N / Ns;                 // a power of two
   const int m = 31 - __clz(M);
   if (m & 1) {
-    stockham_pass<T, 2>(x, y, N, Ns, tw, sign, nb);
+    stockham_pass<T, 2>(x, y, N, Ns, lg, has3, tw, sign, nb);
     C<T>* t = x; x = y; y = t;
     Ns *= 2;
+    lg += 1;
   }
-  for (; Ns < N; Ns *= 4) {
-    stockham_pass<T, 4>(x, y, N, Ns, tw, sign, nb);
+  for (; Ns < N; Ns *= 4, lg += 2) {
+    stockham_pass<T, 4>(x, y, N, Ns, lg, has3, tw, sign, nb);
     C<T>* t = x; x = y; y = t;
   }
   return x;

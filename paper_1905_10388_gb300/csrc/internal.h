@@ -37,7 +37,7 @@ struct SolveArgs {
   int nfc; const double2* fc[3]; double fc_coef[3];
   double bc_coef;
   // epilogue
-  double2* xt_out; double2* xc_out;
+  double2* xt_out; double2* xc_out; float2* xc32_out;   // xc32_out: FP32 copy (mixed precision)
   const double* ep_mv_vals; double2* ep_mv_store;
   const int32_t* ep_indptr; const int32_t* ep_indices; int ep_nnz;    // pattern of ep_mv_vals
   // tables (device)
@@ -62,6 +62,26 @@ struct TransformPlan {
   void* dct32 = nullptr;
 };
 
+// Per-problem descriptors of the transform kernels (tw / wq / gz / h are
+// typed by the precision of the launch).
+struct ZDesc {
+  int Nc, Ng, radix3, P;
+  const void* tw; const void* wq;
+  // backward
+  const int32_t* f_var; const int32_t* f_op; const double* kx; const double2* xc; int xc_stride; void* gz;
+  const float* kx32; const float2* xc32;     // FP32 copies (mixed precision)
+  // forward
+  const void* h; double2* fc;
+};
+struct XDesc {
+  int N, radix3, rows, K, mode, nf;
+  const void* tw;
+  const void* gz; const double* grid_in; double* grid_out;
+  int nterms; const int32_t* t_eq; const double* t_coef; const int32_t* t_fa; const int32_t* t_fb;
+  int ne; void* h;
+  const float* t_coef32;
+};
+
 // --- launchers (band.cu) ---------------------------------------------------
 cudaError_t launch_band_factor(cudaStream_t s, int P, int n, int nnz, int kl, int ku,
                                const int32_t* indptr, const int32_t* indices,
@@ -69,10 +89,14 @@ cudaError_t launch_band_factor(cudaStream_t s, int P, int n, int nnz, int kl, in
                                double* work, const BandFactor& f, int npad, int lpad, int upad,
                                DevStatus* st);
 cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a);
+size_t pencil_solve_smem(int npad, int lpad, int upad);
+cudaError_t launch_pencil_solve_batched(cudaStream_t s, const SolveArgs* args, const int4* work, int nwork,
+                                        int max_kuu, size_t smem);
 cudaError_t launch_coef_to_solve(cudaStream_t s, int P, int S, int Nz, const double2* xc,
                                  double2* xt, const int32_t* col_map, const int32_t* var_recombine,
                                  const int32_t* var_phase);
 cudaError_t launch_dz(cudaStream_t s, int P, int Nz, double scale, const double2* src, double2* dst);
+cudaError_t launch_to_f32(cudaStream_t s, const double2* src, float2* dst, size_t n);
 
 // --- launchers (transforms.cu) ---------------------------------------------
 // precision: 0 = double, 1 = float.  Buffers of the grid stages are typed by
@@ -80,13 +104,21 @@ cudaError_t launch_dz(cudaStream_t s, int P, int Nz, double scale, const double2
 cudaError_t launch_cheb_backward(cudaStream_t s, int prec, const TransformPlan& pz, int P,
                                  int nf, const int32_t* f_var, const int32_t* f_op,
                                  const double* kx, const double2* xc, int xc_field_stride,
-                                 void* gz);
+                                 void* gz, const float* kx32 = nullptr, const float2* xc32 = nullptr);
 cudaError_t launch_fourier_rows(cudaStream_t s, int prec, const TransformPlan& px, int rows,
                                 int P, int mode, int nf, const void* gz, double* grid_in,
                                 double* grid_out, int nterms, const int32_t* t_eq,
                                 const double* t_coef, const int32_t* t_fa, const int32_t* t_fb,
-                                int ne, void* h);
+                                int ne, void* h, const float* t_coef32 = nullptr);
 cudaError_t launch_cheb_forward(cudaStream_t s, int prec, const TransformPlan& pz, int P, int ne,
                                 const void* h, double2* fc);
+size_t z_smem_bytes(int prec, int Ng, int tile);
+size_t x_smem_bytes(int prec, int N, int mode, int nf, int ne);
+cudaError_t launch_cheb_backward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,
+                                         int nwork, int max_ng);
+cudaError_t launch_cheb_forward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,
+                                        int nwork, int max_ng);
+cudaError_t launch_fourier_rows_batched(cudaStream_t s, int prec, const XDesc* ds, const int4* work, int nwork,
+                                        size_t smem);
 
 }  // namespace spectau

@@ -30,48 +30,49 @@
 
 namespace spectau {
 
-constexpr int Z_TILE = 8;       // pencils (columns) per CTA in the z kernels
 constexpr int Z_THREADS = 256;
 constexpr int X_THREADS = 256;
 
 // ---------------------------------------------------------------------------
-// Chebyshev backward: coefficients (with optional i k_x) -> values on N_gz nodes
+// Chebyshev backward: coefficients (with optional i k_x) -> values on N_gz
+// nodes, for the TP pencil columns [bx TP, bx TP + TP) of grid field by.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(Z_THREADS)
-k_cheb_backward(int Nc, int Ng, int radix3, const C<T>* __restrict__ tw, const C<T>* __restrict__ wq, int P,
-                const int32_t* __restrict__ f_var, const int32_t* __restrict__ f_op,
-                const double* __restrict__ kx, const double2* __restrict__ xc, int xc_field_stride,
-                C<T>* __restrict__ gz) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <typename T, int TP>
+__device__ __forceinline__ void cheb_backward_body(const ZDesc& d, int bx, int f, unsigned char* smem_raw) {
+  const int Nc = d.Nc, Ng = d.Ng, P = d.P;
   C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
-  C<T>* b1 = b0 + Z_TILE * Ng;
-  C<T>* tws = b1 + Z_TILE * Ng;
-  load_twiddles<T>(tws, tw, Ng);
-  const int f = blockIdx.y;
-  const int p0 = blockIdx.x * Z_TILE;
-  const int var = f_var[f], op = f_op[f];
-  const double2* src = xc + (size_t)var * xc_field_stride;
-  auto coef = [&](int c, int k) -> double2 {  // X_k (double), zero beyond N_c
+  C<T>* b1 = b0 + TP * Ng;
+  C<T>* tws = b1 + TP * Ng;
+  const C<T>* wq = reinterpret_cast<const C<T>*>(d.wq);
+  load_twiddles<T>(tws, reinterpret_cast<const C<T>*>(d.tw), Ng);
+  const int p0 = bx * TP;
+  const int var = d.f_var[f], op = d.f_op[f];
+  // coefficients in the transform precision T: FP64 state, or its FP32 copy
+  // in mixed mode, so that an FP32 transform executes no FP64 instruction
+  const C<T>* src = reinterpret_cast<const C<T>*>(sizeof(T) == 8 ? (const void*)d.xc : (const void*)d.xc32) +
+                    (size_t)var * d.xc_stride;
+  const T* kxT = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.kx : (const void*)d.kx32);
+  auto coef = [&](int c, int k) -> C<T> {  // X_k, zero beyond N_c
     const int p = p0 + c;
-    if (p >= P || k >= Nc) return make_double2(0.0, 0.0);
-    double2 x = src[(size_t)p * Nc + k];
-    if (op == SP_OP_DX) x = make_double2(-kx[p] * x.y, kx[p] * x.x);
-    const double s = ((k & 1) ? -1.0 : 1.0) * (k == 0 ? 1.0 : 0.5);
-    return make_double2(s * x.x, s * x.y);
+    if (p >= P || k >= Nc) return mk<T>(0, 0);
+    C<T> x = src[(size_t)p * Nc + k];
+    if (op == SP_OP_DX) x = mk<T>(-kxT[p] * x.y, kxT[p] * x.x);
+    const T s = ((k & 1) ? (T)-1 : (T)1) * (k == 0 ? (T)1 : (T)0.5);
+    return mk<T>(s * x.x, s * x.y);
   };
-  for (int idx = threadIdx.x; idx < Z_TILE * Ng; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < TP * Ng; idx += blockDim.x) {
     const int c = idx / Ng, k = idx - c * Ng;
-    const double2 a = coef(c, k);
-    const double2 b = (k == 0) ? make_double2(0.0, 0.0) : coef(c, Ng - k);
+    const C<T> a = coef(c, k);
+    const C<T> b = (k == 0) ? mk<T>(0, 0) : coef(c, Ng - k);
     // X_k - i X_{N-k}
-    const C<T> d = mk<T>((T)(a.x + b.y), (T)(a.y - b.x));
-    b0[idx] = cmulc<T>(d, wq[k]);
+    const C<T> dd = mk<T>(a.x + b.y, a.y - b.x);
+    b0[idx] = cmulc<T>(dd, wq[k]);
   }
   __syncthreads();
-  C<T>* res = fft_batched<T>(b0, b1, Ng, radix3, tws, +1, Z_TILE);
-  for (int idx = threadIdx.x; idx < Z_TILE * Ng; idx += blockDim.x) {
-    const int zg = idx / Z_TILE, c = idx - zg * Z_TILE;
+  C<T>* res = fft_batched<T>(b0, b1, Ng, d.radix3, tws, +1, TP);
+  C<T>* gz = reinterpret_cast<C<T>*>(d.gz);
+  for (int idx = threadIdx.x; idx < TP * Ng; idx += blockDim.x) {
+    const int zg = idx / TP, c = idx - zg * TP;
     const int p = p0 + c;
     if (p >= P) continue;
     const int j = (zg & 1) ? (Ng - 1 - (zg >> 1)) : (zg >> 1);
@@ -82,27 +83,26 @@ k_cheb_backward(int Nc, int Ng, int radix3, const C<T>* __restrict__ tw, const C
 // ---------------------------------------------------------------------------
 // Chebyshev forward: values on N_gz nodes -> first N_c coefficients (double2)
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(Z_THREADS)
-k_cheb_forward(int Nc, int Ng, int radix3, const C<T>* __restrict__ tw, const C<T>* __restrict__ wq, int P,
-               const C<T>* __restrict__ h, double2* __restrict__ fc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <typename T, int TP>
+__device__ __forceinline__ void cheb_forward_body(const ZDesc& d, int bx, int e, unsigned char* smem_raw) {
+  const int Nc = d.Nc, Ng = d.Ng, P = d.P;
   C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
-  C<T>* b1 = b0 + Z_TILE * Ng;
-  C<T>* tws = b1 + Z_TILE * Ng;
-  load_twiddles<T>(tws, tw, Ng);
-  const int e = blockIdx.y;
-  const int p0 = blockIdx.x * Z_TILE;
-  for (int idx = threadIdx.x; idx < Z_TILE * Ng; idx += blockDim.x) {
-    const int zg = idx / Z_TILE, c = idx - zg * Z_TILE;
+  C<T>* b1 = b0 + TP * Ng;
+  C<T>* tws = b1 + TP * Ng;
+  const C<T>* wq = reinterpret_cast<const C<T>*>(d.wq);
+  load_twiddles<T>(tws, reinterpret_cast<const C<T>*>(d.tw), Ng);
+  const C<T>* h = reinterpret_cast<const C<T>*>(d.h);
+  const int p0 = bx * TP;
+  for (int idx = threadIdx.x; idx < TP * Ng; idx += blockDim.x) {
+    const int zg = idx / TP, c = idx - zg * TP;
     const int p = p0 + c;
     const int j = (zg & 1) ? (Ng - 1 - (zg >> 1)) : (zg >> 1);
     b0[c * Ng + j] = (p < P) ? h[((size_t)e * Ng + zg) * P + p] : mk<T>(0, 0);
   }
   __syncthreads();
-  C<T>* res = fft_batched<T>(b0, b1, Ng, radix3, tws, -1, Z_TILE);
+  C<T>* res = fft_batched<T>(b0, b1, Ng, d.radix3, tws, -1, TP);
   const T inv = (T)1 / (T)Ng;
-  for (int idx = threadIdx.x; idx < Z_TILE * Nc; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < TP * Nc; idx += blockDim.x) {
     const int c = idx / Nc, k = idx - c * Nc;
     const int p = p0 + c;
     if (p >= P) continue;
@@ -114,24 +114,19 @@ k_cheb_forward(int Nc, int Ng, int radix3, const C<T>* __restrict__ tw, const C<
     // the k_x = 0 column is the transform of a real function: its
     // coefficients are real (rounding of the two half-spectrum terms would
     // leave an O(eps) imaginary part)
-    fc[((size_t)e * P + p) * Nc + k] = make_double2((double)(o.x * s), p == 0 ? 0.0 : (double)(o.y * s));
+    d.fc[((size_t)e * P + p) * Nc + k] = make_double2((double)(o.x * s), p == 0 ? 0.0 : (double)(o.y * s));
   }
 }
 
 // ---------------------------------------------------------------------------
-// Fourier rows: [backward x] -> [products] -> [forward x]
+// Fourier rows: [backward x] -> [products] -> [forward x] for z-row `row`
 //   mode & 1: input spectra from gz (else real rows from grid_in)
 //   mode & 2: evaluate the bilinear terms (else pass the fields through)
 //   mode & 4: output spectra to h (else real rows to grid_out)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(X_THREADS)
-k_fourier_rows(int N, int radix3, const C<T>* __restrict__ tw, int rows, int K, int mode, int nf,
-               const C<T>* __restrict__ gz, const double* __restrict__ grid_in, double* __restrict__ grid_out,
-               int nterms, const int32_t* __restrict__ t_eq, const double* __restrict__ t_coef,
-               const int32_t* __restrict__ t_fa, const int32_t* __restrict__ t_fb, int ne,
-               C<T>* __restrict__ h) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsigned char* smem_raw) {
+  const int N = d.N, K = d.K, rows = d.rows, mode = d.mode, nf = d.nf, ne = d.ne;
   const int nout = (mode & 2) ? ne : nf;
   const int nbi = (nf + 1) / 2, nbo = (nout + 1) / 2;
   const int nbmax = max(nbi, nbo);
@@ -140,8 +135,9 @@ k_fourier_rows(int N, int radix3, const C<T>* __restrict__ tw, int rows, int K, 
   C<T>* tws = b1 + (size_t)nbmax * N;
   T* G = reinterpret_cast<T*>(tws + N);
   T* O = G + (size_t)nf * N;
-  load_twiddles<T>(tws, tw, N);
-  const int row = blockIdx.x;
+  load_twiddles<T>(tws, reinterpret_cast<const C<T>*>(d.tw), N);
+  const C<T>* gz = reinterpret_cast<const C<T>*>(d.gz);
+  C<T>* h = reinterpret_cast<C<T>*>(d.h);
   const int tid = threadIdx.x, nt = blockDim.x;
 
   if (mode & 1) {
@@ -166,7 +162,7 @@ k_fourier_rows(int N, int radix3, const C<T>* __restrict__ tw, int rows, int K, 
       b0[idx] = z;
     }
     __syncthreads();
-    C<T>* res = fft_batched<T>(b0, b1, N, radix3, tws, +1, nbi);
+    C<T>* res = fft_batched<T>(b0, b1, N, d.radix3, tws, +1, nbi);
     for (int idx = tid; idx < nbi * N; idx += nt) {
       const int q = idx / N, i = idx - q * N;
       G[(size_t)(2 * q) * N + i] = res[idx].x;
@@ -175,21 +171,30 @@ k_fourier_rows(int N, int radix3, const C<T>* __restrict__ tw, int rows, int K, 
   } else {
     for (int idx = tid; idx < nf * N; idx += nt) {
       const int f = idx / N, i = idx - f * N;
-      G[idx] = (T)grid_in[((size_t)f * rows + row) * N + i];
+      G[idx] = (T)d.grid_in[((size_t)f * rows + row) * N + i];
     }
   }
   __syncthreads();
 
   const T* OUT = G;
   if (mode & 2) {
-    for (int idx = tid; idx < ne * N; idx += nt) {
-      const int e = idx / N, i = idx - e * N;
-      T acc = 0;
-      for (int t = 0; t < nterms; ++t) {
-        if (t_eq[t] != e) continue;
-        acc += (T)t_coef[t] * G[(size_t)t_fa[t] * N + i] * G[(size_t)t_fb[t] * N + i];
+    // term tables in shared memory (at most MAX_TERMS terms), equation loop outermost
+    constexpr int MAX_TERMS = 16;
+    __shared__ T tc[MAX_TERMS];
+    __shared__ int ta[MAX_TERMS], tb[MAX_TERMS], te[MAX_TERMS];
+    const int nterms = min(d.nterms, MAX_TERMS);
+    const T* tcoef = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.t_coef : (const void*)d.t_coef32);
+    if (tid < nterms) {
+      tc[tid] = tcoef[tid]; ta[tid] = d.t_fa[tid] * N; tb[tid] = d.t_fb[tid] * N; te[tid] = d.t_eq[tid];
+    }
+    __syncthreads();
+    for (int e = 0; e < ne; ++e) {
+      for (int i = tid; i < N; i += nt) {
+        T acc = 0;
+        for (int t = 0; t < nterms; ++t)
+          if (te[t] == e) acc += tc[t] * G[ta[t] + i] * G[tb[t] + i];
+        O[(size_t)e * N + i] = acc;
       }
-      O[idx] = acc;
     }
     __syncthreads();
     OUT = O;
@@ -203,7 +208,7 @@ k_fourier_rows(int N, int radix3, const C<T>* __restrict__ tw, int rows, int K, 
       b0[idx] = mk<T>(a, b);
     }
     __syncthreads();
-    C<T>* res = fft_batched<T>(b0, b1, N, radix3, tws, -1, nbo);
+    C<T>* res = fft_batched<T>(b0, b1, N, d.radix3, tws, -1, nbo);
     const T s = (T)1 / (T)(2 * N);
     for (int idx = tid; idx < nbo * K; idx += nt) {
       const int q = idx / K, k = idx - q * K;
@@ -216,86 +221,210 @@ k_fourier_rows(int N, int radix3, const C<T>* __restrict__ tw, int rows, int K, 
   } else {
     for (int idx = tid; idx < nout * N; idx += nt) {
       const int f = idx / N, i = idx - f * N;
-      grid_out[((size_t)f * rows + row) * N + i] = (double)OUT[idx];
+      d.grid_out[((size_t)f * rows + row) * N + i] = (double)OUT[idx];
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// launchers
+// kernels: one problem (descriptor by value) or a batch (descriptor table +
+// work list of (problem, x, y) items, one per CTA)
 // ---------------------------------------------------------------------------
-template <typename T>
-static const C<T>* tw_of(const TransformPlan& pl) {
-  return reinterpret_cast<const C<T>*>(sizeof(T) == 8 ? pl.tw64 : pl.tw32);
+template <typename T, int TP>
+__global__ void __launch_bounds__(Z_THREADS) k_cheb_backward(ZDesc d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cheb_backward_body<T, TP>(d, blockIdx.x, blockIdx.y, smem_raw);
+}
+template <typename T, int TP>
+__global__ void __launch_bounds__(Z_THREADS) k_cheb_backward_batched(const ZDesc* __restrict__ ds,
+                                                                   const int4* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int4 w = work[blockIdx.x];
+  cheb_backward_body<T, TP>(ds[w.x], w.y, w.z, smem_raw);
+}
+template <typename T, int TP>
+__global__ void __launch_bounds__(Z_THREADS) k_cheb_forward(ZDesc d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cheb_forward_body<T, TP>(d, blockIdx.x, blockIdx.y, smem_raw);
+}
+template <typename T, int TP>
+__global__ void __launch_bounds__(Z_THREADS) k_cheb_forward_batched(const ZDesc* __restrict__ ds,
+                                                                  const int4* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int4 w = work[blockIdx.x];
+  cheb_forward_body<T, TP>(ds[w.x], w.y, w.z, smem_raw);
 }
 template <typename T>
-static const C<T>* dct_of(const TransformPlan& pl) {
-  return reinterpret_cast<const C<T>*>(sizeof(T) == 8 ? pl.dct64 : pl.dct32);
+__global__ void __launch_bounds__(X_THREADS) k_fourier_rows(XDesc d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fourier_rows_body<T>(d, blockIdx.x, smem_raw);
+}
+template <typename T>
+__global__ void __launch_bounds__(X_THREADS) k_fourier_rows_batched(const XDesc* __restrict__ ds,
+                                                                  const int4* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int4 w = work[blockIdx.x];
+  fourier_rows_body<T>(ds[w.x], w.y, smem_raw);
 }
 
-template <typename T>
-static cudaError_t cheb_bwd_t(cudaStream_t s, const TransformPlan& pz, int P, int nf, const int32_t* f_var,
-                              const int32_t* f_op, const double* kx, const double2* xc, int stride,
-                              void* gz) {
-  const size_t smem = (2ull * Z_TILE + 1) * pz.Ng * sizeof(C<T>);
-  cudaFuncSetAttribute(k_cheb_backward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((P + Z_TILE - 1) / Z_TILE, nf);
-  k_cheb_backward<T><<<grid, Z_THREADS, smem, s>>>(pz.Nc, pz.Ng, pz.radix3, tw_of<T>(pz), dct_of<T>(pz), P,
-                                                    f_var, f_op, kx, xc, stride,
-                                                    reinterpret_cast<C<T>*>(gz));
-  return cudaGetLastError();
+// ---------------------------------------------------------------------------
+// shared-memory sizes and launchers
+// ---------------------------------------------------------------------------
+size_t z_smem_bytes(int prec, int Ng, int tile) {
+  return (2ull * tile + 1) * Ng * (prec ? sizeof(float2) : sizeof(double2));
 }
+size_t x_smem_bytes(int prec, int N, int mode, int nf, int ne) {
+  const int nout = (mode & 2) ? ne : nf;
+  const int nbmax = std::max((nf + 1) / 2, (nout + 1) / 2);
+  const size_t esz = prec ? sizeof(float) : sizeof(double);
+  size_t smem = (2ull * nbmax + 1) * N * 2 * esz + (size_t)nf * N * esz;
+  if (mode & 2) smem += (size_t)ne * N * esz;
+  return smem;
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t smem) {
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Pencil columns per CTA for a single-problem z launch: the widest tile that
+// still gives at least two CTAs per SM (152 SMs).
+static int z_tile_for(int P, int nfields) {
+  for (int t : {16, 8}) if ((long long)((P + t - 1) / t) * nfields >= 2 * 152) return t;
+  return 4;
+}
+
+#define SPECTAU_TILE_DISPATCH(TILE, CALL) \
+  switch (TILE) {                         \
+    case 4: CALL(4); break;               \
+    case 16: CALL(16); break;             \
+    default: CALL(8); break;              \
+  }
 
 cudaError_t launch_cheb_backward(cudaStream_t s, int prec, const TransformPlan& pz, int P, int nf,
                                  const int32_t* f_var, const int32_t* f_op, const double* kx,
-                                 const double2* xc, int xc_field_stride, void* gz) {
-  return prec ? cheb_bwd_t<float>(s, pz, P, nf, f_var, f_op, kx, xc, xc_field_stride, gz)
-              : cheb_bwd_t<double>(s, pz, P, nf, f_var, f_op, kx, xc, xc_field_stride, gz);
-}
-
-template <typename T>
-static cudaError_t cheb_fwd_t(cudaStream_t s, const TransformPlan& pz, int P, int ne, const void* h,
-                              double2* fc) {
-  const size_t smem = (2ull * Z_TILE + 1) * pz.Ng * sizeof(C<T>);
-  cudaFuncSetAttribute(k_cheb_forward<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((P + Z_TILE - 1) / Z_TILE, ne);
-  k_cheb_forward<T><<<grid, Z_THREADS, smem, s>>>(pz.Nc, pz.Ng, pz.radix3, tw_of<T>(pz), dct_of<T>(pz), P,
-                                                   reinterpret_cast<const C<T>*>(h), fc);
+                                 const double2* xc, int xc_field_stride, void* gz, const float* kx32,
+                                 const float2* xc32) {
+  ZDesc d{};
+  d.Nc = pz.Nc; d.Ng = pz.Ng; d.radix3 = pz.radix3; d.P = P;
+  d.tw = prec ? pz.tw32 : pz.tw64; d.wq = prec ? pz.dct32 : pz.dct64;
+  d.f_var = f_var; d.f_op = f_op; d.kx = kx; d.xc = xc; d.xc_stride = xc_field_stride; d.gz = gz;
+  d.kx32 = kx32; d.xc32 = xc32;
+  if (prec && !xc32) return cudaErrorInvalidValue;
+  const int tile = z_tile_for(P, nf);
+  const size_t smem = z_smem_bytes(prec, pz.Ng, tile);
+  dim3 grid((P + tile - 1) / tile, nf);
+  cudaError_t e = cudaSuccess;
+#define CALL(TT)                                                                                   \
+  if (prec) {                                                                                      \
+    if ((e = set_smem(k_cheb_backward<float, TT>, smem)) == cudaSuccess)                           \
+      k_cheb_backward<float, TT><<<grid, Z_THREADS, smem, s>>>(d);                                  \
+  } else {                                                                                         \
+    if ((e = set_smem(k_cheb_backward<double, TT>, smem)) == cudaSuccess)                          \
+      k_cheb_backward<double, TT><<<grid, Z_THREADS, smem, s>>>(d);                                 \
+  }
+  SPECTAU_TILE_DISPATCH(tile, CALL)
+#undef CALL
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_cheb_forward(cudaStream_t s, int prec, const TransformPlan& pz, int P, int ne,
                                 const void* h, double2* fc) {
-  return prec ? cheb_fwd_t<float>(s, pz, P, ne, h, fc) : cheb_fwd_t<double>(s, pz, P, ne, h, fc);
-}
-
-template <typename T>
-static cudaError_t fourier_rows_t(cudaStream_t s, const TransformPlan& px, int rows, int P, int mode, int nf,
-                                  const void* gz, double* grid_in, double* grid_out, int nterms,
-                                  const int32_t* t_eq, const double* t_coef, const int32_t* t_fa,
-                                  const int32_t* t_fb, int ne, void* h) {
-  const int N = px.Ng;
-  const int nout = (mode & 2) ? ne : nf;
-  const int nbmax = std::max((nf + 1) / 2, (nout + 1) / 2);
-  size_t smem = (2ull * nbmax + 1) * N * sizeof(C<T>) + (size_t)nf * N * sizeof(T);
-  if (mode & 2) smem += (size_t)ne * N * sizeof(T);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaFuncSetAttribute(k_fourier_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_fourier_rows<T><<<rows, X_THREADS, smem, s>>>(N, px.radix3, tw_of<T>(px), rows, P, mode, nf,
-                                                   reinterpret_cast<const C<T>*>(gz), grid_in, grid_out,
-                                                   nterms, t_eq, t_coef, t_fa, t_fb, ne,
-                                                   reinterpret_cast<C<T>*>(h));
+  ZDesc d{};
+  d.Nc = pz.Nc; d.Ng = pz.Ng; d.radix3 = pz.radix3; d.P = P;
+  d.tw = prec ? pz.tw32 : pz.tw64; d.wq = prec ? pz.dct32 : pz.dct64;
+  d.h = h; d.fc = fc;
+  const int tile = z_tile_for(P, ne);
+  const size_t smem = z_smem_bytes(prec, pz.Ng, tile);
+  dim3 grid((P + tile - 1) / tile, ne);
+  cudaError_t e = cudaSuccess;
+#define CALL(TT)                                                                                   \
+  if (prec) {                                                                                      \
+    if ((e = set_smem(k_cheb_forward<float, TT>, smem)) == cudaSuccess)                            \
+      k_cheb_forward<float, TT><<<grid, Z_THREADS, smem, s>>>(d);                                   \
+  } else {                                                                                         \
+    if ((e = set_smem(k_cheb_forward<double, TT>, smem)) == cudaSuccess)                           \
+      k_cheb_forward<double, TT><<<grid, Z_THREADS, smem, s>>>(d);                                  \
+  }
+  SPECTAU_TILE_DISPATCH(tile, CALL)
+#undef CALL
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_fourier_rows(cudaStream_t s, int prec, const TransformPlan& px, int rows, int P, int mode,
                                 int nf, const void* gz, double* grid_in, double* grid_out, int nterms,
                                 const int32_t* t_eq, const double* t_coef, const int32_t* t_fa,
-                                const int32_t* t_fb, int ne, void* h) {
-  return prec ? fourier_rows_t<float>(s, px, rows, P, mode, nf, gz, grid_in, grid_out, nterms, t_eq, t_coef,
-                                      t_fa, t_fb, ne, h)
-              : fourier_rows_t<double>(s, px, rows, P, mode, nf, gz, grid_in, grid_out, nterms, t_eq,
-                                       t_coef, t_fa, t_fb, ne, h);
+                                const int32_t* t_fb, int ne, void* h, const float* t_coef32) {
+  XDesc d{};
+  d.N = px.Ng; d.radix3 = px.radix3; d.rows = rows; d.K = P; d.mode = mode; d.nf = nf;
+  d.tw = prec ? px.tw32 : px.tw64;
+  d.gz = gz; d.grid_in = grid_in; d.grid_out = grid_out;
+  d.nterms = nterms; d.t_eq = t_eq; d.t_coef = t_coef; d.t_fa = t_fa; d.t_fb = t_fb; d.ne = ne; d.h = h;
+  d.t_coef32 = t_coef32;
+  if (prec && nterms > 0 && !t_coef32) return cudaErrorInvalidValue;
+  const size_t smem = x_smem_bytes(prec, px.Ng, mode, nf, ne);
+  cudaError_t e;
+  if (prec) {
+    if ((e = set_smem(k_fourier_rows<float>, smem)) != cudaSuccess) return e;
+    k_fourier_rows<float><<<rows, X_THREADS, smem, s>>>(d);
+  } else {
+    if ((e = set_smem(k_fourier_rows<double>, smem)) != cudaSuccess) return e;
+    k_fourier_rows<double><<<rows, X_THREADS, smem, s>>>(d);
+  }
+  return cudaGetLastError();
+}
+
+// batched launches: one CTA per work item
+cudaError_t launch_cheb_backward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,
+                                         int nwork, int max_ng) {
+  const size_t smem = z_smem_bytes(prec, max_ng, tile);
+  cudaError_t e = cudaSuccess;
+#define CALL(TT)                                                                                   \
+  if (prec) {                                                                                      \
+    if ((e = set_smem(k_cheb_backward_batched<float, TT>, smem)) == cudaSuccess)                   \
+      k_cheb_backward_batched<float, TT><<<nwork, Z_THREADS, smem, s>>>(ds, work);                  \
+  } else {                                                                                         \
+    if ((e = set_smem(k_cheb_backward_batched<double, TT>, smem)) == cudaSuccess)                  \
+      k_cheb_backward_batched<double, TT><<<nwork, Z_THREADS, smem, s>>>(ds, work);                 \
+  }
+  SPECTAU_TILE_DISPATCH(tile, CALL)
+#undef CALL
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_forward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,
+                                        int nwork, int max_ng) {
+  const size_t smem = z_smem_bytes(prec, max_ng, tile);
+  cudaError_t e = cudaSuccess;
+#define CALL(TT)                                                                                   \
+  if (prec) {                                                                                      \
+    if ((e = set_smem(k_cheb_forward_batched<float, TT>, smem)) == cudaSuccess)                    \
+      k_cheb_forward_batched<float, TT><<<nwork, Z_THREADS, smem, s>>>(ds, work);                   \
+  } else {                                                                                         \
+    if ((e = set_smem(k_cheb_forward_batched<double, TT>, smem)) == cudaSuccess)                   \
+      k_cheb_forward_batched<double, TT><<<nwork, Z_THREADS, smem, s>>>(ds, work);                  \
+  }
+  SPECTAU_TILE_DISPATCH(tile, CALL)
+#undef CALL
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fourier_rows_batched(cudaStream_t s, int prec, const XDesc* ds, const int4* work, int nwork,
+                                        size_t smem) {
+  cudaError_t e;
+  if (prec) {
+    if ((e = set_smem(k_fourier_rows_batched<float>, smem)) != cudaSuccess) return e;
+    k_fourier_rows_batched<float><<<nwork, X_THREADS, smem, s>>>(ds, work);
+  } else {
+    if ((e = set_smem(k_fourier_rows_batched<double>, smem)) != cudaSuccess) return e;
+    k_fourier_rows_batched<double><<<nwork, X_THREADS, smem, s>>>(ds, work);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace spectau

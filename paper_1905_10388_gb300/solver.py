@@ -218,3 +218,22 @@ class RBSolver(TauSolver):
             self.set_field(v, zero)
         self.set_field("b", b_grid, layout="g")
         self.dz("b", "bz")
+
+
+def step_batched(solvers, nsteps=1, graph=True):
+    """Advance several problems of one context together (``sp_step_batched``)."""
+    ctx = solvers[0].ctx
+    n = len(solvers)
+    ids = (ctypes.c_int * n)(*[s.pid for s in solvers])
+    dts = np.ascontiguousarray([s.dt for s in solvers], dtype=np.float64)
+    L.check(ctx.handle, L.lib().sp_step_batched(ctx.handle, n, ids, L.f64(dts), int(nsteps), 1 if graph else 0))
+
+
+def batch_tile(solvers):
+    """z-kernel pencil tile chosen by the batch autotuner."""
+    ctx = solvers[0].ctx
+    n = len(solvers)
+    ids = (ctypes.c_int * n)(*[s.pid for s in solvers])
+    t = ctypes.c_int()
+    L.check(ctx.handle, L.lib().sp_batch_tile(ctx.handle, n, ids, ctypes.byref(t)))
+    return t.value

@@ -226,39 +226,51 @@ class PencilProblem:
         indptr = np.cumsum(indptr).astype(np.int32)
         indices = ucol.astype(np.int32)
         P = len(kx_list)
-        Mv = np.zeros((P, nnz))
-        Lv = np.zeros((P, nnz))
         nbc = len(self.bc_slots)
-        bcv = np.zeros((P, nbc), dtype=np.complex128)
         vq = {v: self.var_phase.get(v, 0) for v in self.variables}
+        # every entry belongs to one term (or one boundary alternative); its
+        # value on pencil p is scale[term, p] * base value
+        keys = []
+        key_index = {}
+        ent_key = np.empty(len(ents), dtype=np.int64)
+        for t, e in enumerate(ents):
+            k = e[3]
+            if k not in key_index:
+                key_index[k] = len(keys)
+                keys.append(k)
+            ent_key[t] = key_index[k]
+        base = np.array([e[4] for e in ents], dtype=np.float64)
+        is_M = np.array([e[2] == "M" for e in ents])
+        scale = np.zeros((len(keys), P), dtype=np.complex128)
+        bcv = np.zeros((P, nbc), dtype=np.complex128)
         for p, kx in enumerate(kx_list):
-            Mc = np.zeros(nnz, dtype=np.complex128)
-            Lc = np.zeros(nnz, dtype=np.complex128)
             active = [slot.alternatives.index(slot.pick(kx)) for slot in self.bc_slots]
-            for t, (r, c, group, tk, val) in enumerate(ents):
-                if tk[0] == "eq":
-                    _, ei, g, ti = tk
+            for ki, k in enumerate(keys):
+                if k[0] == "eq":
+                    _, ei, g, ti = k
                     eq = self.equations[ei]
                     term = getattr(eq, g)[ti]
-                    coef = complex(_as_fn(term.coef)(kx))
-                    scale = coef * self._phase(vq[term.var] - eq.phase)
+                    scale[ki, p] = complex(_as_fn(term.coef)(kx)) * self._phase(vq[term.var] - eq.phase)
                 else:
-                    _, si, ai = tk
-                    if active[si] != ai:
-                        continue
-                    alt = self.bc_slots[si].alternatives[ai]
-                    scale = self._phase(vq[alt.var] - alt.phase)
-                if group == "M":
-                    Mc[inv[t]] += scale * val
-                else:
-                    Lc[inv[t]] += scale * val
+                    _, si, ai = k
+                    if active[si] == ai:
+                        alt = self.bc_slots[si].alternatives[ai]
+                        scale[ki, p] = self._phase(vq[alt.var] - alt.phase)
             for si, slot in enumerate(self.bc_slots):
                 alt = slot.pick(kx)
                 bcv[p, si] = complex(_as_fn(alt.value)(kx)) * self._phase(-alt.phase)
-            if np.abs(Mc.imag).max(initial=0) > 1e-14 * max(1.0, np.abs(Mc).max()) or \
-               np.abs(Lc.imag).max(initial=0) > 1e-14 * max(1.0, np.abs(Lc).max()):
+        vals = scale[ent_key, :] * base[:, None]                 # [entries, P]
+        Mc = np.zeros((P, nnz), dtype=np.complex128)
+        Lc = np.zeros((P, nnz), dtype=np.complex128)
+        for mask, out in ((is_M, Mc), (~is_M, Lc)):
+            idx = np.nonzero(mask)[0]
+            tmp = np.zeros((nnz, P), dtype=np.complex128)
+            np.add.at(tmp, inv[idx], vals[idx])
+            out[:] = tmp.T
+        for X in (Mc, Lc):
+            if np.abs(X.imag).max(initial=0) > 1e-14 * max(1.0, np.abs(X).max(initial=0)):
                 raise ValueError("pencil is not real under the given phases")
-            Mv[p], Lv[p] = Mc.real, Lc.real
+        Mv, Lv = Mc.real.copy(), Lc.real.copy()
         col_map, row_map, bc_rows = self.layout(N)
         d = ucol - urow
         return dict(
