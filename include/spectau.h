@@ -189,6 +189,33 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
                           int nsteps, int use_graph);
 sp_status sp_batch_tile(sp_ctx* ctx, int nproblems, const int* problem_ids, int* tile);
 
+/* Discrete adjoint of the step (Sec. "Runge-Kutta IMEX integrators": the
+ * transpose of each stage equation), for the RK222 and RK111 schemes.  The
+ * state space is that of sp_set_field/sp_get_field ('c' layout, all S
+ * variables, [v][p][m] complex), with the real inner product of the
+ * (re, im) components.
+ * sp_adjoint_init: after sp_factor, factors the transposed pencils
+ *   A~^T = M~^T + dt H_ii L~^T (banded LU with partial pivoting, FP64) and
+ *   allocates the adjoint work buffers.
+ * sp_step_adjoint: given the state X^n at the start of a step (x_start_dev,
+ *   device, S*P*N_z complex) and lambda = dJ/dX^{n+1} (lambda_dev, device,
+ *   same layout), overwrites lambda with dJ/dX^n.  It recomputes the first
+ *   stage from X^n, solves the transposed stage systems and applies the
+ *   transposes of the dealiased transforms and products (in the problem's
+ *   transform precision).  The problem's state buffers are used as scratch:
+ *   set the state again before stepping forward.  dt must be the factored
+ *   dt.
+ * sp_transform_adjoint: transpose of sp_transform (direction -1: grid
+ *   adjoint in, coefficient adjoint out; +1: coefficient adjoint in, grid
+ *   adjoint out), FP64.
+ * sp_dz_adjoint: src_bar += D^T dst_bar for the Chebyshev derivative of
+ *   sp_dz (device arrays of P*N_z complex). */
+sp_status sp_adjoint_init(sp_ctx* ctx, int problem);
+sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* x_start_dev, void* lambda_dev);
+sp_status sp_transform_adjoint(sp_ctx* ctx, int problem, const void* in, void* out, int nfields,
+                               int direction, int scale_num, int scale_den, int on_device);
+sp_status sp_dz_adjoint(sp_ctx* ctx, int problem, const void* dst_bar_dev, void* src_bar_dev);
+
 /* Wait for the stream and return the latched device status (SP_OK,
  * SP_ERR_SINGULAR, SP_ERR_NONFINITE or SP_ERR_TIMEOUT); the latch is
  * cleared.  *pencil (may be NULL) receives the first failing pencil or -1. */

@@ -69,7 +69,7 @@ class RB2D:
     Chebyshev mode.
     """
 
-    def __init__(self, n_x, n_z, Ra, Pr=1.0, L_x=4.0, dealias=1.5, cheb_method="mmt"):
+    def __init__(self, n_x, n_z, Ra, Pr=1.0, L_x=4.0, dealias=1.5, cheb_method="mmt", lu_method=None):
         self.Nx, self.Nz, self.Lx = int(n_x), int(n_z), float(L_x)
         self.Ra, self.Pr = float(Ra), float(Pr)
         self.problem, self.kappa, self.nu = rb_problem(self.Nz, self.Ra, self.Pr)
@@ -81,7 +81,13 @@ class RB2D:
         self.var = {v: i for i, v in enumerate(RB_VARIABLES)}
         self._mats = None
         # "mmt": explicit T_n(x_i) quadrature (default); "dct": scipy DCT, the
-        # same definition summed in another order (rounding-floor estimates)
+        # same definition summed in another order, with numpy's derivative
+        # recurrence.  lu_method (timesteppers.PencilLU) picks the pencil
+        # factorization: "auto" (dense LAPACK / SuperLU-COLAMD) or "natural"
+        # (SuperLU in natural order).  The variants give rounding-floor
+        # estimates: the same arithmetic summed in other orders.
+        self.cheb_method = cheb_method
+        self.lu_method = lu_method or ("natural" if cheb_method == "dct" else "auto")
         if cheb_method == "dct":
             self._cf, self._cb = bases.chebyshev_forward_dct, bases.chebyshev_backward_dct
         else:
@@ -154,7 +160,13 @@ class RB2D:
         cb = self._cf(fx, self.Nz, axis=0).T                         # [p, n]
         X = np.zeros((self.S, self.P, self.Nz), dtype=np.complex128)
         X[self.var["b"]] = cb
-        X[self.var["bz"]] = bases.chebyshev_derivative(cb, 0.0, 1.0, axis=1)
+        if self.cheb_method == "dct":
+            # second summation order: numpy's derivative recurrence (chebder)
+            import numpy.polynomial.chebyshev as C
+            d = C.chebder(cb, m=1, scl=2.0, axis=1)
+            X[self.var["bz"], :, : self.Nz - 1] = d
+        else:
+            X[self.var["bz"]] = bases.chebyshev_derivative(cb, 0.0, 1.0, axis=1)
         return X
 
     def conductive_state(self):

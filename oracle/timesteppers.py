@@ -50,13 +50,22 @@ DENSE_LIMIT = 1000
 
 
 class PencilLU:
-    """LU factors of a*M_p + b*L_p for every pencil (dense LAPACK or SuperLU)."""
+    """LU factors of a*M_p + b*L_p for every pencil.
 
-    def __init__(self, mats, a, b):
+    method "auto": dense LAPACK getrf up to DENSE_LIMIT rows, else SuperLU
+    with COLAMD column ordering; "natural": SuperLU in the natural column
+    order (partial pivoting, the elimination order of a band solver).  Both
+    solve the same systems; the second gives another rounding order for
+    floor estimates.
+    """
+
+    def __init__(self, mats, a, b, method="auto"):
         self.factors = []
         for (M, L) in mats:
             A = (a * M + b * L)
-            if A.shape[0] <= DENSE_LIMIT:
+            if method == "natural":
+                self.factors.append(("sparse", spla.splu(sps.csc_matrix(A), permc_spec="NATURAL")))
+            elif A.shape[0] <= DENSE_LIMIT:
                 self.factors.append(("dense", sla.lu_factor(A.toarray())))
             else:
                 self.factors.append(("sparse", spla.splu(sps.csc_matrix(A))))
@@ -76,7 +85,8 @@ class _Factors:
     def get(self, a, b):
         key = (float(a), float(b))
         if key not in self.cache:
-            self.cache[key] = PencilLU(self.system.matrices(), a, b)
+            self.cache[key] = PencilLU(self.system.matrices(), a, b,
+                                       getattr(self.system, "lu_method", "auto"))
         return self.cache[key]
 
 

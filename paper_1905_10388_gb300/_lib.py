@@ -27,7 +27,8 @@ EXPORTS = (
     "sp_set_pencils", "sp_set_bilinear_rhs", "sp_factor", "sp_set_field", "sp_get_field",
     "sp_dz", "sp_step", "sp_step_graph", "sp_sync_status", "sp_transform", "sp_eval_rhs",
     "sp_get_band", "sp_set_timing", "sp_last_solve_time", "sp_transform_backward_static",
-    "sp_step_batched", "sp_batch_tile",
+    "sp_step_batched", "sp_batch_tile", "sp_adjoint_init", "sp_step_adjoint", "sp_transform_adjoint",
+    "sp_dz_adjoint",
 )
 
 
@@ -74,6 +75,10 @@ _SIGS = {
     "sp_transform_backward_static": [P, P, I, I, I, I, I, P, ctypes.c_char_p, I],
     "sp_step_batched": [P, I, ctypes.POINTER(I), F64P, I, I],
     "sp_batch_tile": [P, I, ctypes.POINTER(I), ctypes.POINTER(I)],
+    "sp_adjoint_init": [P, I],
+    "sp_step_adjoint": [P, I, D, P, P],
+    "sp_transform_adjoint": [P, I, P, P, I, I, I, I, I],
+    "sp_dz_adjoint": [P, I, P, P],
 }
 
 

@@ -116,6 +116,16 @@ struct Problem {
   // stepping state
   int iteration = 0;
   bool xt_valid = false, mx_valid = false;
+  // adjoint: factor of the transposed pencils and work buffers
+  bool adj_ready = false;
+  BandFactor facT;
+  int klT = 0, kuT = 0, lpadT = 0;
+  int32_t *d_indptrT = nullptr, *d_indicesT = nullptr;
+  double *d_MvT = nullptr, *d_LvT = nullptr;
+  double2 *d_mu[2] = {nullptr, nullptr}, *d_LTmu = nullptr, *d_MTmu = nullptr, *d_JF = nullptr, *d_lamx = nullptr;
+  double2 *d_X0save = nullptr, *d_Xbar = nullptr, *d_Fbar = nullptr;
+  float2* d_Fbar32 = nullptr;
+  void* d_gzadj = nullptr;
   // graphs
   std::map<std::tuple<int, int, int, double>, cudaGraphExec_t> graphs;
   // timing
@@ -321,6 +331,10 @@ void free_problem(Problem* pr) {
   for (auto b : pr->d_Fc) F(b);
   F(pr->d_gz); F(pr->d_h);
   for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); F(f.rd); }
+  F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd);
+  F(pr->d_indptrT); F(pr->d_indicesT); F(pr->d_MvT); F(pr->d_LvT);
+  F(pr->d_mu[0]); F(pr->d_mu[1]); F(pr->d_LTmu); F(pr->d_MTmu); F(pr->d_JF); F(pr->d_lamx);
+  F(pr->d_X0save); F(pr->d_Xbar); F(pr->d_Fbar); F(pr->d_Fbar32); F(pr->d_gzadj);
   for (auto& kv : pr->plans) { F(kv.second.tw64); F(kv.second.tw32); F(kv.second.dct64); F(kv.second.dct32); }
   for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
   for (auto e : pr->ev) cudaEventDestroy(e);
@@ -511,6 +525,45 @@ XDesc xdesc_rows(Problem* pr) {
   d.t_fb = pr->d_tfb; d.ne = (int)pr->nl_eqs.size(); d.h = pr->d_h;
   d.t_coef32 = pr->d_tcoef32;
   return d;
+}
+
+// --- adjoint ---------------------------------------------------------------
+// Solve arguments for A~^T y = rhs with the transposed factor (no right-hand
+// side assembly beyond stored vectors, no boundary values).
+SolveArgs transposed_args(Problem* pr, sp_ctx* ctx) {
+  SolveArgs a = base_args(pr, ctx, 0);
+  a.kl = pr->klT; a.kuu = pr->klT + pr->kuT; a.lpad = pr->lpadT;
+  a.Lf = pr->facT.L; a.piv = pr->facT.piv; a.Uf = pr->facT.U; a.rd = pr->facT.rd;
+  a.n_nl = 0; a.nbc = 0; a.bc_coef = 0.0;
+  a.xc32_out = nullptr;
+  return a;
+}
+
+// out = J_F(X)^H (sum_k c_k vecs_k) + sum_a w_a adds_a in solve variables,
+// X the T coefficients currently in d_Xc (Sec. "Runge-Kutta IMEX
+// integrators": transpose of the right-hand side of a stage).
+sp_status adjoint_rhs(sp_ctx* ctx, Problem* pr, cudaStream_t s, int nv, const double2* const* vecs,
+                      const double* coefs, int na, const double2* const* adds, const double* wts, double2* out) {
+  TransformPlan& pz = pr->plans.at({pr->Nz, pr->Ngz});
+  TransformPlan& px = pr->plans.at({pr->Nx, pr->Ngx});
+  const int nf = (int)pr->gfields.size(), ne = (int)pr->nl_eqs.size();
+  if (pr->prec && !pr->xc32_valid) {
+    CK(launch_to_f32(s, pr->d_Xc, pr->d_Xc32, (size_t)pr->S * pr->P * pr->Nz));
+    pr->xc32_valid = true;
+  }
+  CK(launch_adj_gather(s, pr->P, pr->Nz, pr->Ngz, pr->n, ne, pr->d_nl_eq, pr->d_row_map, pr->d_eq_diff,
+                       pr->d_eq_ph, nv, vecs, coefs, pr->d_Fbar, pr->prec ? pr->d_Fbar32 : nullptr));
+  CK(launch_cheb_backward(s, pr->prec, pz, pr->P, nf, pr->d_gvar, pr->d_gop, pr->d_kx, pr->d_Xc, pr->P * pr->Nz,
+                          pr->d_gz, pr->d_kx32, pr->d_Xc32));
+  CK(launch_cheb_backward(s, pr->prec, pz, pr->P, ne, pr->d_ident, pr->d_zero, pr->d_kx, pr->d_Fbar,
+                          pr->P * pr->Nz, pr->d_h, pr->d_kx32, pr->d_Fbar32));
+  CK(launch_fourier_rows_adjoint(s, pr->prec, px, pr->Ngz, pr->P, nf, pr->d_gz, ne, pr->d_h,
+                                 (int)pr->t_slot.size(), pr->d_tslot, pr->d_tcoef, pr->d_tcoef32, pr->d_tfa,
+                                 pr->d_tfb, pr->d_gzadj));
+  CK(launch_cheb_forward(s, pr->prec, pz, pr->P, nf, pr->d_gzadj, pr->d_Xbar, 1));
+  CK(launch_adj_combine(s, pr->P, pr->Nz, pr->S, pr->n, nf, pr->d_gvar, pr->d_gop, pr->d_kx, pr->d_Xbar,
+                        pr->d_col_map, pr->d_var_rec, pr->d_var_ph, na, adds, wts, out));
+  return SP_OK;
 }
 
 }  // namespace
@@ -1156,6 +1209,237 @@ sp_status sp_batch_tile(sp_ctx* ctx, int nproblems, const int* problem_ids, int*
   auto it = ctx->batch_tile.find(ids);
   if (it == ctx->batch_tile.end()) return fail(ctx, SP_ERR_STATE, "no batch step has run for these problems");
   *tile = it->second;
+  return SP_OK;
+}
+
+sp_status sp_adjoint_init(sp_ctx* ctx, int problem) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (pr->scheme != SP_RK222 && pr->scheme != SP_RK111)
+    return fail(ctx, SP_ERR_ARG, "the adjoint step is provided for the RK222 and RK111 schemes");
+  if (!pr->factored) return fail(ctx, SP_ERR_STATE, "sp_factor must come before sp_adjoint_init");
+  if (pr->nl_eqs.empty()) return fail(ctx, SP_ERR_ARG, "the problem has no bilinear right-hand side");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const int n = pr->n;
+  const int64_t nnz = pr->nnz;
+  if (!pr->adj_ready) {
+    // CSR of the transposed pencils (same pattern for every pencil)
+    std::vector<int32_t> ipT(n + 1, 0), ixT(nnz);
+    std::vector<int64_t> where(nnz);
+    for (int64_t e = 0; e < nnz; ++e) ipT[pr->indices[e] + 1]++;
+    for (int r = 0; r < n; ++r) ipT[r + 1] += ipT[r];
+    std::vector<int32_t> fill(ipT.begin(), ipT.end() - 1);
+    for (int r = 0; r < n; ++r)
+      for (int e = pr->indptr[r]; e < pr->indptr[r + 1]; ++e) {
+        const int c = pr->indices[e];
+        ixT[fill[c]] = r;
+        where[fill[c]] = e;
+        fill[c]++;
+      }
+    std::vector<double> MT((size_t)pr->P * nnz), LT((size_t)pr->P * nnz);
+    for (int p = 0; p < pr->P; ++p)
+      for (int64_t k = 0; k < nnz; ++k) {
+        MT[(size_t)p * nnz + k] = pr->Mv[(size_t)p * nnz + where[k]];
+        LT[(size_t)p * nnz + k] = pr->Lv[(size_t)p * nnz + where[k]];
+      }
+    CK(upload(&pr->d_indptrT, ipT, s));
+    CK(upload(&pr->d_indicesT, ixT, s));
+    CK(upload(&pr->d_MvT, MT, s));
+    CK(upload(&pr->d_LvT, LT, s));
+    pr->klT = pr->ku;
+    pr->kuT = pr->kl;
+    if (pr->klT > 31) return fail(ctx, SP_ERR_ARG, "transposed lower band width %d > 31", pr->klT);
+    pr->lpadT = std::max(2, (pr->klT + 1) / 2 * 2);
+    CK(dalloc(&pr->facT.L, (size_t)pr->P * pr->npad * pr->lpadT));
+    CK(dalloc(&pr->facT.piv, (size_t)pr->P * pr->npad));
+    CK(dalloc(&pr->facT.U, (size_t)pr->P * pr->npad * pr->upad));
+    CK(dalloc(&pr->facT.rd, (size_t)pr->P * pr->npad));
+    const size_t nvec = (size_t)pr->P * n;
+    for (auto& b : pr->d_mu) CK(dalloc(&b, nvec));
+    CK(dalloc(&pr->d_LTmu, nvec));
+    CK(dalloc(&pr->d_MTmu, nvec));
+    CK(dalloc(&pr->d_JF, nvec));
+    CK(dalloc(&pr->d_lamx, nvec));
+    CK(dalloc(&pr->d_X0save, nvec));
+    const int nf = (int)pr->gfields.size(), ne = (int)pr->nl_eqs.size();
+    CK(dalloc(&pr->d_Xbar, (size_t)nf * pr->P * pr->Nz));
+    CK(dalloc(&pr->d_Fbar, (size_t)ne * pr->P * pr->Nz));
+    if (pr->prec) CK(dalloc(&pr->d_Fbar32, (size_t)ne * pr->P * pr->Nz));
+    CK(cudaMalloc(&pr->d_gzadj, (size_t)nf * pr->Ngz * pr->P * (pr->prec ? 8 : 16)));
+    pr->adj_ready = true;
+  }
+  // factor A~^T = alpha M~^T + beta L~^T with the forward step's coefficients
+  const int ldab = pr->klT + pr->klT + pr->kuT + 1;
+  double* work = nullptr;
+  CK(dalloc(&work, (size_t)pr->P * n * ldab));
+  cudaError_t e = launch_band_factor(s, pr->P, n, (int)nnz, pr->klT, pr->kuT, pr->d_indptrT, pr->d_indicesT,
+                                     pr->d_MvT, pr->d_LvT, pr->fac[0].alpha, pr->fac[0].beta, work, pr->facT,
+                                     pr->npad, pr->lpadT, pr->upad, ctx->d_status);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(work);
+  CK(e);
+  pr->facT.alpha = pr->fac[0].alpha;
+  pr->facT.beta = pr->fac[0].beta;
+  return SP_OK;
+}
+
+sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* x_start_dev, void* lambda_dev) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (!pr->adj_ready || pr->facT.beta != pr->fac[0].beta)
+    return fail(ctx, SP_ERR_STATE, "sp_adjoint_init must follow the last sp_factor");
+  if (!pr->factored || dt != pr->fac_dt)
+    return fail(ctx, SP_ERR_NOT_FACTORED, "dt = %.17g is not the factored step size", dt);
+  if (!x_start_dev || !lambda_dev) return fail(ctx, SP_ERR_ARG, "null pointer");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  sp_status st;
+  const Tableau tb = make_tableau(pr->scheme);
+  const size_t ncoef = (size_t)pr->S * pr->P * pr->Nz;
+  // forward recomputation of the first stage from X^n (the state buffers of
+  // the problem are used as scratch)
+  CK(cudaMemcpyAsync(pr->d_X0save, x_start_dev, ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(pr->d_Xc, x_start_dev, ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  pr->xt_valid = false;
+  pr->xc32_valid = false;
+  pr->mx_valid = false;
+  pr->iteration = 0;
+  if ((st = ensure_solve_vars(ctx, pr, s)) != SP_OK) return st;
+  if (tb.s == 2) {
+    if ((st = eval_rhs(ctx, pr, s, pr->d_Fc[0])) != SP_OK) return st;
+    SolveArgs a = base_args(pr, ctx, 0);
+    a.mv_x = pr->d_Xt; a.mv_coef = 1.0; a.mv_store = nullptr;
+    set_mv_M(pr, a);
+    a.fc[0] = pr->d_Fc[0]; a.fc_coef[0] = dt * tb.A[1][0]; a.nfc = 1;
+    a.bc_coef = dt * tb.A[1][0];
+    a.xc_out = pr->d_Xc;                                   // X^1
+    if ((st = solve(ctx, pr, s, a)) != SP_OK) return st;
+    pr->xc32_valid = (pr->prec != 0);
+  }
+  // lambda^s in solve variables: T^H lambda_X
+  {
+    const double2* none[1] = {nullptr};
+    double w0[1] = {0.0};
+    CK(launch_adj_combine(s, pr->P, pr->Nz, pr->S, pr->n, pr->S, pr->d_ident, pr->d_zero, nullptr,
+                          reinterpret_cast<const double2*>(lambda_dev), pr->d_col_map, pr->d_var_rec, pr->d_var_ph,
+                          0, none, w0, pr->d_lamx));
+  }
+  // stage s: mu_s = A~^-T lambda^s ; keep L~^T mu_s
+  {
+    SolveArgs t = transposed_args(pr, ctx);
+    t.vec[0] = pr->d_lamx; t.vec_coef[0] = 1.0; t.nvec = 1;
+    t.xt_out = pr->d_mu[tb.s - 1];
+    if (tb.s == 2) {
+      t.ep_mv_vals = pr->d_LvT; t.ep_indptr = pr->d_indptrT; t.ep_indices = pr->d_indicesT;
+      t.ep_nnz = (int)pr->nnz; t.ep_mv_store = pr->d_LTmu;
+    } else {
+      t.ep_mv_vals = pr->d_MvT; t.ep_indptr = pr->d_indptrT; t.ep_indices = pr->d_indicesT;
+      t.ep_nnz = (int)pr->nnz; t.ep_mv_store = pr->d_MTmu;
+    }
+    if ((st = solve(ctx, pr, s, t)) != SP_OK) return st;
+  }
+  if (tb.s == 2) {
+    // lambda^1 = dt A21 J_F(X^1)^H mu_2 - dt H21 L~^T mu_2 (X^1 is in d_Xc)
+    const double2* v[1] = {pr->d_mu[1]};
+    const double c[1] = {dt * tb.A[2][1]};
+    const double2* ad[1] = {pr->d_LTmu};
+    const double w[1] = {-dt * tb.H[2][1]};
+    if ((st = adjoint_rhs(ctx, pr, s, 1, v, c, 1, ad, w, pr->d_JF)) != SP_OK) return st;
+    // mu_1 = A~^-T lambda^1 ; M~^T (mu_1 + mu_2)
+    SolveArgs t = transposed_args(pr, ctx);
+    t.vec[0] = pr->d_JF; t.vec_coef[0] = 1.0; t.nvec = 1;
+    t.xt_out = pr->d_mu[0];
+    t.ep_mv_vals = pr->d_MvT; t.ep_indptr = pr->d_indptrT; t.ep_indices = pr->d_indicesT;
+    t.ep_nnz = (int)pr->nnz; t.ep_mv_store = pr->d_MTmu; t.ep_mv_addvec = pr->d_mu[1];
+    if ((st = solve(ctx, pr, s, t)) != SP_OK) return st;
+  }
+  // lambda^0 = M~^T sum_k mu_k + dt J_F(X^0)^H sum_k A_k0 mu_k
+  CK(cudaMemcpyAsync(pr->d_Xc, pr->d_X0save, ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  pr->xc32_valid = false;
+  {
+    const double2* v[2];
+    double c[2];
+    int nv = 0;
+    for (int k = 1; k <= tb.s; ++k) { v[nv] = pr->d_mu[k - 1]; c[nv++] = dt * tb.A[k][0]; }
+    const double2* ad[1] = {pr->d_MTmu};
+    const double w[1] = {1.0};
+    if ((st = adjoint_rhs(ctx, pr, s, nv, v, c, 1, ad, w, pr->d_lamx)) != SP_OK) return st;
+  }
+  CK(launch_adj_tinvh(s, pr->P, pr->Nz, pr->S, pr->n, pr->d_lamx, pr->d_col_map, pr->d_var_rec, pr->d_var_ph,
+                      reinterpret_cast<double2*>(lambda_dev)));
+  // the problem's state buffers were scratch: the next forward step needs a state
+  pr->xt_valid = false;
+  pr->mx_valid = false;
+  pr->xc32_valid = false;
+  return SP_OK;
+}
+
+sp_status sp_transform_adjoint(sp_ctx* ctx, int problem, const void* in, void* out, int nfields, int direction,
+                               int scale_num, int scale_den, int on_device) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (!in || !out || nfields < 1 || nfields > 16 || (direction != 1 && direction != -1))
+    return fail(ctx, SP_ERR_ARG, "bad arguments");
+  if (scale_num <= 0 || scale_den <= 0 || scale_num < scale_den ||
+      (pr->Nx * scale_num) % scale_den || (pr->Nz * scale_num) % scale_den)
+    return fail(ctx, SP_ERR_ARG, "scale must be >= 1 and give integer grid sizes");
+  CK(cudaSetDevice(ctx->device));
+  sp_status st = upload_problem(ctx, pr);
+  if (st != SP_OK) return st;
+  const int Ngx = pr->Nx * scale_num / scale_den, Ngz = pr->Nz * scale_num / scale_den;
+  TransformPlan *px, *pz;
+  if ((st = make_plan(ctx, pr, pr->Nx, Ngx, &px)) != SP_OK) return st;
+  if ((st = make_plan(ctx, pr, pr->Nz, Ngz, &pz)) != SP_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const size_t ncoef = (size_t)nfields * pr->P * pr->Nz, ngrid = (size_t)nfields * Ngz * Ngx;
+  double2* coef = nullptr;
+  double* grid = nullptr;
+  void* mid = nullptr;
+  CK(dalloc(&coef, ncoef));
+  CK(dalloc(&grid, ngrid));
+  CK(cudaMalloc(&mid, (size_t)nfields * Ngz * pr->P * 16));
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e;
+  if (direction < 0) {
+    // transpose of coefficients -> grid: grid adjoint in, coefficient adjoint out
+    e = cudaMemcpyAsync(grid, in, ngrid * sizeof(double), kin, s);
+    if (e == cudaSuccess)
+      e = launch_fourier_rows(s, 0, *px, Ngz, pr->P, 4, nfields, nullptr, grid, nullptr, 0, nullptr, nullptr,
+                              nullptr, nullptr, 0, mid, nullptr, 2);
+    if (e == cudaSuccess) e = launch_cheb_forward(s, 0, *pz, pr->P, nfields, mid, coef, 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, coef, ncoef * sizeof(double2), kout, s);
+  } else {
+    // transpose of grid -> coefficients: coefficient adjoint in, grid adjoint out
+    e = cudaMemcpyAsync(coef, in, ncoef * sizeof(double2), kin, s);
+    if (e == cudaSuccess)
+      e = launch_cheb_backward(s, 0, *pz, pr->P, nfields, pr->d_ident, pr->d_zero, pr->d_kx, coef, pr->P * pr->Nz,
+                               mid, nullptr, nullptr, 1);
+    if (e == cudaSuccess)
+      e = launch_fourier_rows(s, 0, *px, Ngz, pr->P, 1, nfields, mid, nullptr, grid, 0, nullptr, nullptr, nullptr,
+                              nullptr, 0, nullptr, nullptr, 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, grid, ngrid * sizeof(double), kout, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(coef);
+  cudaFree(grid);
+  cudaFree(mid);
+  CK(e);
+  return SP_OK;
+}
+
+sp_status sp_dz_adjoint(sp_ctx* ctx, int problem, const void* dst_bar_dev, void* src_bar_dev) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (!dst_bar_dev || !src_bar_dev) return fail(ctx, SP_ERR_ARG, "null pointer");
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_dz_adjoint(ctx->stream, pr->P, pr->Nz, 2.0 / (pr->zb - pr->za),
+                       reinterpret_cast<const double2*>(dst_bar_dev), reinterpret_cast<double2*>(src_bar_dev)));
   return SP_OK;
 }
 

@@ -504,7 +504,12 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
       double2 s = make_double2(0.0, 0.0);
       for (int e = a.ep_indptr[r]; e < a.ep_indptr[r + 1]; ++e) {
         const double m = vals[e];
-        const double2 x = sm.B[a.ep_indices[e]];
+        double2 x = sm.B[a.ep_indices[e]];
+        if (a.ep_mv_addvec) {
+          const double2 y = a.ep_mv_addvec[prow + a.ep_indices[e]];
+          x.x += y.x;
+          x.y += y.y;
+        }
         s.x = fma(m, x.x, s.x);
         s.y = fma(m, x.y, s.y);
       }
@@ -624,4 +629,171 @@ cudaError_t launch_dz(cudaStream_t s, int P, int Nz, double scale, const double2
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// adjoint-step helpers (discrete adjoint of the RK IMEX step)
+// ---------------------------------------------------------------------------
+// F-bar[slot][p][n] from row-space pencil vectors: the transpose of the
+// right-hand-side placement (row_map), of the equation phase i^{-q_e}, of the
+// T-to-U conversion with its dropped tau row, and of the forward Chebyshev
+// weights (2 - delta_n0)/N_g (so that a plain backward transform follows):
+//   u_m = i^{q_e} sum_k c_k v_k[row(e, m)]
+//   differential: F_n = (u_n - u_{n-2}) / N_g;  algebraic: F_n = u_n (2 - delta_n0) / N_g
+__global__ void k_adj_gather(int P, int Nz, int Ng, int n, int nslot, const int32_t* __restrict__ nl_eq,
+                             const int32_t* __restrict__ row_map, const int32_t* __restrict__ eq_diff,
+                             const int32_t* __restrict__ eq_phase, VecList4 vl, double2* __restrict__ fbar,
+                             float2* __restrict__ fbar32) {
+  const int p = blockIdx.x;
+  const int nvec = vl.n;
+  const double2* v[4];
+  double c[4];
+  for (int k = 0; k < nvec; ++k) { v[k] = vl.p[k] + (size_t)p * n; c[k] = vl.c[k]; }
+  auto u_at = [&](int e, int m) -> double2 {
+    const int row = row_map[e * Nz + m];
+    if (row < 0) return make_double2(0.0, 0.0);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < nvec; ++k) {
+      const double2 x = v[k][row];
+      acc.x = fma(c[k], x.x, acc.x);
+      acc.y = fma(c[k], x.y, acc.y);
+    }
+    return cipow_d(acc, eq_phase[e]);
+  };
+  const double inv = 1.0 / Ng;
+  for (int idx = threadIdx.x; idx < nslot * Nz; idx += blockDim.x) {
+    const int sl = idx / Nz, m = idx - sl * Nz;
+    const int e = nl_eq[sl];
+    double2 f;
+    if (eq_diff[e]) {
+      const double2 u0 = u_at(e, m);
+      const double2 u2 = (m >= 2) ? u_at(e, m - 2) : make_double2(0.0, 0.0);
+      f = make_double2((u0.x - u2.x) * inv, (u0.y - u2.y) * inv);
+    } else {
+      const double2 u0 = u_at(e, m);
+      const double w = (m == 0 ? 1.0 : 2.0) * inv;
+      f = make_double2(u0.x * w, u0.y * w);
+    }
+    const size_t o = ((size_t)sl * P + p) * Nz + m;
+    fbar[o] = f;
+    if (fbar32) fbar32[o] = make_float2((float)f.x, (float)f.y);
+  }
+}
+
+cudaError_t launch_adj_gather(cudaStream_t s, int P, int Nz, int Ng, int n, int nslot, const int32_t* nl_eq,
+                              const int32_t* row_map, const int32_t* eq_diff, const int32_t* eq_phase,
+                              int nvec, const double2* const* vecs, const double* coefs, double2* fbar,
+                              float2* fbar32) {
+  if (nvec > 4) return cudaErrorInvalidValue;
+  VecList4 vl{};
+  vl.n = nvec;
+  for (int k = 0; k < nvec; ++k) { vl.p[k] = vecs[k]; vl.c[k] = coefs[k]; }
+  k_adj_gather<<<P, 128, 0, s>>>(P, Nz, Ng, n, nslot, nl_eq, row_map, eq_diff, eq_phase, vl, fbar, fbar32);
+  return cudaGetLastError();
+}
+
+// out[p][col(v, m)] = i^{-q_v} (Xb_v[m] - rec_v Xb_v[m-2]) + sum_k a_k add_k[p][col(v, m)],
+// Xb_v = sum over grid fields f of variable v of op_f^H xbar_f  (op DX: -i k_x)
+__global__ void k_adj_combine(int P, int Nz, int S, int n, int nf, const int32_t* __restrict__ f_var,
+                              const int32_t* __restrict__ f_op, const double* __restrict__ kx,
+                              const double2* __restrict__ xbar, const int32_t* __restrict__ col_map,
+                              const int32_t* __restrict__ var_rec, const int32_t* __restrict__ var_phase,
+                              VecList4 al, double2* __restrict__ out) {
+  const int p = blockIdx.x;
+  const double k = kx ? kx[p] : 0.0;
+  auto xb = [&](int v, int m) -> double2 {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int f = 0; f < nf; ++f) {
+      if (f_var[f] != v) continue;
+      const double2 x = xbar[((size_t)f * P + p) * Nz + m];
+      if (f_op[f] == SP_OP_DX) {       // times -i k
+        acc.x = fma(k, x.y, acc.x);
+        acc.y = fma(-k, x.x, acc.y);
+      } else {
+        acc.x += x.x;
+        acc.y += x.y;
+      }
+    }
+    return acc;
+  };
+  for (int idx = threadIdx.x; idx < S * Nz; idx += blockDim.x) {
+    const int v = idx / Nz, m = idx - v * Nz;
+    double2 y = xb(v, m);
+    if (var_rec[v] && m >= 2) {
+      const double2 y2 = xb(v, m - 2);
+      y.x -= y2.x;
+      y.y -= y2.y;
+    }
+    y = cipow_d(y, -var_phase[v]);
+    const int c = col_map[idx];
+    for (int a = 0; a < al.n; ++a) {
+      const double2 z = al.p[a][(size_t)p * n + c];
+      y.x = fma(al.c[a], z.x, y.x);
+      y.y = fma(al.c[a], z.y, y.y);
+    }
+    out[(size_t)p * n + c] = y;
+  }
+}
+
+cudaError_t launch_adj_combine(cudaStream_t s, int P, int Nz, int S, int n, int nf, const int32_t* f_var,
+                               const int32_t* f_op, const double* kx, const double2* xbar,
+                               const int32_t* col_map, const int32_t* var_rec, const int32_t* var_phase,
+                               int nadd, const double2* const* adds, const double* add_coefs, double2* out) {
+  if (nadd > 4) return cudaErrorInvalidValue;
+  VecList4 al{};
+  al.n = nadd;
+  for (int k = 0; k < nadd; ++k) { al.p[k] = adds[k]; al.c[k] = add_coefs[k]; }
+  k_adj_combine<<<P, 128, 0, s>>>(P, Nz, S, n, nf, f_var, f_op, kx, xbar, col_map, var_rec, var_phase, al, out);
+  return cudaGetLastError();
+}
+
+// Inverse of the transposed change of variables: Xb_v[m] = i^{q_v} xt[col(v, m)] + rec_v Xb_v[m-2]
+__global__ void k_adj_tinvh(int P, int Nz, int S, int n, const double2* __restrict__ xt,
+                            const int32_t* __restrict__ col_map, const int32_t* __restrict__ var_rec,
+                            const int32_t* __restrict__ var_phase, double2* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P * S) return;
+  const int v = idx / P, p = idx - v * P;
+  double2 m1 = make_double2(0.0, 0.0), m2 = make_double2(0.0, 0.0);   // Xb[m-1], Xb[m-2]
+  for (int m = 0; m < Nz; ++m) {
+    double2 y = cipow_d(xt[(size_t)p * n + col_map[v * Nz + m]], var_phase[v]);
+    if (var_rec[v]) { y.x += m2.x; y.y += m2.y; }
+    out[((size_t)v * P + p) * Nz + m] = y;
+    m2 = m1;
+    m1 = y;
+  }
+}
+
+cudaError_t launch_adj_tinvh(cudaStream_t s, int P, int Nz, int S, int n, const double2* xt_bar,
+                             const int32_t* col_map, const int32_t* var_rec, const int32_t* var_phase,
+                             double2* out) {
+  k_adj_tinvh<<<(P * S + 127) / 128, 128, 0, s>>>(P, Nz, S, n, xt_bar, col_map, var_rec, var_phase, out);
+  return cudaGetLastError();
+}
+
+// Transpose of the Chebyshev derivative (k_dz): with d = D c,
+// D_{ij} = scale 2 j / (1 + delta_i0) for i < j, j - i odd, the adjoint
+// c_bar_j += scale 2 j sum_{i < j, j - i odd} d_bar_i / (1 + delta_i0).
+__global__ void k_dz_adjoint(int P, int Nz, double scale, const double2* __restrict__ dbar,
+                             double2* __restrict__ cbar) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const double2* d = dbar + (size_t)p * Nz;
+  double2* c = cbar + (size_t)p * Nz;
+  double2 run[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};   // prefix sums by parity of i
+  for (int j = 0; j < Nz; ++j) {
+    // sum over i < j with i of parity opposite to j
+    const double2 sacc = run[(j + 1) & 1];
+    const double f = scale * 2.0 * j;
+    c[j] = make_double2(c[j].x + f * sacc.x, c[j].y + f * sacc.y);
+    const double w = (j == 0) ? 0.5 : 1.0;
+    run[j & 1].x += w * d[j].x;
+    run[j & 1].y += w * d[j].y;
+  }
+}
+
+cudaError_t launch_dz_adjoint(cudaStream_t s, int P, int Nz, double scale, const double2* dst_bar,
+                              double2* src_bar) {
+  k_dz_adjoint<<<(P + 127) / 128, 128, 0, s>>>(P, Nz, scale, dst_bar, src_bar);
+  return cudaGetLastError();
+}
 }  // namespace spectau

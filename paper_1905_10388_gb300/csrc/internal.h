@@ -25,6 +25,28 @@ struct BandFactor {
   double* rd = nullptr;         // [P][npad]        1/U_jj (0 on padding columns)
 };
 
+// Up to four device vectors with coefficients, passed to kernels by value.
+struct VecList4 {
+  const double2* p[4];
+  double c[4];
+  int n;
+};
+
+// Adjoint-step helper kernels (band.cu).
+cudaError_t launch_adj_gather(cudaStream_t s, int P, int Nz, int Ng, int n, int nslot, const int32_t* nl_eq,
+                              const int32_t* row_map, const int32_t* eq_diff, const int32_t* eq_phase,
+                              int nvec, const double2* const* vecs, const double* coefs, double2* fbar,
+                              float2* fbar32);
+cudaError_t launch_adj_combine(cudaStream_t s, int P, int Nz, int S, int n, int nf, const int32_t* f_var,
+                               const int32_t* f_op, const double* kx, const double2* xbar,
+                               const int32_t* col_map, const int32_t* var_rec, const int32_t* var_phase,
+                               int nadd, const double2* const* adds, const double* add_coefs, double2* out);
+cudaError_t launch_adj_tinvh(cudaStream_t s, int P, int Nz, int S, int n, const double2* xt_bar,
+                             const int32_t* col_map, const int32_t* var_rec, const int32_t* var_phase,
+                             double2* out);
+cudaError_t launch_dz_adjoint(cudaStream_t s, int P, int Nz, double scale, const double2* dst_bar,
+                              double2* src_bar);
+
 // Arguments of the pencil right-hand-side assembly + solve + epilogue kernel.
 struct SolveArgs {
   int P, n, Nz, S, nbc, nnz;
@@ -39,6 +61,7 @@ struct SolveArgs {
   // epilogue
   double2* xt_out; double2* xc_out; float2* xc32_out;   // xc32_out: FP32 copy (mixed precision)
   const double* ep_mv_vals; double2* ep_mv_store;
+  const double2* ep_mv_addvec;                 // epilogue matvec acts on (X~ + addvec) if set
   const int32_t* ep_indptr; const int32_t* ep_indices; int ep_nnz;    // pattern of ep_mv_vals
   // tables (device)
   const int32_t* indptr; const int32_t* indices;
@@ -72,6 +95,8 @@ struct ZDesc {
   const float* kx32; const float2* xc32;     // FP32 copies (mixed precision)
   // forward
   const void* h; double2* fc;
+  int unweighted;                            // 1: transpose of the backward transform
+  int weighted_in;                           // 1: transpose of the forward transform
 };
 struct XDesc {
   int N, radix3, rows, K, mode, nf;
@@ -80,6 +105,8 @@ struct XDesc {
   int nterms; const int32_t* t_eq; const double* t_coef; const int32_t* t_fa; const int32_t* t_fb;
   int ne; void* h;
   const float* t_coef32;
+  const void* hin; void* gzadj;             // adjoint rows: inputs / outputs
+  int xscale;                                // bit 1: transpose of forward x on input; bit 2: of backward x on output
 };
 
 // --- launchers (band.cu) ---------------------------------------------------
@@ -104,14 +131,19 @@ cudaError_t launch_to_f32(cudaStream_t s, const double2* src, float2* dst, size_
 cudaError_t launch_cheb_backward(cudaStream_t s, int prec, const TransformPlan& pz, int P,
                                  int nf, const int32_t* f_var, const int32_t* f_op,
                                  const double* kx, const double2* xc, int xc_field_stride,
-                                 void* gz, const float* kx32 = nullptr, const float2* xc32 = nullptr);
+                                 void* gz, const float* kx32 = nullptr, const float2* xc32 = nullptr,
+                                 int weighted_in = 0);
 cudaError_t launch_fourier_rows(cudaStream_t s, int prec, const TransformPlan& px, int rows,
                                 int P, int mode, int nf, const void* gz, double* grid_in,
                                 double* grid_out, int nterms, const int32_t* t_eq,
                                 const double* t_coef, const int32_t* t_fa, const int32_t* t_fb,
-                                int ne, void* h, const float* t_coef32 = nullptr);
+                                int ne, void* h, const float* t_coef32 = nullptr, int xscale = 0);
 cudaError_t launch_cheb_forward(cudaStream_t s, int prec, const TransformPlan& pz, int P, int ne,
-                                const void* h, double2* fc);
+                                const void* h, double2* fc, int unweighted = 0);
+cudaError_t launch_fourier_rows_adjoint(cudaStream_t s, int prec, const TransformPlan& px, int rows, int P,
+                                        int nf, const void* gz, int ne, const void* hin, int nterms,
+                                        const int32_t* t_eq, const double* t_coef, const float* t_coef32,
+                                        const int32_t* t_fa, const int32_t* t_fb, void* gzadj);
 size_t z_smem_bytes(int prec, int Ng, int tile);
 size_t x_smem_bytes(int prec, int N, int mode, int nf, int ne);
 cudaError_t launch_cheb_backward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,

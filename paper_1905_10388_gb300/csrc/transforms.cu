@@ -57,7 +57,9 @@ __device__ __forceinline__ void cheb_backward_body(const ZDesc& d, int bx, int f
     if (p >= P || k >= Nc) return mk<T>(0, 0);
     C<T> x = src[(size_t)p * Nc + k];
     if (op == SP_OP_DX) x = mk<T>(-kxT[p] * x.y, kxT[p] * x.x);
-    const T s = ((k & 1) ? (T)-1 : (T)1) * (k == 0 ? (T)1 : (T)0.5);
+    // weighted_in: transpose of the forward transform, c_k (2 - delta_k0) / N_g
+    const T wgt = d.weighted_in ? (k == 0 ? (T)1 : (T)2) / (T)Ng : (T)1;
+    const T s = ((k & 1) ? (T)-1 : (T)1) * (k == 0 ? (T)1 : (T)0.5) * wgt;
     return mk<T>(s * x.x, s * x.y);
   };
   for (int idx = threadIdx.x; idx < TP * Ng; idx += blockDim.x) {
@@ -110,7 +112,9 @@ __device__ __forceinline__ void cheb_forward_body(const ZDesc& d, int bx, int e,
     const C<T> Vr = res[c * Ng + (k == 0 ? 0 : Ng - k)];
     const C<T> w = wq[k];
     const C<T> o = cadd<T>(cmul<T>(w, Vk), cmulc<T>(Vr, w));
-    const T s = ((k & 1) ? (T)-1 : (T)1) * (k == 0 ? inv * (T)0.5 : inv);
+    // out_k = 2 (-1)^k sum_i g_i T_k(x_i): coefficients (2 - delta_k0)/N_g
+    // times that sum; transpose of the backward transform: the sum itself
+    const T s = ((k & 1) ? (T)-1 : (T)1) * (d.unweighted ? (T)0.5 : (k == 0 ? inv * (T)0.5 : inv));
     // the k_x = 0 column is the transform of a real function: its
     // coefficients are real (rounding of the two half-spectrum terms would
     // leave an O(eps) imaginary part)
@@ -145,7 +149,13 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
       const int q = idx / N, k = idx - q * N;
       const int fa = 2 * q, fb = 2 * q + 1;
       auto spec = [&](int f, int kk) -> C<T> {
-        return (f < nf) ? gz[((size_t)f * rows + row) * K + kk] : mk<T>(0, 0);
+        if (f >= nf) return mk<T>(0, 0);
+        C<T> v = gz[((size_t)f * rows + row) * K + kk];
+        if (d.xscale & 1) {            // transpose of forward x: (1/N) with k >= 1 halved
+          const T sc = (kk == 0 ? (T)1 : (T)0.5) / (T)N;
+          v = mk<T>(v.x * sc, v.y * sc);
+        }
+        return v;
       };
       C<T> z;
       if (k == 0) {
@@ -209,9 +219,10 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
     }
     __syncthreads();
     C<T>* res = fft_batched<T>(b0, b1, N, d.radix3, tws, -1, nbo);
-    const T s = (T)1 / (T)(2 * N);
     for (int idx = tid; idx < nbo * K; idx += nt) {
       const int q = idx / K, k = idx - q * K;
+      // forward x: 1/N; transpose of backward x: (2 - delta_k0)
+      const T s = (d.xscale & 2) ? ((k == 0) ? (T)0.5 : (T)1) : (T)1 / (T)(2 * N);
       const C<T> Z = res[(size_t)q * N + k];
       const C<T> Zr = res[(size_t)q * N + (k == 0 ? 0 : N - k)];
       h[((size_t)(2 * q) * rows + row) * K + k] = mk<T>((Z.x + Zr.x) * s, (Z.y - Zr.y) * s);
@@ -223,6 +234,117 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
       const int f = idx / N, i = idx - f * N;
       d.grid_out[((size_t)f * rows + row) * N + i] = (double)OUT[idx];
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the x-row stage for z-row `row`: given the forward fields'
+// spectra gz[f] and the adjoint spectra of the products' forward transform
+// hin[e] (already through the transpose of the z-forward transform), produce
+// the adjoint spectra of the backward x transform of every grid field:
+//   G_f = backward_x(gz_f)                      (forward grid fields)
+//   R_e = (1/N) sum_{k<K} Re(hin_k e^{ikx})      (adjoint of forward x)
+//   Abar_a += c G_b R_e, Abar_b += c G_a R_e     (adjoint of c g_a g_b)
+//   out_k = (2 - delta_k0) sum_i Abar_i e^{-ikx_i}  (adjoint of backward x)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void fourier_rows_adjoint_body(const XDesc& d, int row, unsigned char* smem_raw) {
+  const int N = d.N, K = d.K, rows = d.rows, nf = d.nf, ne = d.ne;
+  const int nbf = (nf + 1) / 2, nbe = (ne + 1) / 2;
+  const int nbmax = max(nbf, nbe);
+  C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* b1 = b0 + (size_t)nbmax * N;
+  C<T>* tws = b1 + (size_t)nbmax * N;
+  T* G = reinterpret_cast<T*>(tws + N);
+  T* R = G + (size_t)nf * N;
+  load_twiddles<T>(tws, reinterpret_cast<const C<T>*>(d.tw), N);
+  const C<T>* gz = reinterpret_cast<const C<T>*>(d.gz);
+  const C<T>* hin = reinterpret_cast<const C<T>*>(d.hin);
+  C<T>* out = reinterpret_cast<C<T>*>(d.gzadj);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // backward x of pairs of spectra from `src` (nfields) into `dst`, with
+  // spectral scale sk(k)
+  auto backward_pairs = [&](const C<T>* src, int nfields, T* dst, bool adjoint_scale) {
+    const int nb = (nfields + 1) / 2;
+    for (int idx = tid; idx < nb * N; idx += nt) {
+      const int q = idx / N, k = idx - q * N;
+      const int fa = 2 * q, fb = 2 * q + 1;
+      auto spec = [&](int f, int kk) -> C<T> {
+        if (f >= nfields) return mk<T>(0, 0);
+        C<T> v = src[((size_t)f * rows + row) * K + kk];
+        if (adjoint_scale) {
+          const T sc = (kk == 0 ? (T)1 : (T)0.5) / (T)N;
+          v = mk<T>(v.x * sc, v.y * sc);
+        }
+        return v;
+      };
+      C<T> z;
+      if (k == 0) {
+        z = mk<T>(spec(fa, 0).x, spec(fb, 0).x);
+      } else if (k < K) {
+        const C<T> A = spec(fa, k), B = spec(fb, k);
+        z = mk<T>(A.x - B.y, A.y + B.x);
+      } else if (k > N - K) {
+        const C<T> A = spec(fa, N - k), B = spec(fb, N - k);
+        z = mk<T>(A.x + B.y, B.x - A.y);
+      } else {
+        z = mk<T>(0, 0);
+      }
+      b0[idx] = z;
+    }
+    __syncthreads();
+    C<T>* res = fft_batched<T>(b0, b1, N, d.radix3, tws, +1, nb);
+    for (int idx = tid; idx < nb * N; idx += nt) {
+      const int q = idx / N, i = idx - q * N;
+      dst[(size_t)(2 * q) * N + i] = res[idx].x;
+      if (2 * q + 1 < nfields) dst[(size_t)(2 * q + 1) * N + i] = res[idx].y;
+    }
+    __syncthreads();
+  };
+  backward_pairs(gz, nf, G, false);
+  backward_pairs(hin, ne, R, true);
+  // adjoint products, pointwise, written over G
+  constexpr int MAX_TERMS = 16, MAX_F = 16;
+  __shared__ T tc[MAX_TERMS];
+  __shared__ int ta[MAX_TERMS], tb[MAX_TERMS], te[MAX_TERMS];
+  const int nterms = min(d.nterms, MAX_TERMS);
+  const T* tcoef = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)d.t_coef : (const void*)d.t_coef32);
+  if (tid < nterms) { tc[tid] = tcoef[tid]; ta[tid] = d.t_fa[tid]; tb[tid] = d.t_fb[tid]; te[tid] = d.t_eq[tid]; }
+  __syncthreads();
+  for (int i = tid; i < N; i += nt) {
+    T g[MAX_F], a[MAX_F];
+#pragma unroll
+    for (int f = 0; f < MAX_F; ++f) { g[f] = (f < nf) ? G[(size_t)f * N + i] : (T)0; a[f] = 0; }
+    for (int t = 0; t < nterms; ++t) {
+      const T r = tc[t] * R[(size_t)te[t] * N + i];
+#pragma unroll
+      for (int f = 0; f < MAX_F; ++f) {
+        if (f == ta[t]) a[f] += r * g[tb[t]];
+        if (f == tb[t]) a[f] += r * g[ta[t]];
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < MAX_F; ++f)
+      if (f < nf) G[(size_t)f * N + i] = a[f];
+  }
+  __syncthreads();
+  // forward x of the adjoint fields, scaled by (2 - delta_k0) N
+  for (int idx = tid; idx < nbf * N; idx += nt) {
+    const int q = idx / N, i = idx - q * N;
+    const T x = G[(size_t)(2 * q) * N + i];
+    const T y = (2 * q + 1 < nf) ? G[(size_t)(2 * q + 1) * N + i] : (T)0;
+    b0[idx] = mk<T>(x, y);
+  }
+  __syncthreads();
+  C<T>* res = fft_batched<T>(b0, b1, N, d.radix3, tws, -1, nbf);
+  for (int idx = tid; idx < nbf * K; idx += nt) {
+    const int q = idx / K, k = idx - q * K;
+    const C<T> Z = res[(size_t)q * N + k];
+    const C<T> Zr = res[(size_t)q * N + (k == 0 ? 0 : N - k)];
+    const T sc = (k == 0) ? (T)0.5 : (T)1;
+    out[((size_t)(2 * q) * rows + row) * K + k] = mk<T>((Z.x + Zr.x) * sc, (Z.y - Zr.y) * sc);
+    if (2 * q + 1 < nf)
+      out[((size_t)(2 * q + 1) * rows + row) * K + k] = mk<T>((Z.y + Zr.y) * sc, (Zr.x - Z.x) * sc);
   }
 }
 
@@ -258,6 +380,11 @@ template <typename T>
 __global__ void __launch_bounds__(X_THREADS) k_fourier_rows(XDesc d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fourier_rows_body<T>(d, blockIdx.x, smem_raw);
+}
+template <typename T>
+__global__ void __launch_bounds__(X_THREADS) k_fourier_rows_adjoint(XDesc d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fourier_rows_adjoint_body<T>(d, blockIdx.x, smem_raw);
 }
 template <typename T>
 __global__ void __launch_bounds__(X_THREADS) k_fourier_rows_batched(const XDesc* __restrict__ ds,
@@ -305,8 +432,9 @@ static int z_tile_for(int P, int nfields) {
 cudaError_t launch_cheb_backward(cudaStream_t s, int prec, const TransformPlan& pz, int P, int nf,
                                  const int32_t* f_var, const int32_t* f_op, const double* kx,
                                  const double2* xc, int xc_field_stride, void* gz, const float* kx32,
-                                 const float2* xc32) {
+                                 const float2* xc32, int weighted_in) {
   ZDesc d{};
+  d.weighted_in = weighted_in;
   d.Nc = pz.Nc; d.Ng = pz.Ng; d.radix3 = pz.radix3; d.P = P;
   d.tw = prec ? pz.tw32 : pz.tw64; d.wq = prec ? pz.dct32 : pz.dct64;
   d.f_var = f_var; d.f_op = f_op; d.kx = kx; d.xc = xc; d.xc_stride = xc_field_stride; d.gz = gz;
@@ -331,8 +459,9 @@ cudaError_t launch_cheb_backward(cudaStream_t s, int prec, const TransformPlan& 
 }
 
 cudaError_t launch_cheb_forward(cudaStream_t s, int prec, const TransformPlan& pz, int P, int ne,
-                                const void* h, double2* fc) {
+                                const void* h, double2* fc, int unweighted) {
   ZDesc d{};
+  d.unweighted = unweighted;
   d.Nc = pz.Nc; d.Ng = pz.Ng; d.radix3 = pz.radix3; d.P = P;
   d.tw = prec ? pz.tw32 : pz.tw64; d.wq = prec ? pz.dct32 : pz.dct64;
   d.h = h; d.fc = fc;
@@ -357,8 +486,9 @@ cudaError_t launch_cheb_forward(cudaStream_t s, int prec, const TransformPlan& p
 cudaError_t launch_fourier_rows(cudaStream_t s, int prec, const TransformPlan& px, int rows, int P, int mode,
                                 int nf, const void* gz, double* grid_in, double* grid_out, int nterms,
                                 const int32_t* t_eq, const double* t_coef, const int32_t* t_fa,
-                                const int32_t* t_fb, int ne, void* h, const float* t_coef32) {
+                                const int32_t* t_fb, int ne, void* h, const float* t_coef32, int xscale) {
   XDesc d{};
+  d.xscale = xscale;
   d.N = px.Ng; d.radix3 = px.radix3; d.rows = rows; d.K = P; d.mode = mode; d.nf = nf;
   d.tw = prec ? px.tw32 : px.tw64;
   d.gz = gz; d.grid_in = grid_in; d.grid_out = grid_out;
@@ -373,6 +503,30 @@ cudaError_t launch_fourier_rows(cudaStream_t s, int prec, const TransformPlan& p
   } else {
     if ((e = set_smem(k_fourier_rows<double>, smem)) != cudaSuccess) return e;
     k_fourier_rows<double><<<rows, X_THREADS, smem, s>>>(d);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fourier_rows_adjoint(cudaStream_t s, int prec, const TransformPlan& px, int rows, int P,
+                                        int nf, const void* gz, int ne, const void* hin, int nterms,
+                                        const int32_t* t_eq, const double* t_coef, const float* t_coef32,
+                                        const int32_t* t_fa, const int32_t* t_fb, void* gzadj) {
+  XDesc d{};
+  d.N = px.Ng; d.radix3 = px.radix3; d.rows = rows; d.K = P; d.mode = 0; d.nf = nf; d.ne = ne;
+  d.tw = prec ? px.tw32 : px.tw64;
+  d.gz = gz; d.hin = hin; d.gzadj = gzadj;
+  d.nterms = nterms; d.t_eq = t_eq; d.t_coef = t_coef; d.t_coef32 = t_coef32; d.t_fa = t_fa; d.t_fb = t_fb;
+  if (nf > 16 || ne > 16 || (prec && nterms > 0 && !t_coef32)) return cudaErrorInvalidValue;
+  const int nbmax = std::max((nf + 1) / 2, (ne + 1) / 2);
+  const size_t esz = prec ? sizeof(float) : sizeof(double);
+  const size_t smem = (2ull * nbmax + 1) * px.Ng * 2 * esz + (size_t)(nf + ne) * px.Ng * esz;
+  cudaError_t e;
+  if (prec) {
+    if ((e = set_smem(k_fourier_rows_adjoint<float>, smem)) != cudaSuccess) return e;
+    k_fourier_rows_adjoint<float><<<rows, X_THREADS, smem, s>>>(d);
+  } else {
+    if ((e = set_smem(k_fourier_rows_adjoint<double>, smem)) != cudaSuccess) return e;
+    k_fourier_rows_adjoint<double><<<rows, X_THREADS, smem, s>>>(d);
   }
   return cudaGetLastError();
 }

@@ -13,18 +13,30 @@ def field_errors(got, ref, names):
     return {v: rel_err(got[i], ref[i]) for i, v in enumerate(names)}
 
 
+# Oracle variants whose spread estimates the rounding floor of each field:
+# (Chebyshev summation, pencil factorization) other than the reference's
+# ("mmt", "auto").  The solve dominates the spread of fields such as bz,
+# whose relative error is set by the conditioning of the pencil matrices.
+FLOOR_VARIANTS = (("dct", "natural"), ("mmt", "natural"), ("dct", "auto"))
+
+
 def oracle_floor(make_system, X0_fn, step_fn, nsteps):
-    """Run the oracle twice (Chebyshev quadrature vs DCT summation) and return
-    (reference, per-field rounding floor)."""
-    out = []
-    for method in ("mmt", "dct"):
-        sysr = make_system(method)
+    """Run the oracle (reference) and its FLOOR_VARIANTS; return (reference,
+    per-field rounding floor = largest deviation of a variant)."""
+    def run(cheb, lu):
+        sysr = make_system(cheb, lu)
         X = X0_fn(sysr)
         st = step_fn(sysr)
         for _ in range(nsteps):
             X = st.step(X, st.dt)
-        out.append(X)
-    return out[0], field_errors(out[1], out[0], NAMES)
+        return X
+
+    ref = run("mmt", "auto")
+    floor = dict.fromkeys(NAMES, 0.0)
+    for cheb, lu in FLOOR_VARIANTS:
+        for k, v in field_errors(run(cheb, lu), ref, NAMES).items():
+            floor[k] = max(floor[k], v)
+    return ref, floor
 
 
 def check_fields(got, ref, floor, bar):

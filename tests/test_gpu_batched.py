@@ -64,7 +64,7 @@ def test_batch_sample_against_oracle():
             st = _RK(sysr)
             st.dt = dt
             return st
-        ref, floor = oracle_floor(lambda m: orb.RB2D(nx, nz, ra, cheb_method=m),
+        ref, floor = oracle_floor(lambda m, lu: orb.RB2D(nx, nz, ra, cheb_method=m, lu_method=lu),
                                   lambda sysr: sysr.initial_state(si.rb_noise(1000 + i, nz, nx)), stepper, 4)
         check_fields(batch[i].get_state(), ref, floor, 1e-12)
     ctx.close()
