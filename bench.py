@@ -257,6 +257,85 @@ def run_batch(args):
     return res
 
 
+def run_adjoint(args):
+    """Gradient of the final-buoyancy misfit through K RK222 steps (discrete
+    adjoint with checkpoints every 50 steps): forward sweep, adjoint sweep,
+    their time ratio, and the gradient checked against central differences
+    of the FP64 forward loss in a random direction."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1905_10388_gb300.adjoint import RBAdjoint
+    from paper_1905_10388_gb300.solver import Context, RBSolver
+    w = si.WORKLOADS[args.workload]
+    nsteps = args.steps
+    ctx = Context(0, torch.cuda.current_stream(0).cuda_stream)
+    stream = torch.cuda.current_stream(0)
+    xi = si.rb_noise(w.seed, w.n_z, w.n_x)
+    s = RBSolver(ctx, w.n_x, w.n_z, w.Ra, w.Pr, w.L_x, scheme=w.scheme, precision=args.precision)
+    s.factor(w.dt)
+    target = np.zeros((w.n_z, w.n_x))
+    s.set_initial_state(si.rb_noise(w.seed + 1, w.n_z, w.n_x))
+    s.step(nsteps)
+    target = s.get_field("b", "g")                            # b* from the seed + 1 state
+    adj = RBAdjoint(s, xi, target, checkpoint=50)
+    q = np.zeros((w.n_z, w.n_x))
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    for _ in range(max(1, args.warmup // 3)):                   # warm-up: one full gradient
+        J, cps, r = adj.forward(q, nsteps)
+        adj.backward(cps, r, nsteps)
+    s.set_initial_state(xi)
+    _, t_plain = timed(lambda: s.step(nsteps))
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.2)
+    (J, cps, r), t_fwd = timed(lambda: adj.forward(q, nsteps))
+    g, t_bwd = timed(lambda: adj.backward(cps, r, nsteps))
+    clk = clocks.stop()
+    ctx.sync_status()
+
+    # gradient check in FP64: adjoint directional derivative vs central
+    # differences (Richardson-extrapolated) of the forward loss
+    s64 = RBSolver(ctx, w.n_x, w.n_z, w.Ra, w.Pr, w.L_x, scheme=w.scheme, precision="fp64")
+    s64.factor(w.dt)
+    a64 = RBAdjoint(s64, xi, target, checkpoint=50)
+    J64, g64 = a64.loss_and_grad(q, nsteps)
+    g64 = g64.cpu().numpy()
+    d = np.random.default_rng(w.seed + 2).standard_normal(q.shape)
+
+    def central(eps):
+        return (a64.forward(q + eps * d, nsteps)[0] - a64.forward(q - eps * d, nsteps)[0]) / (2 * eps)
+
+    fd = (4 * central(5e-3) - central(1e-2)) / 3
+    an = float(np.sum(g64 * d))
+    gm = g.cpu().numpy()
+    res = {"metric": METRIC, "value": w.dof * nsteps / ((t_fwd + t_bwd) * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "steps": nsteps, "warmup": args.warmup, "ms_per_step": (t_fwd + t_bwd) / nsteps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "data": "synthetic (seeded Rayleigh-Benard initial state; target from seed + 1)",
+           "config": {"workload": args.workload, "n_x": w.n_x, "n_z": w.n_z, "Ra": w.Ra, "scheme": w.scheme,
+                      "dt": w.dt, "dof": w.dof, "precision": args.precision, "checkpoint": 50,
+                      "step": "value counts forward + adjoint sweep of one gradient",
+                      "l2": "working set < L2 (factor ~49 MB)"},
+           "adjoint_over_forward": t_bwd / t_plain,
+           "times_ms": {"forward_plain": t_plain, "forward_with_checkpoints": t_fwd, "adjoint_sweep": t_bwd},
+           "gradient_check": {"fd": fd, "adjoint": an, "rel_err": abs(fd - an) / abs(fd),
+                              "precision": "fp64", "mixed_vs_fp64_rel": float(
+                                  np.linalg.norm(gm - g64) / np.linalg.norm(g64)), "loss": J64},
+           "roofline": None, "clocks": clk}
+    ctx.close()
+    return res
+
+
 def oracle_rate(workload, steps_timed, warm):
     """The FP64 CPU oracle on the same workload: returns (DOF*steps/s, seconds)."""
     from oracle import rb as orb
@@ -301,19 +380,23 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None, help="default 200 (500 for the adjoint workload)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 500 if args.workload.endswith("_adjoint") else 200
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         res = run_reference(args)
     elif args.workload == "rb2d_batch64_rk222":
         res = run_batch(args)
+    elif args.workload.endswith("_adjoint"):
+        res = run_adjoint(args)
     else:
         res = run_ours(args)
         if res is not None and not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:

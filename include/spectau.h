@@ -197,21 +197,29 @@ sp_status sp_batch_tile(sp_ctx* ctx, int nproblems, const int* problem_ids, int*
  * sp_adjoint_init: after sp_factor, factors the transposed pencils
  *   A~^T = M~^T + dt H_ii L~^T (banded LU with partial pivoting, FP64) and
  *   allocates the adjoint work buffers.
- * sp_step_adjoint: given the state X^n at the start of a step (x_start_dev,
- *   device, S*P*N_z complex) and lambda = dJ/dX^{n+1} (lambda_dev, device,
- *   same layout), overwrites lambda with dJ/dX^n.  It recomputes the first
- *   stage from X^n, solves the transposed stage systems and applies the
- *   transposes of the dealiased transforms and products (in the problem's
- *   transform precision).  The problem's state buffers are used as scratch:
- *   set the state again before stepping forward.  dt must be the factored
- *   dt.
+ * sp_step_adjoint: given the states of one forward step (states_dev,
+ *   device, nstates consecutive arrays of S*P*N_z complex: X^n alone
+ *   (nstates = 1; the first stage is then recomputed from X^n) or X^n
+ *   followed by the stage states as sp_step_record writes them (nstates =
+ *   number of stages)) and lambda = dJ/dX^{n+1} (lambda_dev, device, one
+ *   state), overwrites lambda with dJ/dX^n.  It solves the transposed stage
+ *   systems and applies the transposes of the dealiased transforms and
+ *   products (in the problem's transform precision).  The problem's state
+ *   buffers are used as scratch: set the state again before stepping
+ *   forward.  dt must be the factored dt; other nstates give SP_ERR_ARG.
+ * sp_step_record: nsteps forward steps exactly as sp_step, also writing,
+ *   for step k, X^{n+k} and its stage states (RK222: X^{n+k} and X^1; RK111:
+ *   X^{n+k}) to states_dev + k * (number of stages) * S*P*N_z complex
+ *   (device, caller-owned), the input of sp_step_adjoint.  Asynchronous.
  * sp_transform_adjoint: transpose of sp_transform (direction -1: grid
  *   adjoint in, coefficient adjoint out; +1: coefficient adjoint in, grid
  *   adjoint out), FP64.
  * sp_dz_adjoint: src_bar += D^T dst_bar for the Chebyshev derivative of
  *   sp_dz (device arrays of P*N_z complex). */
 sp_status sp_adjoint_init(sp_ctx* ctx, int problem);
-sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* x_start_dev, void* lambda_dev);
+sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* states_dev, int nstates,
+                          void* lambda_dev);
+sp_status sp_step_record(sp_ctx* ctx, int problem, double dt, int nsteps, void* states_dev);
 sp_status sp_transform_adjoint(sp_ctx* ctx, int problem, const void* in, void* out, int nfields,
                                int direction, int scale_num, int scale_den, int on_device);
 sp_status sp_dz_adjoint(sp_ctx* ctx, int problem, const void* dst_bar_dev, void* src_bar_dev);

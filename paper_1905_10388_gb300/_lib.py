@@ -28,7 +28,7 @@ EXPORTS = (
     "sp_dz", "sp_step", "sp_step_graph", "sp_sync_status", "sp_transform", "sp_eval_rhs",
     "sp_get_band", "sp_set_timing", "sp_last_solve_time", "sp_transform_backward_static",
     "sp_step_batched", "sp_batch_tile", "sp_adjoint_init", "sp_step_adjoint", "sp_transform_adjoint",
-    "sp_dz_adjoint",
+    "sp_dz_adjoint", "sp_step_record",
 )
 
 
@@ -76,7 +76,8 @@ _SIGS = {
     "sp_step_batched": [P, I, ctypes.POINTER(I), F64P, I, I],
     "sp_batch_tile": [P, I, ctypes.POINTER(I), ctypes.POINTER(I)],
     "sp_adjoint_init": [P, I],
-    "sp_step_adjoint": [P, I, D, P, P],
+    "sp_step_adjoint": [P, I, D, P, I, P],
+    "sp_step_record": [P, I, D, I, P],
     "sp_transform_adjoint": [P, I, P, P, I, I, I, I, I],
     "sp_dz_adjoint": [P, I, P, P],
 }

@@ -4,8 +4,9 @@ Workload: J = 1/2 sum over the scale-1 grid of (b(T) - b_target)^2, control q
 on the scale-1 grid entering the initial buoyancy as
 b0 = 1 - z + (A xi + q) z (1 - z), bz0 = dz b0.  The forward sweep stores a
 checkpoint of the state every ``checkpoint`` steps; the backward sweep
-replays each segment from its checkpoint (storing the segment's states on
-the device) and runs the adjoint steps in reverse (``sp_step_adjoint``).
+replays each segment from its checkpoint, recording every step's start and
+stage states on the device (``sp_step_record``), and runs the adjoint steps
+in reverse from those records (``sp_step_adjoint``).
 Everything numeric runs in the library's kernels; torch holds device buffers
 and the loss.
 """
@@ -61,10 +62,9 @@ class RBAdjoint:
         s = self.s
         self._set_initial(q)
         checkpoints = []
-        for n in range(nsteps):
-            if n % self.K == 0:
-                checkpoints.append(self._get_state())
-            s.step(1)
+        for n0 in range(0, nsteps, self.K):
+            checkpoints.append(self._get_state())
+            s.step(min(self.K, nsteps - n0))
         h = s.ctx.handle
         b = torch.empty((s.Nz, s.Nx), dtype=torch.float64, device="cuda")
         L.check(h, L.lib().sp_get_field(h, s.pid, s.var["b"], ctypes.c_void_p(b.data_ptr()), 1, b"g"))
@@ -78,23 +78,22 @@ class RBAdjoint:
         h = s.ctx.handle
         lam = torch.zeros(self.shape, dtype=torch.complex128, device="cuda")
         rb = r.contiguous()
-        # transpose of the scale-1 backward transform of b
+        # transpose of the scale-1 backward transform of b (lam is indexed by
+        # the solver's variable slots)
         L.check(h, L.lib().sp_transform_adjoint(h, s.pid, ctypes.c_void_p(rb.data_ptr()),
                                                 ctypes.c_void_p(lam[s.var["b"]].data_ptr()), 1, -1, 1, 1, 1))
-        # NB: lam is indexed by the solver's variable slots
-        nseg = len(checkpoints)
-        for seg in reversed(range(nseg)):
+        ns = 2 if s.scheme == "RK222" else 1                  # recorded states per step
+        rec = torch.empty((min(self.K, max(nsteps, 1)), ns) + self.shape, dtype=torch.complex128, device="cuda")
+        per_step = ns * int(np.prod(self.shape)) * 16
+        for seg in reversed(range(len(checkpoints))):
             n0 = seg * self.K
-            n1 = min(nsteps, n0 + self.K)
+            m = min(nsteps, n0 + self.K) - n0
+            # replay the segment from its checkpoint, recording each step's states
             self._set_state(checkpoints[seg])
-            states = []
-            for n in range(n0, n1):
-                states.append(self._get_state())
-                if n + 1 < n1:
-                    s.step(1)
-            for X in reversed(states):
-                L.check(h, L.lib().sp_step_adjoint(h, s.pid, s.dt, ctypes.c_void_p(X.data_ptr()),
-                                                   ctypes.c_void_p(lam.data_ptr())))
+            L.check(h, L.lib().sp_step_record(h, s.pid, s.dt, m, ctypes.c_void_p(rec.data_ptr())))
+            for k in reversed(range(m)):
+                L.check(h, L.lib().sp_step_adjoint(h, s.pid, s.dt, ctypes.c_void_p(rec.data_ptr() + k * per_step),
+                                                   ns, ctypes.c_void_p(lam.data_ptr())))
         # initial-state map: b coefficients from the grid, bz = dz b
         cb = lam[s.var["b"]].clone()
         L.check(h, L.lib().sp_dz_adjoint(h, s.pid, ctypes.c_void_p(lam[s.var["bz"]].data_ptr()),

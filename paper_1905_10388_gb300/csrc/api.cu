@@ -123,7 +123,7 @@ struct Problem {
   int32_t *d_indptrT = nullptr, *d_indicesT = nullptr;
   double *d_MvT = nullptr, *d_LvT = nullptr;
   double2 *d_mu[2] = {nullptr, nullptr}, *d_LTmu = nullptr, *d_MTmu = nullptr, *d_JF = nullptr, *d_lamx = nullptr;
-  double2 *d_X0save = nullptr, *d_Xbar = nullptr, *d_Fbar = nullptr;
+  double2 *d_Xbar = nullptr, *d_Fbar = nullptr;
   float2* d_Fbar32 = nullptr;
   void* d_gzadj = nullptr;
   // graphs
@@ -334,7 +334,7 @@ void free_problem(Problem* pr) {
   F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd);
   F(pr->d_indptrT); F(pr->d_indicesT); F(pr->d_MvT); F(pr->d_LvT);
   F(pr->d_mu[0]); F(pr->d_mu[1]); F(pr->d_LTmu); F(pr->d_MTmu); F(pr->d_JF); F(pr->d_lamx);
-  F(pr->d_X0save); F(pr->d_Xbar); F(pr->d_Fbar); F(pr->d_Fbar32); F(pr->d_gzadj);
+  F(pr->d_Xbar); F(pr->d_Fbar); F(pr->d_Fbar32); F(pr->d_gzadj);
   for (auto& kv : pr->plans) { F(kv.second.tw64); F(kv.second.tw32); F(kv.second.dct64); F(kv.second.dct32); }
   for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
   for (auto e : pr->ev) cudaEventDestroy(e);
@@ -540,20 +540,22 @@ SolveArgs transposed_args(Problem* pr, sp_ctx* ctx) {
 }
 
 // out = J_F(X)^H (sum_k c_k vecs_k) + sum_a w_a adds_a in solve variables,
-// X the T coefficients currently in d_Xc (Sec. "Runge-Kutta IMEX
-// integrators": transpose of the right-hand side of a stage).
-sp_status adjoint_rhs(sp_ctx* ctx, Problem* pr, cudaStream_t s, int nv, const double2* const* vecs,
-                      const double* coefs, int na, const double2* const* adds, const double* wts, double2* out) {
+// X the T coefficients xc ([v][p][m], device) (Sec. "Runge-Kutta IMEX
+// integrators": transpose of the right-hand side of a stage).  In mixed
+// precision the FP32 copy of X is rebuilt in d_Xc32.
+sp_status adjoint_rhs(sp_ctx* ctx, Problem* pr, cudaStream_t s, const double2* xc, int nv,
+                      const double2* const* vecs, const double* coefs, int na, const double2* const* adds,
+                      const double* wts, double2* out) {
   TransformPlan& pz = pr->plans.at({pr->Nz, pr->Ngz});
   TransformPlan& px = pr->plans.at({pr->Nx, pr->Ngx});
   const int nf = (int)pr->gfields.size(), ne = (int)pr->nl_eqs.size();
-  if (pr->prec && !pr->xc32_valid) {
-    CK(launch_to_f32(s, pr->d_Xc, pr->d_Xc32, (size_t)pr->S * pr->P * pr->Nz));
-    pr->xc32_valid = true;
+  if (pr->prec) {
+    CK(launch_to_f32(s, xc, pr->d_Xc32, (size_t)pr->S * pr->P * pr->Nz));
+    pr->xc32_valid = (xc == pr->d_Xc);
   }
   CK(launch_adj_gather(s, pr->P, pr->Nz, pr->Ngz, pr->n, ne, pr->d_nl_eq, pr->d_row_map, pr->d_eq_diff,
                        pr->d_eq_ph, nv, vecs, coefs, pr->d_Fbar, pr->prec ? pr->d_Fbar32 : nullptr));
-  CK(launch_cheb_backward(s, pr->prec, pz, pr->P, nf, pr->d_gvar, pr->d_gop, pr->d_kx, pr->d_Xc, pr->P * pr->Nz,
+  CK(launch_cheb_backward(s, pr->prec, pz, pr->P, nf, pr->d_gvar, pr->d_gop, pr->d_kx, xc, pr->P * pr->Nz,
                           pr->d_gz, pr->d_kx32, pr->d_Xc32));
   CK(launch_cheb_backward(s, pr->prec, pz, pr->P, ne, pr->d_ident, pr->d_zero, pr->d_kx, pr->d_Fbar,
                           pr->P * pr->Nz, pr->d_h, pr->d_kx32, pr->d_Fbar32));
@@ -1262,7 +1264,6 @@ sp_status sp_adjoint_init(sp_ctx* ctx, int problem) {
     CK(dalloc(&pr->d_MTmu, nvec));
     CK(dalloc(&pr->d_JF, nvec));
     CK(dalloc(&pr->d_lamx, nvec));
-    CK(dalloc(&pr->d_X0save, nvec));
     const int nf = (int)pr->gfields.size(), ne = (int)pr->nl_eqs.size();
     CK(dalloc(&pr->d_Xbar, (size_t)nf * pr->P * pr->Nz));
     CK(dalloc(&pr->d_Fbar, (size_t)ne * pr->P * pr->Nz));
@@ -1285,7 +1286,8 @@ sp_status sp_adjoint_init(sp_ctx* ctx, int problem) {
   return SP_OK;
 }
 
-sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* x_start_dev, void* lambda_dev) {
+sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* states_dev, int nstates,
+                          void* lambda_dev) {
   Problem* pr = get(ctx, problem);
   if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
   ctx->err.clear();
@@ -1293,31 +1295,37 @@ sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* x_sta
     return fail(ctx, SP_ERR_STATE, "sp_adjoint_init must follow the last sp_factor");
   if (!pr->factored || dt != pr->fac_dt)
     return fail(ctx, SP_ERR_NOT_FACTORED, "dt = %.17g is not the factored step size", dt);
-  if (!x_start_dev || !lambda_dev) return fail(ctx, SP_ERR_ARG, "null pointer");
+  if (!states_dev || !lambda_dev) return fail(ctx, SP_ERR_ARG, "null pointer");
+  const Tableau tb = make_tableau(pr->scheme);
+  if (nstates != 1 && nstates != tb.s)
+    return fail(ctx, SP_ERR_ARG, "nstates = %d: expected 1 or the number of stages %d", nstates, tb.s);
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = ctx->stream;
   sp_status st;
-  const Tableau tb = make_tableau(pr->scheme);
   const size_t ncoef = (size_t)pr->S * pr->P * pr->Nz;
-  // forward recomputation of the first stage from X^n (the state buffers of
-  // the problem are used as scratch)
-  CK(cudaMemcpyAsync(pr->d_X0save, x_start_dev, ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(pr->d_Xc, x_start_dev, ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  const double2* X0 = reinterpret_cast<const double2*>(states_dev);
+  const double2* X1 = nullptr;                        // stage-1 state (two-stage scheme)
+  // the problem's state buffers are scratch from here on
   pr->xt_valid = false;
   pr->xc32_valid = false;
   pr->mx_valid = false;
   pr->iteration = 0;
-  if ((st = ensure_solve_vars(ctx, pr, s)) != SP_OK) return st;
-  if (tb.s == 2) {
+  if (tb.s == 2 && nstates == 2) {
+    X1 = X0 + ncoef;
+  } else if (tb.s == 2) {
+    // forward recomputation of the first stage from X^n
+    CK(cudaMemcpyAsync(pr->d_Xc, X0, ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    if ((st = ensure_solve_vars(ctx, pr, s)) != SP_OK) return st;
     if ((st = eval_rhs(ctx, pr, s, pr->d_Fc[0])) != SP_OK) return st;
     SolveArgs a = base_args(pr, ctx, 0);
     a.mv_x = pr->d_Xt; a.mv_coef = 1.0; a.mv_store = nullptr;
     set_mv_M(pr, a);
     a.fc[0] = pr->d_Fc[0]; a.fc_coef[0] = dt * tb.A[1][0]; a.nfc = 1;
     a.bc_coef = dt * tb.A[1][0];
-    a.xc_out = pr->d_Xc;                                   // X^1
+    a.xc_out = pr->d_Xc;
+    a.xc32_out = nullptr;
     if ((st = solve(ctx, pr, s, a)) != SP_OK) return st;
-    pr->xc32_valid = (pr->prec != 0);
+    X1 = pr->d_Xc;
   }
   // lambda^s in solve variables: T^H lambda_X
   {
@@ -1327,27 +1335,23 @@ sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* x_sta
                           reinterpret_cast<const double2*>(lambda_dev), pr->d_col_map, pr->d_var_rec, pr->d_var_ph,
                           0, none, w0, pr->d_lamx));
   }
-  // stage s: mu_s = A~^-T lambda^s ; keep L~^T mu_s
+  // stage s: mu_s = A~^-T lambda^s ; keep L~^T mu_s (two stages) or M~^T mu_s
   {
     SolveArgs t = transposed_args(pr, ctx);
     t.vec[0] = pr->d_lamx; t.vec_coef[0] = 1.0; t.nvec = 1;
     t.xt_out = pr->d_mu[tb.s - 1];
-    if (tb.s == 2) {
-      t.ep_mv_vals = pr->d_LvT; t.ep_indptr = pr->d_indptrT; t.ep_indices = pr->d_indicesT;
-      t.ep_nnz = (int)pr->nnz; t.ep_mv_store = pr->d_LTmu;
-    } else {
-      t.ep_mv_vals = pr->d_MvT; t.ep_indptr = pr->d_indptrT; t.ep_indices = pr->d_indicesT;
-      t.ep_nnz = (int)pr->nnz; t.ep_mv_store = pr->d_MTmu;
-    }
+    t.ep_mv_vals = tb.s == 2 ? pr->d_LvT : pr->d_MvT;
+    t.ep_indptr = pr->d_indptrT; t.ep_indices = pr->d_indicesT; t.ep_nnz = (int)pr->nnz;
+    t.ep_mv_store = tb.s == 2 ? pr->d_LTmu : pr->d_MTmu;
     if ((st = solve(ctx, pr, s, t)) != SP_OK) return st;
   }
   if (tb.s == 2) {
-    // lambda^1 = dt A21 J_F(X^1)^H mu_2 - dt H21 L~^T mu_2 (X^1 is in d_Xc)
+    // lambda^1 = dt A21 J_F(X^1)^H mu_2 - dt H21 L~^T mu_2
     const double2* v[1] = {pr->d_mu[1]};
     const double c[1] = {dt * tb.A[2][1]};
     const double2* ad[1] = {pr->d_LTmu};
     const double w[1] = {-dt * tb.H[2][1]};
-    if ((st = adjoint_rhs(ctx, pr, s, 1, v, c, 1, ad, w, pr->d_JF)) != SP_OK) return st;
+    if ((st = adjoint_rhs(ctx, pr, s, X1, 1, v, c, 1, ad, w, pr->d_JF)) != SP_OK) return st;
     // mu_1 = A~^-T lambda^1 ; M~^T (mu_1 + mu_2)
     SolveArgs t = transposed_args(pr, ctx);
     t.vec[0] = pr->d_JF; t.vec_coef[0] = 1.0; t.nvec = 1;
@@ -1357,8 +1361,6 @@ sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* x_sta
     if ((st = solve(ctx, pr, s, t)) != SP_OK) return st;
   }
   // lambda^0 = M~^T sum_k mu_k + dt J_F(X^0)^H sum_k A_k0 mu_k
-  CK(cudaMemcpyAsync(pr->d_Xc, pr->d_X0save, ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, s));
-  pr->xc32_valid = false;
   {
     const double2* v[2];
     double c[2];
@@ -1366,14 +1368,41 @@ sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* x_sta
     for (int k = 1; k <= tb.s; ++k) { v[nv] = pr->d_mu[k - 1]; c[nv++] = dt * tb.A[k][0]; }
     const double2* ad[1] = {pr->d_MTmu};
     const double w[1] = {1.0};
-    if ((st = adjoint_rhs(ctx, pr, s, nv, v, c, 1, ad, w, pr->d_lamx)) != SP_OK) return st;
+    if ((st = adjoint_rhs(ctx, pr, s, X0, nv, v, c, 1, ad, w, pr->d_lamx)) != SP_OK) return st;
   }
   CK(launch_adj_tinvh(s, pr->P, pr->Nz, pr->S, pr->n, pr->d_lamx, pr->d_col_map, pr->d_var_rec, pr->d_var_ph,
                       reinterpret_cast<double2*>(lambda_dev)));
-  // the problem's state buffers were scratch: the next forward step needs a state
-  pr->xt_valid = false;
-  pr->mx_valid = false;
-  pr->xc32_valid = false;
+  return SP_OK;
+}
+
+sp_status sp_step_record(sp_ctx* ctx, int problem, double dt, int nsteps, void* states_dev) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (pr->scheme != SP_RK222 && pr->scheme != SP_RK111)
+    return fail(ctx, SP_ERR_ARG, "sp_step_record is provided for the RK222 and RK111 schemes");
+  if (nsteps < 0) return fail(ctx, SP_ERR_ARG, "nsteps < 0");
+  if (!states_dev && nsteps > 0) return fail(ctx, SP_ERR_ARG, "null pointer");
+  if (!pr->factored || dt != pr->fac_dt)
+    return fail(ctx, SP_ERR_NOT_FACTORED, "dt = %.17g is not the factored step size", dt);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  sp_status st;
+  const size_t ncoef = (size_t)pr->S * pr->P * pr->Nz;
+  double2* rec = reinterpret_cast<double2*>(states_dev);
+  for (int k = 0; k < nsteps; ++k) {
+    if ((st = ensure_solve_vars(ctx, pr, s)) != SP_OK) return st;
+    const std::vector<StagePlan> plan = plan_step(ctx, pr, dt);
+    const size_t ns = plan.size();
+    for (size_t i = 0; i < ns; ++i) {
+      // X^n before the first stage, X^i after stage i < s
+      CK(cudaMemcpyAsync(rec + ((size_t)k * ns + i) * ncoef, pr->d_Xc, ncoef * sizeof(double2),
+                         cudaMemcpyDeviceToDevice, s));
+      if ((st = eval_rhs(ctx, pr, s, plan[i].fc_out)) != SP_OK) return st;
+      if ((st = solve(ctx, pr, s, plan[i].args)) != SP_OK) return st;
+    }
+    commit_step(pr);
+  }
   return SP_OK;
 }
 

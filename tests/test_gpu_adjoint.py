@@ -101,18 +101,21 @@ def test_step_adjoint_against_gpu_forward_differences():
     Xd = torch.as_tensor(_to_slots(s, X0), device="cuda").contiguous()
     Ld = torch.as_tensor(_to_slots(s, lam), device="cuda").contiguous()
     h = ctx.handle
-    _lib.check(h, _lib.lib().sp_step_adjoint(h, s.pid, DT, Xd.data_ptr(), Ld.data_ptr()))
+    _lib.check(h, _lib.lib().sp_step_adjoint(h, s.pid, DT, Xd.data_ptr(), 1, Ld.data_ptr()))
     ctx.sync_status()
     an = _ip(_from_slots(s, Ld.cpu().numpy()), V)
     assert abs(fd - an) < 1e-8 * abs(fd), (fd, an)
     ctx.close()
 
 
-def test_step_adjoint_matches_oracle():
+@pytest.mark.parametrize("given_stage", [False, True])
+def test_step_adjoint_matches_oracle(given_stage):
+    """One adjoint step against the oracle, with the first stage recomputed
+    from X^n (nstates = 1) or supplied (nstates = 2, the oracle's X^1)."""
     ctx = Context(0)
     s = RBSolver(ctx, NX, NZ, RA, scheme="RK222")
     s.factor(DT)
-    adj = RBAdjoint(s, si.rb_noise(1, NZ, NX), np.zeros((NZ, NX)))
+    RBAdjoint(s, si.rb_noise(1, NZ, NX), np.zeros((NZ, NX)))
     sysr = orb.RB2D(NX, NZ, RA)
     oadj = OracleAdjoint(sysr)
     X0 = oadj.initial_state_q(si.rb_noise(2, NZ, NX) * 50.0, 0.0)
@@ -123,14 +126,40 @@ def test_step_adjoint_matches_oracle():
     lam = rng.standard_normal(X0.shape) + 1j * rng.standard_normal(X0.shape)
     X1 = oadj.stage1(X0, DT)
     ref = oadj.step_adjoint(X0, X1, lam, DT)
-    Xd = torch.as_tensor(_to_slots(s, X0), device="cuda").contiguous()
+    states = [_to_slots(s, X0)] + ([_to_slots(s, X1)] if given_stage else [])
+    Xd = torch.as_tensor(np.stack(states), device="cuda").contiguous()
     Ld = torch.as_tensor(_to_slots(s, lam), device="cuda").contiguous()
     h = ctx.handle
-    _lib.check(h, _lib.lib().sp_step_adjoint(h, s.pid, DT, Xd.data_ptr(), Ld.data_ptr()))
+    _lib.check(h, _lib.lib().sp_step_adjoint(h, s.pid, DT, Xd.data_ptr(), len(states), Ld.data_ptr()))
     ctx.sync_status()
     got = _from_slots(s, Ld.cpu().numpy())
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err < 1e-10, err
+    with pytest.raises(_lib.SpectauError):
+        _lib.check(h, _lib.lib().sp_step_adjoint(h, s.pid, DT, Xd.data_ptr(), 3, Ld.data_ptr()))
+    ctx.close()
+
+
+def test_step_record_states():
+    """sp_step_record advances like sp_step and records X^n and the stage
+    state X^1 of every step (checked against the oracle's stage state)."""
+    ctx = Context(0)
+    a = RBSolver(ctx, NX, NZ, RA, scheme="RK222")
+    b = RBSolver(ctx, NX, NZ, RA, scheme="RK222")
+    for s in (a, b):
+        s.factor(DT)
+        s.set_initial_state(si.rb_noise(8, NZ, NX) * 50.0)
+    a.step(3)
+    rec = torch.zeros((3, 2, a.S, a.P, a.Nz), dtype=torch.complex128, device="cuda")
+    h = ctx.handle
+    _lib.check(h, _lib.lib().sp_step_record(h, b.pid, DT, 3, rec.data_ptr()))
+    assert np.array_equal(a.get_state(), b.get_state())
+    rec = rec.cpu().numpy()
+    oadj = OracleAdjoint(orb.RB2D(NX, NZ, RA))
+    for k in range(3):
+        Xn, X1 = _from_slots(b, rec[k, 0]), _from_slots(b, rec[k, 1])
+        ref = oadj.stage1(Xn, DT)
+        assert np.linalg.norm(X1 - ref) < 1e-12 * np.linalg.norm(ref)
     ctx.close()
 
 
