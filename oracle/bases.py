@@ -70,6 +70,44 @@ def fourier_backward(f, n_grid, axis=-1):
     return np.moveaxis(g, -1, axis)
 
 
+def fourier_c_modes(n_coeff):
+    """Signed mode numbers of the N_c stored slots of a complex Fourier axis,
+    in FFT order: slot s holds n = s for s < N_c/2 and n = s - N_c above;
+    the Nyquist slot s = N_c/2 is kept at zero (Sec. "Fourier basis")."""
+    s = np.arange(n_coeff)
+    return np.where(s < n_coeff // 2, s, s - n_coeff)
+
+
+def fourier_c_wavenumbers(n_coeff, length):
+    """Physical wavenumbers 2 pi n / L of the stored slots of a complex axis."""
+    return 2.0 * np.pi * fourier_c_modes(n_coeff) / length
+
+
+def fourier_c_forward(g, n_coeff, axis=-1):
+    """Complex grid values on N_g points -> N_c complex amplitudes in FFT order,
+    f_n = (1/N_g) sum_i g(y_i) exp(-i n y_i) for |n| < N_c/2; Nyquist slot zero."""
+    g = np.moveaxis(np.asarray(g, dtype=np.complex128), axis, -1)
+    n_grid = g.shape[-1]
+    full = np.fft.fft(g, axis=-1) / n_grid
+    n = fourier_c_modes(n_coeff)
+    f = full[..., n % n_grid]
+    f[..., n_coeff // 2] = 0.0
+    return np.moveaxis(f, -1, axis)
+
+
+def fourier_c_backward(f, n_grid, axis=-1):
+    """N_c amplitudes in FFT order -> complex grid values on N_g >= N_c points,
+    g(y_i) = sum_{|n| < N_c/2} f_n exp(i n y_i) (Nyquist slot ignored)."""
+    f = np.moveaxis(np.asarray(f, dtype=np.complex128), axis, -1)
+    n_coeff = f.shape[-1]
+    n = fourier_c_modes(n_coeff)
+    keep = np.arange(n_coeff) != n_coeff // 2
+    full = np.zeros(f.shape[:-1] + (n_grid,), dtype=np.complex128)
+    full[..., n[keep] % n_grid] = f[..., keep]
+    g = np.fft.ifft(full, axis=-1) * n_grid
+    return np.moveaxis(g, -1, axis)
+
+
 # ----------------------------------------------------------------------------
 # Chebyshev
 # ----------------------------------------------------------------------------

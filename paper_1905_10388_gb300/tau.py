@@ -43,7 +43,7 @@ def _as_fn(c):
 class Term:
     var: str
     op: str            # "I" or "dz"
-    coef: object       # number or function of k_x
+    coef: object       # number or function of the wavenumber(s) (evaluated on arrays)
 
 
 @dataclass
@@ -63,7 +63,7 @@ class BCAlternative:
     var: str
     side: str          # "left" (z = a) or "right" (z = b)
     value: object = 0.0
-    condition: Optional[Callable[[float], bool]] = None
+    condition: Optional[Callable] = None    # wavenumber arrays -> boolean array
     phase: int = 0
 
 
@@ -71,12 +71,6 @@ class BCAlternative:
 class BCSlot:
     """One boundary row; exactly one alternative applies to each pencil."""
     alternatives: List[BCAlternative]
-
-    def pick(self, kx):
-        hits = [a for a in self.alternatives if a.condition is None or a.condition(kx)]
-        if len(hits) != 1:
-            raise ValueError(f"boundary slot needs exactly one alternative at k_x={kx}")
-        return hits[0]
 
 
 # --- 1D operator entries on N Chebyshev modes (native interval [-1, 1]) ------
@@ -206,13 +200,20 @@ class PencilProblem:
     def _phase(self, q):
         return 1j ** (q % 4)
 
-    def build(self, N, kx_list):
+    def build(self, N, wavenumbers, values=True):
         """Assemble every pencil on a shared (union) CSR pattern.
 
-        Returns a dict with indptr, indices, M [P, nnz], L [P, nnz] (real),
-        bc_values [P, nbc] complex, the layout tables and the band widths.
+        ``wavenumbers`` gives one entry per pencil: an array of k_x (one
+        Fourier axis) or a tuple of arrays (k_x, k_y) (two Fourier axes);
+        coefficient functions, boundary values and conditions are evaluated
+        on those arrays.  Returns a dict with indptr, indices, the layout
+        tables, the band widths, bc_values [P, nbc] complex and a function
+        ``values(p0, p1)`` -> (M, L) real [p1 - p0, nnz] for a range of
+        pencils (and, when ``values`` is true, M and L for all pencils).
         """
-        kx_list = np.asarray(kx_list, dtype=np.float64)
+        k = tuple(np.asarray(a, dtype=np.float64) for a in wavenumbers) if isinstance(wavenumbers, tuple) \
+            else np.asarray(wavenumbers, dtype=np.float64)
+        P = len(k[0]) if isinstance(k, tuple) else len(k)
         S, n = self.S, self.S * N
         ents = self.pattern(N)
         rows = np.array([e[0] for e in ents], dtype=np.int64)
@@ -225,56 +226,67 @@ class PencilProblem:
         np.add.at(indptr, urow + 1, 1)
         indptr = np.cumsum(indptr).astype(np.int32)
         indices = ucol.astype(np.int32)
-        P = len(kx_list)
         nbc = len(self.bc_slots)
         vq = {v: self.var_phase.get(v, 0) for v in self.variables}
+
+        def per_pencil(c, dtype=np.complex128):
+            return np.broadcast_to(np.asarray(_as_fn(c)(k), dtype=dtype), (P,))
+
+        # the boundary alternative that applies to each pencil
+        active = np.zeros((nbc, P), dtype=np.int64)
+        for si, slot in enumerate(self.bc_slots):
+            hits = np.stack([np.ones(P, bool) if a.condition is None else per_pencil(a.condition, bool)
+                             for a in slot.alternatives])
+            if not np.all(hits.sum(axis=0) == 1):
+                raise ValueError(f"boundary slot {si} needs exactly one alternative on every pencil")
+            active[si] = np.argmax(hits, axis=0)
         # every entry belongs to one term (or one boundary alternative); its
         # value on pencil p is scale[term, p] * base value
-        keys = []
-        key_index = {}
+        keys, key_index = [], {}
         ent_key = np.empty(len(ents), dtype=np.int64)
         for t, e in enumerate(ents):
-            k = e[3]
-            if k not in key_index:
-                key_index[k] = len(keys)
-                keys.append(k)
-            ent_key[t] = key_index[k]
+            kk = e[3]
+            if kk not in key_index:
+                key_index[kk] = len(keys)
+                keys.append(kk)
+            ent_key[t] = key_index[kk]
         base = np.array([e[4] for e in ents], dtype=np.float64)
         is_M = np.array([e[2] == "M" for e in ents])
         scale = np.zeros((len(keys), P), dtype=np.complex128)
+        for ki, kk in enumerate(keys):
+            if kk[0] == "eq":
+                _, ei, g, ti = kk
+                eq = self.equations[ei]
+                term = getattr(eq, g)[ti]
+                scale[ki] = per_pencil(term.coef) * self._phase(vq[term.var] - eq.phase)
+            else:
+                _, si, ai = kk
+                alt = self.bc_slots[si].alternatives[ai]
+                scale[ki] = np.where(active[si] == ai, self._phase(vq[alt.var] - alt.phase), 0.0)
         bcv = np.zeros((P, nbc), dtype=np.complex128)
-        for p, kx in enumerate(kx_list):
-            active = [slot.alternatives.index(slot.pick(kx)) for slot in self.bc_slots]
-            for ki, k in enumerate(keys):
-                if k[0] == "eq":
-                    _, ei, g, ti = k
-                    eq = self.equations[ei]
-                    term = getattr(eq, g)[ti]
-                    scale[ki, p] = complex(_as_fn(term.coef)(kx)) * self._phase(vq[term.var] - eq.phase)
-                else:
-                    _, si, ai = k
-                    if active[si] == ai:
-                        alt = self.bc_slots[si].alternatives[ai]
-                        scale[ki, p] = self._phase(vq[alt.var] - alt.phase)
-            for si, slot in enumerate(self.bc_slots):
-                alt = slot.pick(kx)
-                bcv[p, si] = complex(_as_fn(alt.value)(kx)) * self._phase(-alt.phase)
-        vals = scale[ent_key, :] * base[:, None]                 # [entries, P]
-        Mc = np.zeros((P, nnz), dtype=np.complex128)
-        Lc = np.zeros((P, nnz), dtype=np.complex128)
-        for mask, out in ((is_M, Mc), (~is_M, Lc)):
+        for si, slot in enumerate(self.bc_slots):
+            for ai, alt in enumerate(slot.alternatives):
+                bcv[:, si] += np.where(active[si] == ai, per_pencil(alt.value) * self._phase(-alt.phase), 0.0)
+        # value maps: nnz x keys (base values summed per structural slot)
+        import scipy.sparse as sps
+        maps = []
+        for mask in (is_M, ~is_M):
             idx = np.nonzero(mask)[0]
-            tmp = np.zeros((nnz, P), dtype=np.complex128)
-            np.add.at(tmp, inv[idx], vals[idx])
-            out[:] = tmp.T
-        for X in (Mc, Lc):
-            if np.abs(X.imag).max(initial=0) > 1e-14 * max(1.0, np.abs(X).max(initial=0)):
-                raise ValueError("pencil is not real under the given phases")
-        Mv, Lv = Mc.real.copy(), Lc.real.copy()
+            maps.append(sps.csr_matrix((base[idx], (inv[idx], ent_key[idx])), shape=(nnz, len(keys))))
+
+        def pencil_values(p0, p1):
+            out = []
+            for A in maps:
+                X = (A @ scale[:, p0:p1]).T                        # [p1 - p0, nnz] complex
+                if np.abs(X.imag).max(initial=0) > 1e-14 * max(1.0, np.abs(X).max(initial=0)):
+                    raise ValueError("pencil is not real under the given phases")
+                out.append(np.ascontiguousarray(X.real))
+            return tuple(out)
+
         col_map, row_map, bc_rows = self.layout(N)
         d = ucol - urow
-        return dict(
-            n=n, N=N, S=S, P=P, indptr=indptr, indices=indices, M=Mv, L=Lv,
+        res = dict(
+            n=n, N=N, S=S, P=P, indptr=indptr, indices=indices, values=pencil_values,
             bc_values=bcv, bc_rows=bc_rows, col_map=col_map, row_map=row_map,
             kl=int(max(0, -d.min())), ku=int(max(0, d.max())),
             var_recombine=np.array([v in self.recombine for v in self.variables], np.int32),
@@ -282,3 +294,6 @@ class PencilProblem:
             eq_differential=np.array([e.differential for e in self.equations], np.int32),
             eq_phase=np.array([e.phase for e in self.equations], np.int32),
         )
+        if values:
+            res["M"], res["L"] = pencil_values(0, P)
+        return res
