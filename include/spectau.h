@@ -27,9 +27,10 @@
  *    [p][m], p = 0 .. P-1 the stored k_x >= 0 modes (k_x = 2 pi p / L_x,
  *    Nyquist dropped, Sec. "Fourier basis"), m = 0 .. N_z-1 the Chebyshev
  *    mode (Sec. "Chebyshev basis");
- *  - grid layout 'g': real FP64 indexed [iz][ix] on the Gauss-Chebyshev nodes
- *    z_i = a + (b - a)(1 - cos(pi (i + 1/2) / N_gz)) / 2 (ascending) and
- *    the Fourier nodes x_i = L_x i / N_gx.
+ *    (3D: p = i_y N_x/2 + i_x, see sp_add_problem);
+ *  - grid layout 'g': real FP64 indexed [iz][ix] (3D: [iz][iy][ix]) on the
+ *    Gauss-Chebyshev nodes z_i = a + (b - a)(1 - cos(pi (i + 1/2) / N_gz)) / 2
+ *    (ascending) and the Fourier nodes x_i = L_x i / N_gx, y_i = L_y i / N_gy.
  */
 #ifndef SPECTAU_H
 #define SPECTAU_H
@@ -75,8 +76,9 @@ typedef enum { SP_RK222 = 0, SP_SBDF1 = 1, SP_SBDF2 = 2, SP_RK111 = 3 } sp_schem
  * pencil factorization, right-hand-side assembly and solves in FP64. */
 typedef enum { SP_PREC_FP64 = 0, SP_PREC_MIXED = 1 } sp_precision;
 
-/* Operators in bilinear right-hand-side terms. */
-typedef enum { SP_OP_ID = 0, SP_OP_DX = 1 } sp_op;
+/* Operators in bilinear right-hand-side terms (DY: three-dimensional
+ * problems only). */
+typedef enum { SP_OP_ID = 0, SP_OP_DX = 1, SP_OP_DY = 2 } sp_op;
 
 /* Create a context on CUDA device `device`, queueing work on `cuda_stream`
  * (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = the
@@ -91,11 +93,18 @@ sp_status sp_destroy(sp_ctx* ctx);
 const char* sp_last_error(const sp_ctx* ctx);
 
 /* Declare a problem (Sec. "Domains", Sec. "Problems").  ndim = 2:
- * bases[0] Fourier (x), bases[1] Chebyshev (z, the coupled axis, last).
+ * bases[0] Fourier (x), bases[1] Chebyshev (z, the coupled axis, last);
+ * ndim = 3: bases[0] Fourier (x, real data), bases[1] Fourier (y, complex
+ * axis), bases[2] Chebyshev (z).  Pencils: one per stored Fourier mode,
+ * P = N_x/2 (2D) or P = N_y N_x/2 (3D, pencil p = i_y N_x/2 + i_x, i_y the
+ * y slot in FFT order: mode i_y for i_y < N_y/2, i_y - N_y above, the
+ * Nyquist slot N_y/2 held at zero by the transforms).
  * nvars = S = number of first-order variables = number of equations.
- * Sizes supported by the kernels: N_x even with N_gx = N_x * scale of the
- * form 2^k or 3*2^k (16 <= N_gx <= 4096), N_z with N_gz likewise
- * (8 <= N_gz <= 1536), S <= 16.  *problem_id receives the handle. */
+ * Sizes supported by the kernels: N_x, N_y even with N_gx = N_x * scale and
+ * N_gy of the form 2^k or 3*2^k (16 <= N_gx <= 4096, 4 <= N_gy <= 4096),
+ * N_z with N_gz likewise (8 <= N_gz <= 1536), S <= 16.  Batched stepping,
+ * the adjoint entry points and sp_transform_backward_static take 2D
+ * problems only (SP_ERR_ARG otherwise).  *problem_id receives the handle. */
 sp_status sp_add_problem(sp_ctx* ctx, int ndim, const sp_basis* bases, int nvars,
                          int scheme, int precision, int* problem_id);
 
@@ -151,7 +160,8 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt);
 
 /* Set / get one variable of the state (Sec. "Initial conditions").
  * layout 'c': P*N_z complex (re, im) doubles [p][m], true coefficients;
- * layout 'g': N_z*N_x real doubles [iz][ix] on the scale-1 grid
+ * layout 'g': N_z*N_x (3D: N_z*N_y*N_x) real doubles [iz][ix] ([iz][iy][ix])
+ * on the scale-1 grid
  * (forward-transformed on the device).  Setting a variable restarts
  * multistep history (the next SBDF2 step is an SBDF1 step). */
 sp_status sp_set_field(sp_ctx* ctx, int problem, int var, const void* data, int on_device,
@@ -230,9 +240,10 @@ sp_status sp_dz_adjoint(sp_ctx* ctx, int problem, const void* dst_bar_dev, void*
 sp_status sp_sync_status(sp_ctx* ctx, int64_t* pencil);
 
 /* Transform nfields fields between coefficient and grid space at scale
- * scale_num/scale_den along both axes (Sec. "Scaled transforms &
+ * scale_num/scale_den along every axis (Sec. "Scaled transforms &
  * dealiasing"): direction -1 = backward (in: 'c' layout [f][p][m] complex,
- * out: grid [f][iz][ix] real, N_g = scale * N_c with zero padding),
+ * out: grid [f][iz][ix] (3D: [f][iz][iy][ix]) real, N_g = scale * N_c with
+ * zero padding; order z, y, x),
  * direction +1 = forward (in: grid, out: 'c', truncation to N_c).
  * Arithmetic in the problem's transform precision; in/out are host
  * (on_device = 0) or device (on_device = 1) FP64 arrays. */

@@ -20,7 +20,7 @@ SP_FOURIER, SP_CHEBYSHEV = 0, 1
 SP_RK222, SP_SBDF1, SP_SBDF2, SP_RK111 = 0, 1, 2, 3
 SCHEMES = {"RK222": SP_RK222, "SBDF1": SP_SBDF1, "SBDF2": SP_SBDF2, "RK111": SP_RK111}
 SP_PREC_FP64, SP_PREC_MIXED = 0, 1
-SP_OP_ID, SP_OP_DX = 0, 1
+SP_OP_ID, SP_OP_DX, SP_OP_DY = 0, 1, 2
 
 EXPORTS = (
     "sp_create", "sp_destroy", "sp_last_error", "sp_add_problem", "sp_set_layout",

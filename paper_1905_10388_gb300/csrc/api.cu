@@ -62,9 +62,10 @@ struct DevBuf {
 
 struct Problem {
   int ndim = 2, S = 0, scheme = 0, prec = 0;
-  sp_basis bx{}, bz{};
+  sp_basis bx{}, by{}, bz{};
   int Nx = 0, Nz = 0, P = 0, Ngx = 0, Ngz = 0;
-  double Lx = 0, za = 0, zb = 1;
+  int Ny = 1, Ngy = 1, K = 0;     // y axis (3D; 1 on 2D problems), K = N_x / 2 x modes per pencil row
+  double Lx = 0, Ly = 0, za = 0, zb = 1;
   // layout
   bool has_layout = false;
   std::vector<int32_t> col_map, row_map, var_rec, var_ph, eq_diff, eq_ph, bc_rows;
@@ -106,6 +107,7 @@ struct Problem {
   double2* d_LX[3] = {nullptr, nullptr, nullptr};
   double2* d_Fc[3] = {nullptr, nullptr, nullptr};
   void* d_gz = nullptr;
+  void* d_gy = nullptr;            // 3D: y-transformed fields [f][zg][yg][i_x]
   void* d_h = nullptr;
   BandFactor fac[2];
   int nfac = 0;
@@ -265,8 +267,14 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
   std::vector<double2> bcv(pr->bc_values.size() / 2);
   for (size_t i = 0; i < bcv.size(); ++i) bcv[i] = make_double2(pr->bc_values[2 * i], pr->bc_values[2 * i + 1]);
   CK(upload(&pr->d_bc_values, bcv, s));
-  std::vector<double> kx(pr->P);
-  for (int p = 0; p < pr->P; ++p) kx[p] = 2.0 * 3.14159265358979323846 * p / pr->Lx;
+  // k_x of every pencil, then k_y (zero in 2D); y slots in FFT order
+  std::vector<double> kx(2 * (size_t)pr->P, 0.0);
+  const double twopi = 2.0 * 3.14159265358979323846;
+  for (int p = 0; p < pr->P; ++p) {
+    const int ix = p % pr->K, iy = p / pr->K;
+    kx[p] = twopi * ix / pr->Lx;
+    if (pr->ndim == 3) kx[pr->P + p] = twopi * (iy < pr->Ny / 2 ? iy : iy - pr->Ny) / pr->Ly;
+  }
   CK(upload(&pr->d_kx, kx, s));
   std::vector<int32_t> gv, go;
   for (auto& g : pr->gfields) { gv.push_back(g.var); go.push_back(g.op); }
@@ -297,18 +305,25 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
   for (auto& b : pr->d_Fc) CK(dalloc(&b, (size_t)nl * pr->P * pr->Nz));
   const size_t esz = pr->prec ? sizeof(float2) : sizeof(double2);
   const int nf = std::max<int>(1, (int)pr->gfields.size());
-  CK(cudaMalloc(&pr->d_gz, (size_t)nf * pr->Ngz * pr->P * esz));
-  CK(cudaMalloc(&pr->d_h, (size_t)nl * pr->Ngz * pr->P * esz));
+  const size_t rows = (size_t)pr->Ngz * pr->Ngy;   // x rows of the dealiased grid
+  CK(cudaMalloc(&pr->d_gz, (size_t)std::max(nf, nl) * pr->Ngz * pr->P * esz));
+  CK(cudaMalloc(&pr->d_h, (size_t)nl * rows * pr->K * esz));
+  if (pr->ndim == 3) CK(cudaMalloc(&pr->d_gy, (size_t)nf * rows * pr->K * esz));
   TransformPlan* tp;
   sp_status st;
   if ((st = make_plan(ctx, pr, pr->Nz, pr->Ngz, &tp)) != SP_OK) return st;
   if ((st = make_plan(ctx, pr, pr->Nx, pr->Ngx, &tp)) != SP_OK) return st;
+  if (pr->ndim == 3 && (st = make_plan(ctx, pr, pr->Ny, pr->Ngy, &tp)) != SP_OK) return st;
   // band storage
   const int kuu = pr->kl + pr->ku;
   pr->npad = (pr->n + SOLVE_CHUNK - 1) / SOLVE_CHUNK * SOLVE_CHUNK;
   pr->lpad = std::max(2, (pr->kl + 1) / 2 * 2);
   pr->upad = kuu <= 31 ? 32 : 64;
-  for (auto& f : pr->fac) {
+  // SBDF2 keeps two factors (its SBDF1 start and the SBDF2 matrix); the
+  // other schemes one
+  const int nfactors = pr->scheme == SP_SBDF2 ? 2 : 1;
+  for (int fi = 0; fi < nfactors; ++fi) {
+    BandFactor& f = pr->fac[fi];
     CK(dalloc(&f.L, (size_t)pr->P * pr->npad * pr->lpad));
     CK(dalloc(&f.piv, (size_t)pr->P * pr->npad));
     CK(dalloc(&f.U, (size_t)pr->P * pr->npad * pr->upad));
@@ -329,7 +344,7 @@ void free_problem(Problem* pr) {
   for (auto b : pr->d_MX) F(b);
   for (auto b : pr->d_LX) F(b);
   for (auto b : pr->d_Fc) F(b);
-  F(pr->d_gz); F(pr->d_h);
+  F(pr->d_gz); F(pr->d_gy); F(pr->d_h);
   for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); F(f.rd); }
   F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd);
   F(pr->d_indptrT); F(pr->d_indicesT); F(pr->d_MvT); F(pr->d_LvT);
@@ -340,7 +355,41 @@ void free_problem(Problem* pr) {
   for (auto e : pr->ev) cudaEventDestroy(e);
 }
 
-// F(X) for the current coefficient state: z backward -> x rows (products) -> z forward
+// Grid <-> coefficient transforms of nf fields at grid sizes (Ngx, Ngy, Ngz)
+// (Ngy = 1 on 2D problems) in precision prec, device buffers:
+//   grid [f][iz][iy][ix] real FP64, coefficients [f][p][m] complex FP64
+//   (backward: fields f_var[0 .. nf) of xc with field stride xstride, or of
+//   an FP32 copy xc32 in mixed precision).
+// Scratch: mid1 and mid2, grid_scratch_elems complex values each in precision prec.
+size_t grid_scratch_elems(Problem* pr, int nf, int Ngy, int Ngz) {
+  return (size_t)nf * Ngz * std::max((size_t)Ngy * pr->K, (size_t)pr->P);
+}
+cudaError_t grid_to_coef(Problem* pr, cudaStream_t s, int prec, int nf, TransformPlan& px, TransformPlan* py,
+                         TransformPlan& pz, int Ngy, int Ngz, double* grid, double2* coef, void* mid1, void* mid2) {
+  cudaError_t e = launch_fourier_rows(s, prec, px, Ngz * Ngy, pr->K, 4, nf, nullptr, grid, nullptr, 0, nullptr,
+                                      nullptr, nullptr, nullptr, 0, mid1);
+  if (e != cudaSuccess) return e;
+  if (pr->ndim == 3) {
+    if ((e = launch_fourier_y(s, prec, *py, +1, nf, Ngz, pr->K, mid1, mid2)) != cudaSuccess) return e;
+    return launch_cheb_forward(s, prec, pz, pr->P, nf, mid2, coef);
+  }
+  return launch_cheb_forward(s, prec, pz, pr->P, nf, mid1, coef);
+}
+cudaError_t coef_to_grid(Problem* pr, cudaStream_t s, int prec, int nf, TransformPlan& px, TransformPlan* py,
+                         TransformPlan& pz, int Ngy, int Ngz, const int32_t* f_var, const double2* xc, int xstride,
+                         const float2* xc32, double* grid, void* mid1, void* mid2) {
+  void* zout = pr->ndim == 3 ? mid2 : mid1;
+  cudaError_t e = launch_cheb_backward(s, prec, pz, pr->P, nf, f_var, pr->d_zero, pr->d_kx, xc, xstride, zout,
+                                       pr->d_kx32, xc32);
+  if (e != cudaSuccess) return e;
+  if (pr->ndim == 3 && (e = launch_fourier_y(s, prec, *py, -1, nf, Ngz, pr->K, mid2, mid1)) != cudaSuccess)
+    return e;
+  return launch_fourier_rows(s, prec, px, Ngz * Ngy, pr->K, 1, nf, mid1, nullptr, grid, 0, nullptr, nullptr,
+                             nullptr, nullptr, 0, nullptr);
+}
+
+// F(X) for the current coefficient state: z backward -> (y backward) -> x
+// rows (products) -> (y forward) -> z forward
 sp_status eval_rhs(sp_ctx* ctx, Problem* pr, cudaStream_t s, double2* fc_out) {
   if (pr->nl_eqs.empty()) {
     CK(cudaMemsetAsync(fc_out, 0, (size_t)pr->P * pr->Nz * sizeof(double2), s));
@@ -355,7 +404,17 @@ sp_status eval_rhs(sp_ctx* ctx, Problem* pr, cudaStream_t s, double2* fc_out) {
   }
   CK(launch_cheb_backward(s, pr->prec, pz, pr->P, nf, pr->d_gvar, pr->d_gop, pr->d_kx, pr->d_Xc,
                           pr->P * pr->Nz, pr->d_gz, pr->d_kx32, pr->d_Xc32));
-  CK(launch_fourier_rows(s, pr->prec, px, pr->Ngz, pr->P, 7, nf, pr->d_gz, nullptr, nullptr,
+  if (pr->ndim == 3) {
+    TransformPlan& py = pr->plans.at({pr->Ny, pr->Ngy});
+    CK(launch_fourier_y(s, pr->prec, py, -1, nf, pr->Ngz, pr->K, pr->d_gz, pr->d_gy));
+    CK(launch_fourier_rows(s, pr->prec, px, pr->Ngz * pr->Ngy, pr->K, 7, nf, pr->d_gy, nullptr, nullptr,
+                           (int)pr->t_slot.size(), pr->d_tslot, pr->d_tcoef, pr->d_tfa, pr->d_tfb, ne, pr->d_h,
+                           pr->d_tcoef32));
+    CK(launch_fourier_y(s, pr->prec, py, +1, ne, pr->Ngz, pr->K, pr->d_h, pr->d_gz));
+    CK(launch_cheb_forward(s, pr->prec, pz, pr->P, ne, pr->d_gz, fc_out));
+    return SP_OK;
+  }
+  CK(launch_fourier_rows(s, pr->prec, px, pr->Ngz, pr->K, 7, nf, pr->d_gz, nullptr, nullptr,
                          (int)pr->t_slot.size(), pr->d_tslot, pr->d_tcoef, pr->d_tfa, pr->d_tfb, ne, pr->d_h,
                          pr->d_tcoef32));
   CK(launch_cheb_forward(s, pr->prec, pz, pr->P, ne, pr->d_h, fc_out));
@@ -723,17 +782,19 @@ sp_status sp_add_problem(sp_ctx* ctx, int ndim, const sp_basis* bases, int nvars
                          int* problem_id) {
   if (!ctx) return SP_ERR_ARG;
   ctx->err.clear();
-  if (ndim != 2) return fail(ctx, SP_ERR_ARG, "only ndim = 2 (Fourier x Chebyshev) is supported");
+  if (ndim != 2 && ndim != 3)
+    return fail(ctx, SP_ERR_ARG, "ndim must be 2 (Fourier x Chebyshev) or 3 (Fourier x Fourier x Chebyshev)");
   if (!bases || !problem_id) return fail(ctx, SP_ERR_ARG, "null argument");
   const sp_basis& bx = bases[0];
-  const sp_basis& bz = bases[1];
-  if (bx.kind != SP_FOURIER || bz.kind != SP_CHEBYSHEV)
-    return fail(ctx, SP_ERR_ARG, "bases must be (Fourier, Chebyshev), the Chebyshev axis last");
+  const sp_basis& bz = bases[ndim - 1];
+  if (bx.kind != SP_FOURIER || bz.kind != SP_CHEBYSHEV || (ndim == 3 && bases[1].kind != SP_FOURIER))
+    return fail(ctx, SP_ERR_ARG, "bases must be Fourier axes followed by one Chebyshev axis (last)");
   if (nvars < 1 || nvars > 16) return fail(ctx, SP_ERR_ARG, "nvars must be in [1, 16]");
   if (scheme < SP_RK222 || scheme > SP_RK111) return fail(ctx, SP_ERR_ARG, "unknown scheme %d", scheme);
   if (precision != SP_PREC_FP64 && precision != SP_PREC_MIXED)
     return fail(ctx, SP_ERR_ARG, "unknown precision %d", precision);
   auto pr = std::make_unique<Problem>();
+  pr->ndim = ndim;
   pr->S = nvars;
   pr->scheme = scheme;
   pr->prec = precision == SP_PREC_MIXED ? 1 : 0;
@@ -743,7 +804,8 @@ sp_status sp_add_problem(sp_ctx* ctx, int ndim, const sp_basis* bases, int nvars
   pr->Nz = bz.n_coeff;
   if (pr->Nx < 4 || pr->Nx % 2) return fail(ctx, SP_ERR_ARG, "N_x must be even and >= 4");
   if (pr->Nz < 4) return fail(ctx, SP_ERR_ARG, "N_z must be >= 4");
-  for (const sp_basis* b : {&bx, &bz}) {
+  for (int i = 0; i < ndim; ++i) {
+    const sp_basis* b = &bases[i];
     if (b->dealias_num <= 0 || b->dealias_den <= 0 || (b->n_coeff * b->dealias_num) % b->dealias_den)
       return fail(ctx, SP_ERR_ARG, "dealias scale must give an integer grid size");
     if (b->dealias_num < b->dealias_den) return fail(ctx, SP_ERR_ARG, "dealias scale must be >= 1");
@@ -755,7 +817,18 @@ sp_status sp_add_problem(sp_ctx* ctx, int ndim, const sp_basis* bases, int nvars
     return fail(ctx, SP_ERR_ARG, "N_gx = %d must be 2^k or 3*2^k in [16, 4096]", pr->Ngx);
   if (!is_smooth_length(pr->Ngz) || pr->Ngz < 8 || pr->Ngz > 1536)
     return fail(ctx, SP_ERR_ARG, "N_gz = %d must be 2^k or 3*2^k in [8, 1536]", pr->Ngz);
-  pr->P = pr->Nx / 2;
+  pr->K = pr->Nx / 2;
+  if (ndim == 3) {
+    const sp_basis& by = bases[1];
+    pr->by = by;
+    pr->Ny = by.n_coeff;
+    if (pr->Ny < 2 || pr->Ny % 2) return fail(ctx, SP_ERR_ARG, "N_y must be even and >= 2");
+    pr->Ngy = by.n_coeff * by.dealias_num / by.dealias_den;
+    if (!is_smooth_length(pr->Ngy) || pr->Ngy < 4 || pr->Ngy > 4096)
+      return fail(ctx, SP_ERR_ARG, "N_gy = %d must be 2^k or 3*2^k in [4, 4096]", pr->Ngy);
+    pr->Ly = by.b - by.a;
+  }
+  pr->P = pr->Ny * pr->K;
   pr->Lx = bx.b - bx.a;
   pr->za = bz.a;
   pr->zb = bz.b;
@@ -874,8 +947,9 @@ sp_status sp_set_bilinear_rhs(sp_ctx* ctx, int problem, int nterms, const int32_
   for (int t = 0; t < nterms; ++t) {
     if (eq[t] < 0 || eq[t] >= pr->S || var_a[t] < 0 || var_a[t] >= pr->S || var_b[t] < 0 || var_b[t] >= pr->S)
       return fail(ctx, SP_ERR_ARG, "term %d: index out of range", t);
-    if ((op_a[t] != SP_OP_ID && op_a[t] != SP_OP_DX) || (op_b[t] != SP_OP_ID && op_b[t] != SP_OP_DX))
-      return fail(ctx, SP_ERR_ARG, "term %d: unknown operator", t);
+    auto op_ok = [&](int op) { return op == SP_OP_ID || op == SP_OP_DX || (op == SP_OP_DY && pr->ndim == 3); };
+    if (!op_ok(op_a[t]) || !op_ok(op_b[t]))
+      return fail(ctx, SP_ERR_ARG, "term %d: unknown operator (DY needs a 3D problem)", t);
     int slot = -1;
     for (size_t i = 0; i < pr->nl_eqs.size(); ++i)
       if (pr->nl_eqs[i] == eq[t]) slot = (int)i;
@@ -947,23 +1021,25 @@ sp_status sp_set_field(sp_ctx* ctx, int problem, int var, const void* data, int 
     CK(cudaMemcpyAsync(dst, data, ncoef * sizeof(double2),
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   } else if (layout == 'g') {
-    TransformPlan *px, *pz;
-    if ((st = make_plan(ctx, pr, pr->Nx, pr->Nx, &px)) != SP_OK) return st;
-    if ((st = make_plan(ctx, pr, pr->Nz, pr->Nz, &pz)) != SP_OK) return st;
-    const size_t ng = (size_t)pr->Nz * pr->Nx;
-    double* grid = nullptr;
-    void* h = nullptr;
-    CK(dalloc(&grid, ng));
     // set-up transforms run in FP64 in every precision mode: an initial
     // state carries small perturbations on an O(1) background
-    CK(cudaMalloc(&h, (size_t)pr->Nz * pr->P * 16));
+    TransformPlan *px, *pz, *py = nullptr;
+    if ((st = make_plan(ctx, pr, pr->Nx, pr->Nx, &px)) != SP_OK) return st;
+    if ((st = make_plan(ctx, pr, pr->Nz, pr->Nz, &pz)) != SP_OK) return st;
+    if (pr->ndim == 3 && (st = make_plan(ctx, pr, pr->Ny, pr->Ny, &py)) != SP_OK) return st;
+    const size_t ng = (size_t)pr->Nz * pr->Ny * pr->Nx;
+    double* grid = nullptr;
+    double2 *m1 = nullptr, *m2 = nullptr;
+    const size_t nm = grid_scratch_elems(pr, 1, pr->Ny, pr->Nz);
+    CK(dalloc(&grid, ng));
+    CK(dalloc(&m1, nm));
+    CK(dalloc(&m2, nm));
     CK(cudaMemcpyAsync(grid, data, ng * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    CK(launch_fourier_rows(s, 0, *px, pr->Nz, pr->P, 4, 1, nullptr, grid, nullptr, 0, nullptr, nullptr,
-                           nullptr, nullptr, 0, h));
-    CK(launch_cheb_forward(s, 0, *pz, pr->P, 1, h, dst));
+    CK(grid_to_coef(pr, s, 0, 1, *px, py, *pz, pr->Ny, pr->Nz, grid, dst, m1, m2));
     CK(cudaStreamSynchronize(s));
     cudaFree(grid);
-    cudaFree(h);
+    cudaFree(m1);
+    cudaFree(m2);
   } else {
     return fail(ctx, SP_ERR_ARG, "layout must be 'c' or 'g'");
   }
@@ -989,23 +1065,25 @@ sp_status sp_get_field(sp_ctx* ctx, int problem, int var, void* data, int on_dev
     CK(cudaMemcpyAsync(data, src, ncoef * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   } else if (layout == 'g') {
-    TransformPlan *px, *pz;
+    TransformPlan *px, *pz, *py = nullptr;
     sp_status st;
     if ((st = make_plan(ctx, pr, pr->Nx, pr->Nx, &px)) != SP_OK) return st;
     if ((st = make_plan(ctx, pr, pr->Nz, pr->Nz, &pz)) != SP_OK) return st;
-    const size_t ng = (size_t)pr->Nz * pr->Nx;
+    if (pr->ndim == 3 && (st = make_plan(ctx, pr, pr->Ny, pr->Ny, &py)) != SP_OK) return st;
+    const size_t ng = (size_t)pr->Nz * pr->Ny * pr->Nx;
     double* grid = nullptr;
-    void* gz = nullptr;
+    double2 *m1 = nullptr, *m2 = nullptr;
+    const size_t nm = grid_scratch_elems(pr, 1, pr->Ny, pr->Nz);
     CK(dalloc(&grid, ng));
-    CK(cudaMalloc(&gz, (size_t)pr->Nz * pr->P * 16));
-    CK(launch_cheb_backward(s, 0, *pz, pr->P, 1, pr->d_ident + var, pr->d_zero, pr->d_kx, pr->d_Xc,
-                            pr->P * pr->Nz, gz));
-    CK(launch_fourier_rows(s, 0, *px, pr->Nz, pr->P, 1, 1, gz, nullptr, grid, 0, nullptr, nullptr,
-                           nullptr, nullptr, 0, nullptr));
+    CK(dalloc(&m1, nm));
+    CK(dalloc(&m2, nm));
+    CK(coef_to_grid(pr, s, 0, 1, *px, py, *pz, pr->Ny, pr->Nz, pr->d_ident + var, pr->d_Xc, pr->P * pr->Nz,
+                    nullptr, grid, m1, m2));
     CK(cudaMemcpyAsync(data, grid, ng * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     cudaFree(grid);
-    cudaFree(gz);
+    cudaFree(m1);
+    cudaFree(m2);
   } else {
     return fail(ctx, SP_ERR_ARG, "layout must be 'c' or 'g'");
   }
@@ -1106,6 +1184,7 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
     if (!pr->factored || dts[q] != pr->fac_dt)
       return fail(ctx, SP_ERR_NOT_FACTORED, "problem %d: dt = %.17g is not its factored step size", ids[q], dts[q]);
     if (pr->nl_eqs.empty()) return fail(ctx, SP_ERR_ARG, "problem %d has no bilinear right-hand side", ids[q]);
+    if (pr->ndim != 2) return fail(ctx, SP_ERR_ARG, "problem %d: batched stepping takes 2D problems", ids[q]);
     ps.push_back(pr);
   }
   for (Problem* pr : ps)
@@ -1220,6 +1299,7 @@ sp_status sp_adjoint_init(sp_ctx* ctx, int problem) {
   ctx->err.clear();
   if (pr->scheme != SP_RK222 && pr->scheme != SP_RK111)
     return fail(ctx, SP_ERR_ARG, "the adjoint step is provided for the RK222 and RK111 schemes");
+  if (pr->ndim != 2) return fail(ctx, SP_ERR_ARG, "the adjoint step is provided for 2D problems");
   if (!pr->factored) return fail(ctx, SP_ERR_STATE, "sp_factor must come before sp_adjoint_init");
   if (pr->nl_eqs.empty()) return fail(ctx, SP_ERR_ARG, "the problem has no bilinear right-hand side");
   CK(cudaSetDevice(ctx->device));
@@ -1416,6 +1496,7 @@ sp_status sp_transform_adjoint(sp_ctx* ctx, int problem, const void* in, void* o
   if (scale_num <= 0 || scale_den <= 0 || scale_num < scale_den ||
       (pr->Nx * scale_num) % scale_den || (pr->Nz * scale_num) % scale_den)
     return fail(ctx, SP_ERR_ARG, "scale must be >= 1 and give integer grid sizes");
+  if (pr->ndim != 2) return fail(ctx, SP_ERR_ARG, "sp_transform_adjoint takes 2D problems");
   CK(cudaSetDevice(ctx->device));
   sp_status st = upload_problem(ctx, pr);
   if (st != SP_OK) return st;
@@ -1494,25 +1575,29 @@ sp_status sp_transform(sp_ctx* ctx, int problem, const void* in, void* out, int 
   ctx->err.clear();
   if (!in || !out || nfields < 1 || nfields > 16 || (direction != 1 && direction != -1))
     return fail(ctx, SP_ERR_ARG, "bad arguments");
-  if (scale_num <= 0 || scale_den <= 0 || scale_num < scale_den ||
-      (pr->Nx * scale_num) % scale_den || (pr->Nz * scale_num) % scale_den)
+  if (scale_num <= 0 || scale_den <= 0 || scale_num < scale_den || (pr->Nx * scale_num) % scale_den ||
+      (pr->Nz * scale_num) % scale_den || (pr->ndim == 3 && (pr->Ny * scale_num) % scale_den))
     return fail(ctx, SP_ERR_ARG, "scale must be >= 1 and give integer grid sizes");
   CK(cudaSetDevice(ctx->device));
   sp_status st = upload_problem(ctx, pr);
   if (st != SP_OK) return st;
   const int Ngx = pr->Nx * scale_num / scale_den, Ngz = pr->Nz * scale_num / scale_den;
-  TransformPlan *px, *pz;
+  const int Ngy = pr->ndim == 3 ? pr->Ny * scale_num / scale_den : 1;
+  TransformPlan *px, *pz, *py = nullptr;
   if ((st = make_plan(ctx, pr, pr->Nx, Ngx, &px)) != SP_OK) return st;
   if ((st = make_plan(ctx, pr, pr->Nz, Ngz, &pz)) != SP_OK) return st;
+  if (pr->ndim == 3 && (st = make_plan(ctx, pr, pr->Ny, Ngy, &py)) != SP_OK) return st;
   cudaStream_t s = ctx->stream;
-  const size_t ncoef = (size_t)nfields * pr->P * pr->Nz, ngrid = (size_t)nfields * Ngz * Ngx;
+  const size_t ncoef = (size_t)nfields * pr->P * pr->Nz, ngrid = (size_t)nfields * Ngz * Ngy * Ngx;
   const size_t esz = pr->prec ? 8 : 16;
+  const size_t nm = grid_scratch_elems(pr, nfields, Ngy, Ngz);
   double2* coef = nullptr;
   double* grid = nullptr;
-  void* mid = nullptr;
+  void *m1 = nullptr, *m2 = nullptr;
   CK(dalloc(&coef, ncoef));
   CK(dalloc(&grid, ngrid));
-  CK(cudaMalloc(&mid, (size_t)nfields * Ngz * pr->P * esz));
+  CK(cudaMalloc(&m1, nm * esz));
+  CK(cudaMalloc(&m2, nm * esz));
   const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   cudaError_t e;
@@ -1524,24 +1609,19 @@ sp_status sp_transform(sp_ctx* ctx, int problem, const void* in, void* out, int 
       if (e == cudaSuccess) e = launch_to_f32(s, coef, coef32, ncoef);
     }
     if (e == cudaSuccess)
-      e = launch_cheb_backward(s, pr->prec, *pz, pr->P, nfields, pr->d_ident, pr->d_zero, pr->d_kx, coef,
-                               pr->P * pr->Nz, mid, pr->d_kx32, coef32);
-    if (e == cudaSuccess)
-      e = launch_fourier_rows(s, pr->prec, *px, Ngz, pr->P, 1, nfields, mid, nullptr, grid, 0, nullptr, nullptr,
-                              nullptr, nullptr, 0, nullptr);
+      e = coef_to_grid(pr, s, pr->prec, nfields, *px, py, *pz, Ngy, Ngz, pr->d_ident, coef, pr->P * pr->Nz, coef32,
+                       grid, m1, m2);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, grid, ngrid * sizeof(double), kout, s);
   } else {
     e = cudaMemcpyAsync(grid, in, ngrid * sizeof(double), kin, s);
-    if (e == cudaSuccess)
-      e = launch_fourier_rows(s, pr->prec, *px, Ngz, pr->P, 4, nfields, nullptr, grid, nullptr, 0, nullptr,
-                              nullptr, nullptr, nullptr, 0, mid);
-    if (e == cudaSuccess) e = launch_cheb_forward(s, pr->prec, *pz, pr->P, nfields, mid, coef);
+    if (e == cudaSuccess) e = grid_to_coef(pr, s, pr->prec, nfields, *px, py, *pz, Ngy, Ngz, grid, coef, m1, m2);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, coef, ncoef * sizeof(double2), kout, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(coef);
   cudaFree(grid);
-  cudaFree(mid);
+  cudaFree(m1);
+  cudaFree(m2);
   if (coef32) cudaFree(coef32);
   CK(e);
   return SP_OK;

@@ -415,7 +415,11 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     double w[RU], nw[RU];
 #pragma unroll
     for (int r = 0; r < RU; ++r) {
-      const int i = npad - W + lane + 32 * r;      // congruent to lane + 32 r (mod W)
+      // the row of [npad - W, npad) congruent to lane + 32 r (mod W): slot
+      // (lane, r) always holds rows of that residue (npad is a multiple of
+      // 32 but not necessarily of W)
+      const int base = npad - W;
+      const int i = base + ((lane + 32 * r - base) & (W - 1));
       w[r] = (ok && i >= 0) ? Bd[2 * i] : 0.0;
       nw[r] = (ok && i - W >= 0) ? Bd[2 * (i - W)] : 0.0;
     }

@@ -109,6 +109,13 @@ struct XDesc {
   int xscale;                                // bit 1: transpose of forward x on input; bit 2: of backward x on output
 };
 
+// Complex Fourier y transform of nf x nz planes of N_y slots x K columns.
+struct YDesc {
+  int Ny, Ng, K, nz, radix3, dir;
+  const void* tw;
+  const void* src; void* dst;
+};
+
 // --- launchers (band.cu) ---------------------------------------------------
 cudaError_t launch_band_factor(cudaStream_t s, int P, int n, int nnz, int kl, int ku,
                                const int32_t* indptr, const int32_t* indices,
@@ -144,6 +151,10 @@ cudaError_t launch_fourier_rows_adjoint(cudaStream_t s, int prec, const Transfor
                                         int nf, const void* gz, int ne, const void* hin, int nterms,
                                         const int32_t* t_eq, const double* t_coef, const float* t_coef32,
                                         const int32_t* t_fa, const int32_t* t_fb, void* gzadj);
+// dir < 0: slots -> grid, dir > 0: grid -> slots (1/N_gy, Nyquist slot zero);
+// py = plan (N_y, N_gy); buffers [f][zg][slot or yg][K] in the precision.
+cudaError_t launch_fourier_y(cudaStream_t s, int prec, const TransformPlan& py, int dir, int nf, int nz, int K,
+                             const void* src, void* dst);
 size_t z_smem_bytes(int prec, int Ng, int tile);
 size_t x_smem_bytes(int prec, int N, int mode, int nf, int ne);
 cudaError_t launch_cheb_backward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,

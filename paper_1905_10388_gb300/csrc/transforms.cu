@@ -56,7 +56,9 @@ __device__ __forceinline__ void cheb_backward_body(const ZDesc& d, int bx, int f
     const int p = p0 + c;
     if (p >= P || k >= Nc) return mk<T>(0, 0);
     C<T> x = src[(size_t)p * Nc + k];
+    // kx holds k_x for every pencil followed by k_y (zero on 2D problems)
     if (op == SP_OP_DX) x = mk<T>(-kxT[p] * x.y, kxT[p] * x.x);
+    else if (op == SP_OP_DY) x = mk<T>(-kxT[P + p] * x.y, kxT[P + p] * x.x);
     // weighted_in: transpose of the forward transform, c_k (2 - delta_k0) / N_g
     const T wgt = d.weighted_in ? (k == 0 ? (T)1 : (T)2) / (T)Ng : (T)1;
     const T s = ((k & 1) ? (T)-1 : (T)1) * (k == 0 ? (T)1 : (T)0.5) * wgt;
@@ -349,6 +351,74 @@ __device__ __forceinline__ void fourier_rows_adjoint_body(const XDesc& d, int ro
 }
 
 // ---------------------------------------------------------------------------
+// Fourier y axis (complex data, Sec. "Fourier basis"), for field f, z-row zg
+// and the TX x-mode columns [bx TX, bx TX + TX): the N_y stored slots (FFT
+// order, slot s = mode s for s < N_y/2 and s - N_y above, Nyquist slot
+// dropped) and the N_gy grid points, one complex FFT of length N_gy per
+// column.
+//   backward (dir < 0): src[f][zg][s][ix] -> dst[f][zg][yg][ix],
+//                       g_j = sum_n f_n exp(+2 pi i n j / N_gy)
+//   forward  (dir > 0): src[f][zg][yg][ix] -> dst[f][zg][s][ix],
+//                       f_n = (1/N_gy) sum_j g_j exp(-2 pi i n j / N_gy),
+//                       Nyquist slot set to zero
+// ---------------------------------------------------------------------------
+template <typename T, int TX>
+__device__ __forceinline__ void fourier_y_body(const YDesc& d, int bx, int zg, int f, unsigned char* smem_raw) {
+  const int Ny = d.Ny, Ng = d.Ng, K = d.K;
+  C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
+  C<T>* b1 = b0 + TX * Ng;
+  C<T>* tws = b1 + TX * Ng;
+  load_twiddles<T>(tws, reinterpret_cast<const C<T>*>(d.tw), Ng);
+  const int ix0 = bx * TX;
+  const C<T>* src = reinterpret_cast<const C<T>*>(d.src);
+  C<T>* dst = reinterpret_cast<C<T>*>(d.dst);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const size_t plane = (size_t)f * d.nz + zg;
+  const int half = Ny / 2;
+  auto slot_index = [&](int sl) {       // position of slot sl in the length-N_gy spectrum
+    const int n = sl < half ? sl : sl - Ny;
+    return n < 0 ? n + Ng : n;
+  };
+  if (d.dir < 0) {
+    for (int idx = tid; idx < TX * Ng; idx += nt) b0[idx] = mk<T>(0, 0);
+    __syncthreads();
+    const C<T>* in = src + plane * Ny * K;
+    for (int idx = tid; idx < TX * Ny; idx += nt) {
+      const int sl = idx / TX, c = idx - sl * TX;
+      const int ix = ix0 + c;
+      if (sl == half || ix >= K) continue;
+      b0[c * Ng + slot_index(sl)] = in[(size_t)sl * K + ix];
+    }
+    __syncthreads();
+    const C<T>* res = fft_batched<T>(b0, b1, Ng, d.radix3, tws, +1, TX);
+    C<T>* out = dst + plane * Ng * K;
+    for (int idx = tid; idx < TX * Ng; idx += nt) {
+      const int yg = idx / TX, c = idx - yg * TX;
+      const int ix = ix0 + c;
+      if (ix < K) out[(size_t)yg * K + ix] = res[c * Ng + yg];
+    }
+  } else {
+    const C<T>* in = src + plane * Ng * K;
+    for (int idx = tid; idx < TX * Ng; idx += nt) {
+      const int yg = idx / TX, c = idx - yg * TX;
+      const int ix = ix0 + c;
+      b0[c * Ng + yg] = (ix < K) ? in[(size_t)yg * K + ix] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    const C<T>* res = fft_batched<T>(b0, b1, Ng, d.radix3, tws, -1, TX);
+    const T inv = (T)1 / (T)Ng;
+    C<T>* out = dst + plane * Ny * K;
+    for (int idx = tid; idx < TX * Ny; idx += nt) {
+      const int sl = idx / TX, c = idx - sl * TX;
+      const int ix = ix0 + c;
+      if (ix >= K) continue;
+      const C<T> v = (sl == half) ? mk<T>(0, 0) : res[c * Ng + slot_index(sl)];
+      out[(size_t)sl * K + ix] = mk<T>(v.x * inv, v.y * inv);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // kernels: one problem (descriptor by value) or a batch (descriptor table +
 // work list of (problem, x, y) items, one per CTA)
 // ---------------------------------------------------------------------------
@@ -375,6 +445,12 @@ __global__ void __launch_bounds__(Z_THREADS) k_cheb_forward_batched(const ZDesc*
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int4 w = work[blockIdx.x];
   cheb_forward_body<T, TP>(ds[w.x], w.y, w.z, smem_raw);
+}
+constexpr int Y_TILE = 8;
+template <typename T>
+__global__ void __launch_bounds__(Z_THREADS) k_fourier_y(YDesc d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fourier_y_body<T, Y_TILE>(d, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 template <typename T>
 __global__ void __launch_bounds__(X_THREADS) k_fourier_rows(XDesc d) {
@@ -577,6 +653,26 @@ cudaError_t launch_fourier_rows_batched(cudaStream_t s, int prec, const XDesc* d
   } else {
     if ((e = set_smem(k_fourier_rows_batched<double>, smem)) != cudaSuccess) return e;
     k_fourier_rows_batched<double><<<nwork, X_THREADS, smem, s>>>(ds, work);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fourier_y(cudaStream_t s, int prec, const TransformPlan& py, int dir, int nf, int nz, int K,
+                             const void* src, void* dst) {
+  YDesc d{};
+  d.Ny = py.Nc; d.Ng = py.Ng; d.K = K; d.nz = nz; d.radix3 = py.radix3; d.dir = dir;
+  d.tw = prec ? py.tw32 : py.tw64;
+  d.src = src; d.dst = dst;
+  if (nz > 65535 || nf > 65535) return cudaErrorInvalidValue;
+  const size_t smem = (2ull * Y_TILE + 1) * py.Ng * (prec ? sizeof(float2) : sizeof(double2));
+  dim3 grid((K + Y_TILE - 1) / Y_TILE, nz, nf);
+  cudaError_t e;
+  if (prec) {
+    if ((e = set_smem(k_fourier_y<float>, smem)) != cudaSuccess) return e;
+    k_fourier_y<float><<<grid, Z_THREADS, smem, s>>>(d);
+  } else {
+    if ((e = set_smem(k_fourier_y<double>, smem)) != cudaSuccess) return e;
+    k_fourier_y<double><<<grid, Z_THREADS, smem, s>>>(d);
   }
   return cudaGetLastError();
 }

@@ -52,29 +52,43 @@ class Context:
 
 
 class TauSolver:
-    """One Fourier(x) x Chebyshev(z) first-order problem in the library."""
+    """One Fourier(x) [x Fourier(y)] x Chebyshev(z) first-order problem in the
+    library (``n_y`` given: three dimensions, pencil p = i_y N_x/2 + i_x)."""
 
     def __init__(self, ctx, problem, n_x, n_z, L_x, kx_scale=None, scheme="RK222",
-                 precision="fp64", dealias=(3, 2), z_interval=(0.0, 1.0), bilinear=()):
+                 precision="fp64", dealias=(3, 2), z_interval=(0.0, 1.0), bilinear=(), n_y=None, L_y=None):
         self.ctx = ctx
         self.problem = problem
         self.Nx, self.Nz, self.Lx = int(n_x), int(n_z), float(L_x)
-        self.P = self.Nx // 2
+        self.ndim = 2 if n_y is None else 3
+        self.Ny = 1 if n_y is None else int(n_y)
+        self.Ly = float(L_y) if L_y is not None else None
+        self.K = self.Nx // 2
+        self.P = self.Ny * self.K
         self.S = problem.S
         self.var = {v: i for i, v in enumerate(problem.variables)}
         self.state_order = tuple(problem.variables)   # order of get_state / set_state
         self.eq = {e.name: i for i, e in enumerate(problem.equations)}
         lib, h = L.lib(), ctx.handle
-        bases = (L.sp_basis * 2)()
+        bases = (L.sp_basis * self.ndim)()
         bases[0] = L.sp_basis(L.SP_FOURIER, self.Nx, 0.0, self.Lx, dealias[0], dealias[1])
-        bases[1] = L.sp_basis(L.SP_CHEBYSHEV, self.Nz, z_interval[0], z_interval[1], dealias[0], dealias[1])
+        if self.ndim == 3:
+            bases[1] = L.sp_basis(L.SP_FOURIER, self.Ny, 0.0, self.Ly, dealias[0], dealias[1])
+        bases[self.ndim - 1] = L.sp_basis(L.SP_CHEBYSHEV, self.Nz, z_interval[0], z_interval[1],
+                                          dealias[0], dealias[1])
         pid = ctypes.c_int()
         prec = L.SP_PREC_MIXED if precision == "mixed" else L.SP_PREC_FP64
-        L.check(h, lib.sp_add_problem(h, 2, bases, self.S, L.SCHEMES[scheme], prec, ctypes.byref(pid)))
+        L.check(h, lib.sp_add_problem(h, self.ndim, bases, self.S, L.SCHEMES[scheme], prec, ctypes.byref(pid)))
         self.pid = pid.value
         self.scheme, self.precision = scheme, precision
-        kx = 2 * np.pi * np.arange(self.P) / self.Lx
-        asm = problem.build(self.Nz, kx)
+        kx = 2 * np.pi * np.arange(self.K) / self.Lx
+        if self.ndim == 2:
+            wavenumbers = kx
+        else:
+            iy = np.arange(self.Ny)
+            ky = 2 * np.pi * np.where(iy < self.Ny // 2, iy, iy - self.Ny) / self.Ly
+            wavenumbers = (np.tile(kx, self.Ny), np.repeat(ky, self.K))
+        asm = problem.build(self.Nz, wavenumbers, values=self.P <= 4096)
         self.assembly = asm
         c = lambda a: np.ascontiguousarray(a, dtype=np.int32)
         bcv = np.ascontiguousarray(np.stack([asm["bc_values"].real, asm["bc_values"].imag], -1), dtype=np.float64)
@@ -82,15 +96,17 @@ class TauSolver:
                                      L.i32(c(asm["var_recombine"])), L.i32(c(asm["var_phase"])),
                                      L.i32(c(asm["eq_differential"])), L.i32(c(asm["eq_phase"])),
                                      len(asm["bc_rows"]), L.i32(c(asm["bc_rows"])), L.f64(bcv)))
-        Mv = np.ascontiguousarray(asm["M"], dtype=np.float64)
-        Lv = np.ascontiguousarray(asm["L"], dtype=np.float64)
-        L.check(h, lib.sp_set_pencils(h, self.pid, 0, self.P, asm["n"], len(asm["indices"]),
-                                      L.i32(c(asm["indptr"])), L.i32(c(asm["indices"])), L.f64(Mv), L.f64(Lv)))
+        chunk = 4096                                   # pencils per sp_set_pencils call
+        for p0 in range(0, self.P, chunk):
+            p1 = min(self.P, p0 + chunk)
+            Mv, Lv = asm["values"](p0, p1)
+            L.check(h, lib.sp_set_pencils(h, self.pid, p0, p1 - p0, asm["n"], len(asm["indices"]),
+                                          L.i32(c(asm["indptr"])), L.i32(c(asm["indices"])), L.f64(Mv), L.f64(Lv)))
         self.set_bilinear(bilinear)
         self.dt = None
 
     def set_bilinear(self, terms):
-        ops = {"ID": L.SP_OP_ID, "DX": L.SP_OP_DX}
+        ops = {"ID": L.SP_OP_ID, "DX": L.SP_OP_DX, "DY": L.SP_OP_DY}
         eq = np.array([self.eq[t[0]] for t in terms], np.int32)
         coef = np.array([t[1] for t in terms], np.float64)
         oa = np.array([ops[t[2]] for t in terms], np.int32)
@@ -144,10 +160,14 @@ class TauSolver:
         if layout == "c":
             out = np.zeros((self.P, self.Nz), np.complex128)
         else:
-            out = np.zeros((self.Nz, self.Nx), np.float64)
+            out = np.zeros(self.grid_shape(), np.float64)
         L.check(h, L.lib().sp_get_field(h, self.pid, self.var[name], out.ctypes.data_as(ctypes.c_void_p), 0,
                                         layout.encode()))
         return out
+
+    def grid_shape(self, scale=(1, 1)):
+        g = lambda n: n * scale[0] // scale[1]
+        return (g(self.Nz), g(self.Nx)) if self.ndim == 2 else (g(self.Nz), g(self.Ny), g(self.Nx))
 
     def get_state(self):
         """State coefficients [var][p][m] in ``state_order``."""
@@ -163,13 +183,13 @@ class TauSolver:
         L.check(h, L.lib().sp_dz(h, self.pid, self.var[src], self.var[dst]))
 
     def transform(self, data, direction, scale=(1, 1)):
-        """direction -1: coefficients [f][p][m] -> grid [f][iz][ix]; +1: back."""
+        """direction -1: coefficients [f][p][m] -> grid [f][iz][ix] (3D:
+        [f][iz][iy][ix]); +1: back."""
         h = self.ctx.handle
         if direction < 0:
             inp = np.ascontiguousarray(data, np.complex128)
             nf = inp.shape[0]
-            ngx, ngz = self.Nx * scale[0] // scale[1], self.Nz * scale[0] // scale[1]
-            out = np.zeros((nf, ngz, ngx), np.float64)
+            out = np.zeros((nf,) + self.grid_shape(scale), np.float64)
         else:
             inp = np.ascontiguousarray(data, np.float64)
             nf = inp.shape[0]
@@ -213,6 +233,29 @@ class RBSolver(TauSolver):
         device), bz = dz b (device recurrence), all other fields zero."""
         z = rbmod.chebyshev_nodes(self.Nz)[:, None]
         b_grid = 1.0 - z + amplitude * noise * z * (1.0 - z)
+        zero = np.zeros((self.P, self.Nz), np.complex128)
+        for v in self.problem.variables:
+            self.set_field(v, zero)
+        self.set_field("b", b_grid, layout="g")
+        self.dz("b", "bz")
+
+
+class RB3DSolver(TauSolver):
+    """3D Rayleigh-Benard convection (b, p, u, v, w, bz, uz, vz, wz) on
+    Fourier x, Fourier y, Chebyshev z."""
+
+    def __init__(self, ctx, n_x, n_y, n_z, Ra, Pr=1.0, L_x=4.0, L_y=4.0, scheme="RK222", precision="fp64",
+                 dealias=(3, 2)):
+        problem = rbmod.rb3d_pencil_problem(Ra, Pr)
+        super().__init__(ctx, problem, n_x, n_z, L_x, scheme=scheme, precision=precision, dealias=dealias,
+                         bilinear=rbmod.BILINEAR_TERMS_3D, n_y=n_y, L_y=L_y)
+        self.state_order = rbmod.VARIABLES_3D
+        self.Ra, self.Pr = Ra, Pr
+
+    def set_initial_state(self, noise, amplitude=1e-3):
+        """b = 1 - z + A xi z (1 - z) on the scale-1 grid (xi[z, y, x]), bz = dz b."""
+        z = rbmod.chebyshev_nodes(self.Nz)[:, None, None]
+        b_grid = 1.0 - z + amplitude * np.asarray(noise) * z * (1.0 - z)
         zero = np.zeros((self.P, self.Nz), np.complex128)
         for v in self.problem.variables:
             self.set_field(v, zero)

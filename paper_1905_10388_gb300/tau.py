@@ -274,13 +274,17 @@ class PencilProblem:
             idx = np.nonzero(mask)[0]
             maps.append(sps.csr_matrix((base[idx], (inv[idx], ent_key[idx])), shape=(nnz, len(keys))))
 
+        scale_re = np.ascontiguousarray(scale.real)
+        scale_im = np.ascontiguousarray(scale.imag)
+
         def pencil_values(p0, p1):
             out = []
             for A in maps:
-                X = (A @ scale[:, p0:p1]).T                        # [p1 - p0, nnz] complex
-                if np.abs(X.imag).max(initial=0) > 1e-14 * max(1.0, np.abs(X).max(initial=0)):
+                Xr = (A @ scale_re[:, p0:p1]).T                     # [p1 - p0, nnz]
+                Xi = A @ scale_im[:, p0:p1]
+                if np.abs(Xi).max(initial=0) > 1e-14 * max(1.0, np.abs(Xr).max(initial=0)):
                     raise ValueError("pencil is not real under the given phases")
-                out.append(np.ascontiguousarray(X.real))
+                out.append(np.ascontiguousarray(Xr))
             return tuple(out)
 
         col_map, row_map, bc_rows = self.layout(N)

@@ -62,6 +62,11 @@ def rb_noise(seed, n_z, n_x):
     return np.random.default_rng(seed).standard_normal((n_z, n_x))
 
 
+def rb_noise3(seed, n_z, n_y, n_x):
+    """xi[z, y, x]: i.i.d. standard normals on the 3D scale-1 grid."""
+    return np.random.default_rng(seed).standard_normal((n_z, n_y, n_x))
+
+
 def batched_workloads(count=64, seed=7):
     """Uneven batch: N_x from {64..512}, N_z from {32..256}, Ra log-uniform."""
     rng = np.random.default_rng(seed)

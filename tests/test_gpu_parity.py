@@ -254,3 +254,30 @@ def test_bad_sizes_rejected(ctx):
     with pytest.raises(_lib.SpectauError) as e:
         RBSolver(ctx, 40, 16, 1e6)           # N_gx = 60 is not 2^k or 3 2^k
     assert e.value.status == _lib.SP_ERR_ARG
+
+
+@pytest.mark.parametrize("Nz", [16, 32])
+def test_wide_band_two_register_window(ctx, Nz):
+    """A row/variable order of the same RB pencils with kl + ku = 36 > 31
+    (the back substitution keeps two window registers per lane); at N_z = 32
+    the padded length 224 is not a multiple of the 64-row window."""
+    from paper_1905_10388_gb300 import rb as prb
+    from paper_1905_10388_gb300.solver import TauSolver
+    Nx, Ra, dt, nsteps = 32, 1e5, 2e-3, 3
+    V = ("w", "wz", "uz", "u", "b", "bz", "p")
+    E = ("uz_def", "wz_def", "bz_def", "u", "w", "b", "div")
+    s = TauSolver(ctx, prb.rb_pencil_problem(Ra, variables=V, row_order=E), Nx, Nz, 4.0, scheme="RK222",
+                  bilinear=prb.BILINEAR_TERMS)
+    s.state_order = prb.VARIABLES
+    assert sum(s.band()[1:]) > 31
+    s.factor(dt)
+    xi = si.rb_noise(13, Nz, Nx)
+    z = prb.chebyshev_nodes(Nz)[:, None]
+    for v in s.problem.variables:
+        s.set_field(v, np.zeros((s.P, Nz), complex))
+    s.set_field("b", 1 - z + 1e-3 * xi * z * (1 - z), "g")
+    s.dz("b", "bz")
+    s.step(nsteps)
+    s.sync()
+    ref, floor = _reference(Nx, Nz, Ra, xi, "RK222", dt, nsteps)
+    _check(s.get_state(), ref, floor, 1e-12)

@@ -84,6 +84,29 @@ def test_assembler_matches_oracle_pencil(N, kx):
         assert np.abs(got[v] - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max()), v
 
 
+@pytest.mark.parametrize("k", [(0.0, 0.0), (1.5707963267948966, 0.0), (0.0, -3.14159265358979),
+                               (4.71238898038469, 1.5707963267948966)])
+def test_3d_assembler_matches_oracle_pencil(k):
+    from oracle import rb3d as orb3
+    N, Ra, Pr, a = 12, 1e5, 1.0, 3e-3
+    prob = prb.rb3d_pencil_problem(Ra, Pr)
+    asm = prob.build(N, (np.array([k[0]]), np.array([k[1]])))
+    n = asm["n"]
+    At = _csr_dense(asm["indptr"], asm["indices"], asm["M"][0] + a * asm["L"][0], n)
+    opr, _, _ = orb3.rb3d_problem(N, Ra, Pr)
+    M, L = opr.pencil_matrices(k)
+    rng = np.random.default_rng(5)
+    F = {e: rng.standard_normal(N) + 1j * rng.standard_normal(N) for e in ("b", "u", "v", "w")}
+    X_ref = np.linalg.solve((M + a * L).toarray(), opr.rhs_vector(F, k))
+    B = _place_rhs(asm, 0, F, [e.name for e in prob.equations])
+    x = np.linalg.solve(At, B.real) + 1j * np.linalg.solve(At, B.imag)
+    got = _unmap(asm, x, prob.variables)
+    for i, v in enumerate(orb3.RB3D_VARIABLES):
+        ref = X_ref[i * N:(i + 1) * N]
+        assert np.abs(got[v] - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max()), v
+    assert (asm["kl"], asm["ku"]) == (9, 29)
+
+
 def test_band_widths_of_rb_ordering():
     asm = prb.rb_pencil_problem(1e6).build(32, np.array([0.0, 1.0]))
     assert (asm["kl"], asm["ku"]) == (7, 22)
