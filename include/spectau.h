@@ -267,6 +267,19 @@ sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku);
  * their number.  Events are recorded on the context stream around each
  * launch. */
 sp_status sp_set_timing(sp_ctx* ctx, int problem, int max_launches);
+
+/* Choice of the substitution kernel of the pencil solves (Sec. "Matrix
+ * solvers"; the arithmetic is the same, the order of every FMA too, so both
+ * give identical results): SP_SOLVE_AUTO picks SP_SOLVE_LANES for problems
+ * with at least 4096 pencils when (kl, kl + ku) is (9, 38) or (7, 29), else
+ * SP_SOLVE_WINDOW.  WINDOW: one warp per pencil and real/imaginary part,
+ * the band across the lanes (latency-bound few-pencil problems).  LANES:
+ * one lane per pencil and real/imaginary part (throughput-bound
+ * many-pencil problems; SP_ERR_ARG for other band widths).  Must precede
+ * the first call that moves the problem to the device (sp_factor,
+ * sp_set_field, sp_transform): SP_ERR_STATE afterwards. */
+typedef enum { SP_SOLVE_AUTO = 0, SP_SOLVE_WINDOW = 1, SP_SOLVE_LANES = 2 } sp_solve_kernel;
+sp_status sp_set_solve_kernel(sp_ctx* ctx, int problem, int kind);
 sp_status sp_last_solve_time(sp_ctx* ctx, int problem, double* ms_per_launch, int* launches);
 
 /* Backward transform without any device allocation.  The paper has no

@@ -21,6 +21,8 @@ SP_RK222, SP_SBDF1, SP_SBDF2, SP_RK111 = 0, 1, 2, 3
 SCHEMES = {"RK222": SP_RK222, "SBDF1": SP_SBDF1, "SBDF2": SP_SBDF2, "RK111": SP_RK111}
 SP_PREC_FP64, SP_PREC_MIXED = 0, 1
 SP_OP_ID, SP_OP_DX, SP_OP_DY = 0, 1, 2
+SP_SOLVE_AUTO, SP_SOLVE_WINDOW, SP_SOLVE_LANES = 0, 1, 2
+SOLVE_KERNELS = {"auto": SP_SOLVE_AUTO, "window": SP_SOLVE_WINDOW, "lanes": SP_SOLVE_LANES}
 
 EXPORTS = (
     "sp_create", "sp_destroy", "sp_last_error", "sp_add_problem", "sp_set_layout",
@@ -28,7 +30,7 @@ EXPORTS = (
     "sp_dz", "sp_step", "sp_step_graph", "sp_sync_status", "sp_transform", "sp_eval_rhs",
     "sp_get_band", "sp_set_timing", "sp_last_solve_time", "sp_transform_backward_static",
     "sp_step_batched", "sp_batch_tile", "sp_adjoint_init", "sp_step_adjoint", "sp_transform_adjoint",
-    "sp_dz_adjoint", "sp_step_record",
+    "sp_dz_adjoint", "sp_step_record", "sp_set_solve_kernel",
 )
 
 
@@ -78,6 +80,7 @@ _SIGS = {
     "sp_adjoint_init": [P, I],
     "sp_step_adjoint": [P, I, D, P, I, P],
     "sp_step_record": [P, I, D, I, P],
+    "sp_set_solve_kernel": [P, I, I],
     "sp_transform_adjoint": [P, I, P, P, I, I, I, I, I],
     "sp_dz_adjoint": [P, I, P, P],
 }

@@ -114,6 +114,10 @@ struct Problem {
   double fac_dt = 0;
   bool factored = false;
   int npad = 0, lpad = 0, upad = 0;
+  // lane-per-pencil substitution (many pencils): its B~ / x~ / y buffers
+  bool lanes = false;
+  int solve_kind = SP_SOLVE_AUTO;
+  double2 *d_bg = nullptr, *d_xg = nullptr, *d_yg = nullptr;
   std::map<std::pair<int, int>, TransformPlan> plans;
   // stepping state
   int iteration = 0;
@@ -322,8 +326,22 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
   // SBDF2 keeps two factors (its SBDF1 start and the SBDF2 matrix); the
   // other schemes one
   const int nfactors = pr->scheme == SP_SBDF2 ? 2 : 1;
+  // thousands of pencils fill the GPU with one lane per right-hand side
+  pr->lanes = pr->solve_kind == SP_SOLVE_LANES ||
+              (pr->solve_kind == SP_SOLVE_AUTO && pr->P >= LANE_MIN_PENCILS && lanes_supported(pr->kl, kuu));
+  const size_t ngroups = (pr->P + LANE_GROUP - 1) / LANE_GROUP;
+  if (pr->lanes) {
+    CK(dalloc(&pr->d_bg, (size_t)pr->P * pr->n));
+    CK(dalloc(&pr->d_xg, (size_t)pr->P * pr->n));
+    CK(dalloc(&pr->d_yg, ngroups * LANE_GROUP * pr->n));
+  }
   for (int fi = 0; fi < nfactors; ++fi) {
     BandFactor& f = pr->fac[fi];
+    if (pr->lanes) {
+      CK(dalloc(&f.Lg, ngroups * pr->n * pr->kl * LANE_GROUP));
+      CK(dalloc(&f.Ug, ngroups * pr->n * (kuu + 1) * LANE_GROUP));
+      CK(dalloc(&f.pg, ngroups * pr->n * LANE_GROUP));
+    }
     CK(dalloc(&f.L, (size_t)pr->P * pr->npad * pr->lpad));
     CK(dalloc(&f.piv, (size_t)pr->P * pr->npad));
     CK(dalloc(&f.U, (size_t)pr->P * pr->npad * pr->upad));
@@ -345,7 +363,8 @@ void free_problem(Problem* pr) {
   for (auto b : pr->d_LX) F(b);
   for (auto b : pr->d_Fc) F(b);
   F(pr->d_gz); F(pr->d_gy); F(pr->d_h);
-  for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); F(f.rd); }
+  for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); F(f.rd); F(f.Lg); F(f.Ug); F(f.pg); }
+  F(pr->d_bg); F(pr->d_xg); F(pr->d_yg);
   F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd);
   F(pr->d_indptrT); F(pr->d_indicesT); F(pr->d_MvT); F(pr->d_LvT);
   F(pr->d_mu[0]); F(pr->d_mu[1]); F(pr->d_LTmu); F(pr->d_MTmu); F(pr->d_JF); F(pr->d_lamx);
@@ -434,6 +453,7 @@ SolveArgs base_args(Problem* pr, sp_ctx* ctx, int fac) {
   a.bc_rows = pr->d_bc_rows; a.bc_values = pr->d_bc_values;
   a.status = ctx->d_status;
   a.xc32_out = pr->d_Xc32;   // null unless mixed precision
+  a.Lg = pr->fac[fac].Lg; a.Ug = pr->fac[fac].Ug; a.pg = pr->fac[fac].pg;   // null unless lane mode
   return a;
 }
 
@@ -450,7 +470,18 @@ void set_ep_L(Problem* pr, SolveArgs& a) {
 sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
   const bool t = pr->timing && pr->ev_used + 2 <= pr->ev.size();
   if (t) CK(cudaEventRecord(pr->ev[pr->ev_used], s));
-  CK(launch_pencil_solve(s, a));
+  if (a.Lg && pr->lanes) {
+    // assembly -> lane-per-pencil substitution -> epilogue
+    SolveArgs a1 = a;
+    a1.mode = 1; a1.bg = pr->d_bg;
+    CK(launch_pencil_solve(s, a1));
+    CK(launch_pencil_lanes(s, pr->P, pr->n, a.kl, a.kuu, a.Lg, a.Ug, a.pg, pr->d_bg, pr->d_yg, pr->d_xg));
+    SolveArgs a2 = a;
+    a2.mode = 2; a2.xg = pr->d_xg;
+    CK(launch_pencil_solve(s, a2));
+  } else {
+    CK(launch_pencil_solve(s, a));
+  }
   if (t) {
     CK(cudaEventRecord(pr->ev[pr->ev_used + 1], s));
     pr->ev_used += 2;
@@ -595,6 +626,7 @@ SolveArgs transposed_args(Problem* pr, sp_ctx* ctx) {
   a.Lf = pr->facT.L; a.piv = pr->facT.piv; a.Uf = pr->facT.U; a.rd = pr->facT.rd;
   a.n_nl = 0; a.nbc = 0; a.bc_coef = 0.0;
   a.xc32_out = nullptr;
+  a.Lg = nullptr; a.Ug = nullptr; a.pg = nullptr;
   return a;
 }
 
@@ -993,6 +1025,9 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
     cudaError_t e = launch_band_factor(ctx->stream, pr->P, pr->n, (int)pr->nnz, pr->kl, pr->ku, pr->d_indptr,
                                        pr->d_indices, pr->d_Mv, pr->d_Lv, ab[f][0], ab[f][1], work, pr->fac[f],
                                        pr->npad, pr->lpad, pr->upad, ctx->d_status);
+    if (e == cudaSuccess && pr->lanes)
+      e = launch_factor_relayout(ctx->stream, pr->P, pr->n, pr->npad, pr->kl, pr->kl + pr->ku, pr->lpad, pr->upad,
+                                 pr->fac[f]);
     if (e != cudaSuccess) { cudaFree(work); CK(e); }
   }
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -1649,6 +1684,20 @@ sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku) {
   if (n) *n = pr->n;
   if (kl) *kl = pr->kl;
   if (ku) *ku = pr->ku;
+  return SP_OK;
+}
+
+sp_status sp_set_solve_kernel(sp_ctx* ctx, int problem, int kind) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (kind != SP_SOLVE_AUTO && kind != SP_SOLVE_WINDOW && kind != SP_SOLVE_LANES)
+    return fail(ctx, SP_ERR_ARG, "unknown solve kernel %d", kind);
+  if (pr->uploaded) return fail(ctx, SP_ERR_STATE, "the solve kernel is fixed once the problem is on the device");
+  if (kind == SP_SOLVE_LANES && (pr->nnz < 0 || !lanes_supported(pr->kl, pr->kl + pr->ku)))
+    return fail(ctx, SP_ERR_ARG, "no lane-per-pencil substitution for kl = %d, kl + ku = %d (set the pencils first)",
+                pr->kl, pr->kl + pr->ku);
+  pr->solve_kind = kind;
   return SP_OK;
 }
 

@@ -265,21 +265,29 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   };
 
   if (tid == 0 && active) {
-    for (int s = 0; s < SOLVE_RING; ++s) {
-      mbar_init(&sm.barL[s], 1);
-      mbar_init(&sm.barU[s], 1);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sm.abort_flag = 0;
-    // the factor does not depend on the prologue: start streaming now
-    for (int c = 0; c < min(SOLVE_RING, nchunks); ++c) issue_L(c);
-    for (int k = 0; k < min(SOLVE_RING, nchunks); ++k) issue_U(k);
+    if (a.mode == 0) {
+      for (int s = 0; s < SOLVE_RING; ++s) {
+        mbar_init(&sm.barL[s], 1);
+        mbar_init(&sm.barU[s], 1);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      // the factor does not depend on the prologue: start streaming now
+      for (int c = 0; c < min(SOLVE_RING, nchunks); ++c) issue_L(c);
+      for (int k = 0; k < min(SOLVE_RING, nchunks); ++k) issue_U(k);
+    }
   }
 
   // ---- prologue: B~ = linear combination of stored vectors, one matvec,
   //      left-preconditioned F~ (T-to-U conversion, tau rows dropped) and
   //      boundary values
   const size_t prow = (size_t)pp * n;
+  const int Nz = a.Nz;
+  if (a.mode == 2) {
+    // epilogue only: X~ (already divided by U_jj) from the substitution kernel
+    for (int r = tid; active && r < n; r += nt) sm.B[r] = a.xg[prow + r];
+    __syncthreads();
+  } else {
   for (int r = tid; active && r < n; r += nt) {
     double2 acc = make_double2(0.0, 0.0);
     for (int k = 0; k < a.nvec; ++k) {
@@ -304,7 +312,6 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   }
   for (int r = n + tid; active && r < a.npad + 64; r += nt) sm.B[r] = make_double2(0.0, 0.0);
   __syncthreads();
-  const int Nz = a.Nz;
   for (int idx = tid; active && idx < a.n_nl * Nz; idx += nt) {
     const int sl = idx / Nz, m = idx - sl * Nz;
     const int e = a.nl_eq[sl];
@@ -345,6 +352,12 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     sm.B[row] = b;
   }
   __syncthreads();
+  }
+  if (a.mode == 1) {
+    // prologue only: hand B~ to the substitution kernel
+    for (int r = tid; active && r < n; r += nt) a.bg[prow + r] = sm.B[r];
+    return;
+  }
 
   // ---- substitution, over the padded columns [0, npad): padding columns
   //      carry zero factors, so they pass zeros through.  Warp 0 solves the
@@ -361,7 +374,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   //      Both warps read each ring slot; named barrier 1 (64 threads) at the
   //      top of every chunk both agrees on a timed-out wait and frees the
   //      previous slot for refilling.
-  if (active && tid < 64) {
+  if (a.mode == 0 && active && tid < 64) {
     const int lane = tid & 31;
     const int comp = tid >> 5;                 // 0: real part, 1: imaginary part
     double* Bd = reinterpret_cast<double*>(sm.B) + comp;   // element j at Bd[2 j]
@@ -475,7 +488,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   //      coefficients, optional M~ X~
   {
     const double* rdp = a.rd + (size_t)pp * a.npad;
-    for (int r = tid; work && r < n; r += nt) {
+    for (int r = tid; work && a.mode == 0 && r < n; r += nt) {
       const double q = rdp[r];
       const double2 b = sm.B[r];
       sm.B[r] = make_double2(b.x * q, b.y * q);
@@ -565,6 +578,112 @@ cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a) {
     cudaFuncSetAttribute(k_pencil_solve<2, PPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_pencil_solve<2, PPC><<<grid, 128, smem, s>>>(a);
   }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Lane-per-pencil substitution for problems with many pencils (3D): the
+// window kernel above keeps one pencil's band across a warp's lanes, which
+// leaves most lanes idle in the forward pass (kl of 32) and, with two window
+// registers, in the back substitution (kl + ku of 64); it is the right shape
+// when a few hundred dependent chains cannot fill the GPU anyway.  With tens
+// of thousands of pencils the FP64 pipe is the limit instead, so here each
+// lane carries one real right-hand side (lane 2i: real part, 2i + 1:
+// imaginary part of pencil i of a group of LANE_GROUP) through the whole
+// substitution with its window of pending rows in registers; every warp
+// FMA does useful work on all 32 lanes.  The factor is stored interleaved
+// by pencil within a group, so a warp's load of one factor entry reads 16
+// consecutive doubles.
+// ---------------------------------------------------------------------------
+template <int KL, int KUU>
+__global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, const double* __restrict__ Lg,
+                                                      const double* __restrict__ Ug,
+                                                      const uint8_t* __restrict__ pg,
+                                                      const double2* __restrict__ b, double2* __restrict__ y,
+                                                      double2* __restrict__ x) {
+  const int gl = blockIdx.x * blockDim.x + threadIdx.x;
+  const int comp = gl & 1;
+  const int pen = gl >> 1;                       // pencil
+  if (pen >= P) return;
+  const int g = pen / LANE_GROUP, i = pen - g * LANE_GROUP;
+  const double* bp = reinterpret_cast<const double*>(b + (size_t)pen * n) + comp;
+  double* yp = reinterpret_cast<double*>(y + (size_t)g * n * LANE_GROUP + i) + comp;   // row j at yp[2 j LANE_GROUP]
+  const size_t gn = (size_t)g * n;
+  // forward: row interchanges and unit-lower multipliers; win[t] = row j + t
+  double win[KL + 1];
+#pragma unroll
+  for (int t = 0; t <= KL; ++t) win[t] = (t < n) ? bp[2 * t] : 0.0;
+  for (int j = 0; j < n; ++j) {
+    const int off = pg[(gn + j) * LANE_GROUP + i];
+    const double* Lrow = Lg + (gn + j) * KL * LANE_GROUP + i;
+    double piv_val = win[0];
+#pragma unroll
+    for (int t = 1; t <= KL; ++t) piv_val = (off == t) ? win[t] : piv_val;
+#pragma unroll
+    for (int t = 1; t <= KL; ++t) win[t] = (off == t) ? win[0] : win[t];
+    const double yj = piv_val;
+    yp[(size_t)2 * j * LANE_GROUP] = yj;
+#pragma unroll
+    for (int t = 1; t <= KL; ++t) win[t] = fma(-Lrow[(t - 1) * LANE_GROUP], yj, win[t]);
+#pragma unroll
+    for (int t = 0; t < KL; ++t) win[t] = win[t + 1];
+    win[KL] = (j + KL + 1 < n) ? bp[2 * (j + KL + 1)] : 0.0;
+  }
+  // back substitution with the scaled columns U_{j-t,j} / U_jj; the rows
+  // of y this lane wrote are read back by this lane only
+  double w[KUU + 1];                             // w[t] = pending row j - t
+#pragma unroll
+  for (int t = 0; t <= KUU; ++t) w[t] = (n - 1 - t >= 0) ? yp[(size_t)2 * (n - 1 - t) * LANE_GROUP] : 0.0;
+  double* xp = reinterpret_cast<double*>(x + (size_t)pen * n) + comp;
+  for (int j = n - 1; j >= 0; --j) {
+    const double* Urow = Ug + (gn + j) * (KUU + 1) * LANE_GROUP + i;
+    const double bj = w[0];
+    xp[2 * j] = bj * Urow[0];
+#pragma unroll
+    for (int t = 1; t <= KUU; ++t) w[t] = fma(-Urow[t * LANE_GROUP], bj, w[t]);
+#pragma unroll
+    for (int t = 0; t < KUU; ++t) w[t] = w[t + 1];
+    w[KUU] = (j - KUU - 1 >= 0) ? yp[(size_t)2 * (j - KUU - 1) * LANE_GROUP] : 0.0;
+  }
+}
+
+// The (kl, kl + ku) pairs compiled: the 3D Rayleigh-Benard pencil (9, 38)
+// and the 2D one (7, 29).
+bool lanes_supported(int kl, int kuu) { return (kl == 9 && kuu == 38) || (kl == 7 && kuu == 29); }
+
+cudaError_t launch_pencil_lanes(cudaStream_t s, int P, int n, int kl, int kuu, const double* Lg, const double* Ug,
+                                const uint8_t* pg, const double2* b, double2* y, double2* x) {
+  const int threads = 2 * P;
+  const int grid = (threads + 127) / 128;
+  if (kl == 9 && kuu == 38)
+    k_pencil_lanes<9, 38><<<grid, 128, 0, s>>>(P, n, Lg, Ug, pg, b, y, x);
+  else if (kl == 7 && kuu == 29)
+    k_pencil_lanes<7, 29><<<grid, 128, 0, s>>>(P, n, Lg, Ug, pg, b, y, x);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// Copy a factor into the lane-interleaved layout (one thread per pencil row).
+__global__ void k_factor_relayout(int P, int n, int npad, int kl, int kuu, int lpad, int upad,
+                                  const double* __restrict__ L, const uint8_t* __restrict__ piv,
+                                  const double* __restrict__ U, double* __restrict__ Lg, double* __restrict__ Ug,
+                                  uint8_t* __restrict__ pg) {
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)P * n) return;
+  const int p = (int)(idx / n), j = (int)(idx - (size_t)p * n);
+  const int g = p / LANE_GROUP, i = p - g * LANE_GROUP;
+  const size_t row = (size_t)g * n + j;
+  for (int t = 0; t < kl; ++t) Lg[(row * kl + t) * LANE_GROUP + i] = L[((size_t)p * npad + j) * lpad + t];
+  for (int t = 0; t <= kuu; ++t) Ug[(row * (kuu + 1) + t) * LANE_GROUP + i] = U[((size_t)p * npad + j) * upad + t];
+  pg[row * LANE_GROUP + i] = piv[(size_t)p * npad + j];
+}
+
+cudaError_t launch_factor_relayout(cudaStream_t s, int P, int n, int npad, int kl, int kuu, int lpad, int upad,
+                                   const BandFactor& f) {
+  const size_t total = (size_t)P * n;
+  k_factor_relayout<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P, n, npad, kl, kuu, lpad, upad, f.L, f.piv,
+                                                                   f.U, f.Lg, f.Ug, f.pg);
   return cudaGetLastError();
 }
 

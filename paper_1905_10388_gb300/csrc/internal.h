@@ -23,7 +23,18 @@ struct BandFactor {
   uint8_t* piv = nullptr;       // [P][npad]        pivot row offset (piv - j) in [0, kl]
   double* U = nullptr;          // [P][npad][upad]  t=0: 1/U_jj, t>=1: U_{j-t,j}/U_jj
   double* rd = nullptr;         // [P][npad]        1/U_jj (0 on padding columns)
+  // lane-interleaved copies for k_pencil_lanes (groups of LANE_GROUP pencils):
+  double* Lg = nullptr;         // [G][n][kl][16]
+  double* Ug = nullptr;         // [G][n][kl+ku+1][16]  t=0: 1/U_jj
+  uint8_t* pg = nullptr;        // [G][n][16]
 };
+
+// Pencils per warp in the lane-per-pencil substitution (two lanes each:
+// real and imaginary part).
+constexpr int LANE_GROUP = 16;
+// Problems with at least this many pencils use the lane-per-pencil
+// substitution (2 P lanes = P / 16 warps: several per SM).
+constexpr int LANE_MIN_PENCILS = 4096;
 
 // Up to four device vectors with coefficients, passed to kernels by value.
 struct VecList4 {
@@ -71,6 +82,13 @@ struct SolveArgs {
   const int32_t* nl_eq; int n_nl;        // equation index of each nonlinear slot
   const int32_t* bc_rows; const double2* bc_values;
   DevStatus* status;
+  // mode 0: assembly, substitution and epilogue in one kernel; 1: assembly
+  // only, B~ to bg [p][n]; 2: epilogue only, from xg [p][n] (x~ = y / U_jj)
+  // (the substitution then runs in k_pencil_lanes)
+  int mode;
+  double2* bg; const double2* xg;
+  // factor in the lane-interleaved layout (null: not available)
+  const double* Lg; const double* Ug; const uint8_t* pg;
 };
 
 // Transform arguments.
@@ -126,6 +144,15 @@ cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a);
 size_t pencil_solve_smem(int npad, int lpad, int upad);
 cudaError_t launch_pencil_solve_batched(cudaStream_t s, const SolveArgs* args, const int4* work, int nwork,
                                         int max_kuu, size_t smem);
+// Lane-per-pencil substitution (many-pencil problems): forward and back
+// substitution of P pencils, B~ [p][n] in, x~ = y / U_jj [p][n] out, y scratch
+// [G][n][16] complex.  Returns cudaErrorInvalidValue when (kl, kl + ku) has
+// no compiled instance (lanes_supported).
+bool lanes_supported(int kl, int kuu);
+cudaError_t launch_pencil_lanes(cudaStream_t s, int P, int n, int kl, int kuu, const double* Lg, const double* Ug,
+                                const uint8_t* pg, const double2* b, double2* y, double2* x);
+cudaError_t launch_factor_relayout(cudaStream_t s, int P, int n, int npad, int kl, int kuu, int lpad, int upad,
+                                   const BandFactor& f);
 cudaError_t launch_coef_to_solve(cudaStream_t s, int P, int S, int Nz, const double2* xc,
                                  double2* xt, const int32_t* col_map, const int32_t* var_recombine,
                                  const int32_t* var_phase);

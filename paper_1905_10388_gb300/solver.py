@@ -105,6 +105,11 @@ class TauSolver:
         self.set_bilinear(bilinear)
         self.dt = None
 
+    def set_solve_kernel(self, kind):
+        """'auto', 'window' or 'lanes' (before the problem moves to the device)."""
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_set_solve_kernel(h, self.pid, L.SOLVE_KERNELS[kind]))
+
     def set_bilinear(self, terms):
         ops = {"ID": L.SP_OP_ID, "DX": L.SP_OP_DX, "DY": L.SP_OP_DY}
         eq = np.array([self.eq[t[0]] for t in terms], np.int32)

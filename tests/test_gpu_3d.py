@@ -167,3 +167,30 @@ def test_full_size_one_step_properties(ctx):
         iz, iy, ix = rng.integers(N), rng.integers(w.n_y), rng.integers(w.n_x)
         ref = _coef_value(X[var["b"]], s, w.L_x * ix / w.n_x, w.L_y * iy / w.n_y, zs[iz])
         assert abs(g[iz, iy, ix] - ref) < 1e-12 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("case", ["3d-RK222", "3d-SBDF2", "2d-RK222", "2d-SBDF2-mixed"])
+def test_lane_substitution_equals_window(ctx, case):
+    """The lane-per-pencil substitution (one lane per pencil and real or
+    imaginary part) performs the window kernel's FMAs in the same order, so
+    states after several steps agree bit for bit."""
+    from paper_1905_10388_gb300.solver import RBSolver
+    dim, scheme = case.split("-")[:2]
+    prec = "mixed" if case.endswith("mixed") else "fp64"
+    out = []
+    for kind in ("window", "lanes"):
+        if dim == "3d":
+            s = RB3DSolver(ctx, 16, 16, 16, 1e6, scheme=scheme, precision=prec)
+            s.set_solve_kernel(kind)
+            s.factor(2e-3)
+            s.set_initial_state(si.rb_noise3(11, 16, 16, 16) * 30.0)
+        else:
+            s = RBSolver(ctx, 64, 32, 1e6, scheme=scheme, precision=prec)
+            s.set_solve_kernel(kind)
+            s.factor(1e-3)
+            s.set_initial_state(si.rb_noise(5, 32, 64) * 30.0)
+        s.step(4)
+        s.sync()
+        out.append(s.get_state())
+    assert np.isfinite(out[0]).all()
+    assert np.array_equal(out[0], out[1])
