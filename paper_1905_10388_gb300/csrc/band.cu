@@ -218,8 +218,12 @@ __host__ __device__ inline size_t solve_smem_bytes(int npad, int lpad, int upad)
 // PPC pencils per CTA of 128 threads (1 or 2); with PPC = 2 threads
 // [0, 64) serve pencil 2b and [64, 128) pencil 2b + 1, each half with its own
 // shared-memory region.
-template <int RU, int PPC>
+template <int RU, int PPC, int MODE = -1>
 __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block, unsigned char* smem_raw) {
+  // MODE >= 0 fixes the stage at compile time (assembly-only and
+  // epilogue-only kernels carry neither the factor ring nor the substitution)
+  const int mode = MODE >= 0 ? MODE : a.mode;
+  const int lp = mode == 0 ? a.lpad : 0, up = mode == 0 ? a.upad : 0;
   const int half = (PPC == 2) ? (threadIdx.x >> 6) : 0;
   const int p = block * PPC + half;
   const bool active = p < a.P;
@@ -228,13 +232,13 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   const int n = a.n;
   SolveSmem sm;
   {
-    size_t off = (size_t)half * solve_smem_bytes(a.npad, a.lpad, a.upad);
+    size_t off = (size_t)half * solve_smem_bytes(a.npad, lp, up);
     sm.B = reinterpret_cast<double2*>(smem_raw + off);
     off += align_up((size_t)(a.npad + 64) * 16, 128);
     sm.Lring = reinterpret_cast<double*>(smem_raw + off);
-    off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK * a.lpad * 8, 128);
+    off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK * lp * 8, 128);
     sm.Uring = reinterpret_cast<double*>(smem_raw + off);
-    off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK * a.upad * 8, 128);
+    off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK * up * 8, 128);
     sm.Pring = reinterpret_cast<uint8_t*>(smem_raw + off);
     off += align_up((size_t)SOLVE_RING * SOLVE_CHUNK, 128);
     sm.barL = reinterpret_cast<uint64_t*>(smem_raw + off);
@@ -266,7 +270,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
 
   if (tid == 0 && active) {
     *sm.abort_flag = 0;
-    if (a.mode == 0) {
+    if (mode == 0) {
       for (int s = 0; s < SOLVE_RING; ++s) {
         mbar_init(&sm.barL[s], 1);
         mbar_init(&sm.barU[s], 1);
@@ -283,7 +287,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   //      boundary values
   const size_t prow = (size_t)pp * n;
   const int Nz = a.Nz;
-  if (a.mode == 2) {
+  if (mode == 2) {
     // epilogue only: X~ (already divided by U_jj) from the substitution kernel
     for (int r = tid; active && r < n; r += nt) sm.B[r] = a.xg[prow + r];
     __syncthreads();
@@ -353,7 +357,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   }
   __syncthreads();
   }
-  if (a.mode == 1) {
+  if (mode == 1) {
     // prologue only: hand B~ to the substitution kernel
     for (int r = tid; active && r < n; r += nt) a.bg[prow + r] = sm.B[r];
     return;
@@ -374,7 +378,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   //      Both warps read each ring slot; named barrier 1 (64 threads) at the
   //      top of every chunk both agrees on a timed-out wait and frees the
   //      previous slot for refilling.
-  if (a.mode == 0 && active && tid < 64) {
+  if (mode == 0 && active && tid < 64) {
     const int lane = tid & 31;
     const int comp = tid >> 5;                 // 0: real part, 1: imaginary part
     double* Bd = reinterpret_cast<double*>(sm.B) + comp;   // element j at Bd[2 j]
@@ -488,7 +492,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   //      coefficients, optional M~ X~
   {
     const double* rdp = a.rd + (size_t)pp * a.npad;
-    for (int r = tid; work && a.mode == 0 && r < n; r += nt) {
+    for (int r = tid; work && mode == 0 && r < n; r += nt) {
       const double q = rdp[r];
       const double2 b = sm.B[r];
       sm.B[r] = make_double2(b.x * q, b.y * q);
@@ -542,6 +546,14 @@ __global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
   pencil_solve_body<RU, PPC>(a, blockIdx.x, smem_raw);
 }
 
+// right-hand-side assembly only (MODE 1) or epilogue only (MODE 2), around
+// k_pencil_lanes: shared memory for B~ alone, several CTAs per SM
+template <int MODE>
+__global__ void __launch_bounds__(128, 6) k_pencil_stage(SolveArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  pencil_solve_body<1, 1, MODE>(a, blockIdx.x, smem_raw);
+}
+
 // a batch of problems: work item (problem, pencil) per CTA
 template <int RU>
 __global__ void __launch_bounds__(128, 1) k_pencil_solve_batched(const SolveArgs* __restrict__ args,
@@ -567,6 +579,18 @@ cudaError_t launch_pencil_solve_batched(cudaStream_t s, const SolveArgs* args, c
 }
 
 cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a) {
+  if (a.mode == 1 || a.mode == 2) {
+    const size_t smem = solve_smem_bytes(a.npad, 0, 0);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    if (a.mode == 1) {
+      cudaFuncSetAttribute(k_pencil_stage<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_pencil_stage<1><<<a.P, 128, smem, s>>>(a);
+    } else {
+      cudaFuncSetAttribute(k_pencil_stage<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_pencil_stage<2><<<a.P, 128, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
   constexpr int PPC = 1;
   const size_t smem = PPC * solve_smem_bytes(a.npad, a.lpad, a.upad);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;

@@ -32,8 +32,8 @@ __device__ __forceinline__ void load_twiddles(C<T>* dst, const C<T>* __restrict_
 
 // One radix-R Stockham pass (R = 2, 3 or 4) over nb sequences.  Ns is
 // 2^ns_log2 or 3 * 2^ns_log2 (ns_has3); Q = N / R.  Index arithmetic avoids
-// run-time integer division: the sequence loop is outermost and j / Ns,
-// j mod Ns use shifts and a division by the constant 3.
+// run-time integer division: j / Ns and j mod Ns use shifts and a division
+// by the constant 3; the sequence index comes from one FP32 multiply.
 template <typename T, int R>
 __device__ __forceinline__ void stockham_pass(const C<T>* __restrict__ x, C<T>* __restrict__ y, int N, int Ns,
                                               int ns_log2, bool ns_has3, const C<T>* __restrict__ tw, int sign,
@@ -45,10 +45,16 @@ __device__ __forceinline__ void stockham_pass(const C<T>* __restrict__ x, C<T>* 
     w1 = tw_get<T>(tw, N / 3, sign);
     w2 = tw_get<T>(tw, 2 * (N / 3), sign);
   }
-  for (int b = 0; b < nb; ++b) {
+  // butterflies of all nb sequences share one thread loop; the sequence of
+  // butterfly idx is floor((idx + 1/2) / Q), exact in FP32 for idx < 2^20
+  const float invQ = 1.0f / (float)Q;
+  const int total = nb * Q;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int b = (nb == 1) ? 0 : __float2int_rd(((float)idx + 0.5f) * invQ);
+    const int j = idx - b * Q;
     const C<T>* xb = x + b * N;
     C<T>* yb = y + b * N;
-    for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+    {
       int jq = j >> ns_log2;                       // j / Ns
       if (ns_has3) jq /= 3;
       const int k = j - jq * Ns;                   // j mod Ns
