@@ -341,6 +341,7 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
       CK(dalloc(&f.Lg, ngroups * pr->n * pr->kl * LANE_GROUP));
       CK(dalloc(&f.Ug, ngroups * pr->n * (kuu + 1) * LANE_GROUP));
       CK(dalloc(&f.pg, ngroups * pr->n * LANE_GROUP));
+      CK(dalloc(&f.umask, (size_t)pr->n));
     }
     CK(dalloc(&f.L, (size_t)pr->P * pr->npad * pr->lpad));
     CK(dalloc(&f.piv, (size_t)pr->P * pr->npad));
@@ -363,7 +364,7 @@ void free_problem(Problem* pr) {
   for (auto b : pr->d_LX) F(b);
   for (auto b : pr->d_Fc) F(b);
   F(pr->d_gz); F(pr->d_gy); F(pr->d_h);
-  for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); F(f.rd); F(f.Lg); F(f.Ug); F(f.pg); }
+  for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); F(f.rd); F(f.Lg); F(f.Ug); F(f.pg); F(f.umask); }
   F(pr->d_bg); F(pr->d_xg); F(pr->d_yg);
   F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd);
   F(pr->d_indptrT); F(pr->d_indicesT); F(pr->d_MvT); F(pr->d_LvT);
@@ -454,6 +455,7 @@ SolveArgs base_args(Problem* pr, sp_ctx* ctx, int fac) {
   a.status = ctx->d_status;
   a.xc32_out = pr->d_Xc32;   // null unless mixed precision
   a.Lg = pr->fac[fac].Lg; a.Ug = pr->fac[fac].Ug; a.pg = pr->fac[fac].pg;   // null unless lane mode
+  a.umask = pr->fac[fac].umask;
   return a;
 }
 
@@ -475,7 +477,7 @@ sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
     SolveArgs a1 = a;
     a1.mode = 1; a1.bg = pr->d_bg;
     CK(launch_pencil_solve(s, a1));
-    CK(launch_pencil_lanes(s, pr->P, pr->n, a.kl, a.kuu, a.Lg, a.Ug, a.pg, pr->d_bg, pr->d_yg, pr->d_xg));
+    CK(launch_pencil_lanes(s, pr->P, pr->n, a.kl, a.kuu, a.Lg, a.Ug, a.pg, a.umask, pr->d_bg, pr->d_yg, pr->d_xg));
     SolveArgs a2 = a;
     a2.mode = 2; a2.xg = pr->d_xg;
     CK(launch_pencil_solve(s, a2));
@@ -626,7 +628,7 @@ SolveArgs transposed_args(Problem* pr, sp_ctx* ctx) {
   a.Lf = pr->facT.L; a.piv = pr->facT.piv; a.Uf = pr->facT.U; a.rd = pr->facT.rd;
   a.n_nl = 0; a.nbc = 0; a.bc_coef = 0.0;
   a.xc32_out = nullptr;
-  a.Lg = nullptr; a.Ug = nullptr; a.pg = nullptr;
+  a.Lg = nullptr; a.Ug = nullptr; a.pg = nullptr; a.umask = nullptr;
   return a;
 }
 
@@ -1028,6 +1030,11 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
     if (e == cudaSuccess && pr->lanes)
       e = launch_factor_relayout(ctx->stream, pr->P, pr->n, pr->npad, pr->kl, pr->kl + pr->ku, pr->lpad, pr->upad,
                                  pr->fac[f]);
+    if (e == cudaSuccess && pr->lanes)
+      e = cudaMemsetAsync(pr->fac[f].umask, 0, (size_t)pr->n * sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess && pr->lanes)
+      e = launch_u_mask(ctx->stream, pr->P, pr->n, pr->npad, pr->kl + pr->ku, pr->upad, pr->fac[f].U,
+                        pr->fac[f].umask);
     if (e != cudaSuccess) { cudaFree(work); CK(e); }
   }
   cudaError_t e = cudaStreamSynchronize(ctx->stream);

@@ -619,10 +619,17 @@ cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a) {
 // by pencil within a group, so a warp's load of one factor entry reads 16
 // consecutive doubles.
 // ---------------------------------------------------------------------------
+// L1 prefetch of the line holding p
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+constexpr int LANE_AHEAD = 8;      // rows prefetched ahead
+
 template <int KL, int KUU>
 __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, const double* __restrict__ Lg,
                                                       const double* __restrict__ Ug,
                                                       const uint8_t* __restrict__ pg,
+                                                      const unsigned long long* __restrict__ umask,
                                                       const double2* __restrict__ b, double2* __restrict__ y,
                                                       double2* __restrict__ x) {
   const int gl = blockIdx.x * blockDim.x + threadIdx.x;
@@ -637,7 +644,16 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, const double
   double win[KL + 1];
 #pragma unroll
   for (int t = 0; t <= KL; ++t) win[t] = (t < n) ? bp[2 * t] : 0.0;
+  const int lane = threadIdx.x & 31;
   for (int j = 0; j < n; ++j) {
+    // a lane serves one dependent chain, so few warps share an SM: pull the
+    // rows LANE_AHEAD steps ahead into L1 (the warp's lanes split the lines)
+    if (j + LANE_AHEAD < n) {
+      const size_t ra = gn + j + LANE_AHEAD;
+      if (lane < KL) prefetch_l1(Lg + (ra * KL + lane) * LANE_GROUP);
+      else if (lane == KL && ((j + LANE_AHEAD) & 7) == 0) prefetch_l1(pg + ra * LANE_GROUP);
+      if (((j + LANE_AHEAD) & 1) == 0 && j + LANE_AHEAD + KL + 1 < n) prefetch_l1(bp + 2 * (j + LANE_AHEAD + KL + 1));
+    }
     const int off = pg[(gn + j) * LANE_GROUP + i];
     const double* Lrow = Lg + (gn + j) * KL * LANE_GROUP + i;
     double piv_val = win[0];
@@ -659,12 +675,30 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, const double
 #pragma unroll
   for (int t = 0; t <= KUU; ++t) w[t] = (n - 1 - t >= 0) ? yp[(size_t)2 * (n - 1 - t) * LANE_GROUP] : 0.0;
   double* xp = reinterpret_cast<double*>(x + (size_t)pen * n) + comp;
+  unsigned long long m_next = umask[n - 1];
   for (int j = n - 1; j >= 0; --j) {
+    const unsigned long long m = m_next;            // this row's mask, loaded one row ahead
+    if (j >= 1) m_next = umask[j - 1];
+    if (j - LANE_AHEAD >= 0) {
+      const size_t ra = gn + j - LANE_AHEAD;
+      const unsigned long long ma = umask[j - LANE_AHEAD];
+      for (int t = lane; t <= KUU; t += 32)
+        if ((ma >> t) & 1ull) prefetch_l1(Ug + (ra * (KUU + 1) + t) * LANE_GROUP);
+      const int ry = j - LANE_AHEAD - KUU - 1;
+      if (ry >= 0 && (lane & 15) == 0) prefetch_l1(y + ((size_t)g * n + ry) * LANE_GROUP + (lane >> 4) * 8);
+    }
     const double* Urow = Ug + (gn + j) * (KUU + 1) * LANE_GROUP + i;
+    // entries that are zero in every pencil (most of the band: the pattern
+    // of the interleaved tau system) are neither loaded nor applied; an FMA
+    // with a zero product would leave w unchanged anyway
+    double u[KUU + 1];
+#pragma unroll
+    for (int t = 1; t <= KUU; ++t) u[t] = ((m >> t) & 1ull) ? Urow[t * LANE_GROUP] : 0.0;
     const double bj = w[0];
     xp[2 * j] = bj * Urow[0];
 #pragma unroll
-    for (int t = 1; t <= KUU; ++t) w[t] = fma(-Urow[t * LANE_GROUP], bj, w[t]);
+    for (int t = 1; t <= KUU; ++t)
+      if ((m >> t) & 1ull) w[t] = fma(-u[t], bj, w[t]);
 #pragma unroll
     for (int t = 0; t < KUU; ++t) w[t] = w[t + 1];
     w[KUU] = (j - KUU - 1 >= 0) ? yp[(size_t)2 * (j - KUU - 1) * LANE_GROUP] : 0.0;
@@ -676,15 +710,36 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, const double
 bool lanes_supported(int kl, int kuu) { return (kl == 9 && kuu == 38) || (kl == 7 && kuu == 29); }
 
 cudaError_t launch_pencil_lanes(cudaStream_t s, int P, int n, int kl, int kuu, const double* Lg, const double* Ug,
-                                const uint8_t* pg, const double2* b, double2* y, double2* x) {
+                                const uint8_t* pg, const unsigned long long* umask, const double2* b, double2* y,
+                                double2* x) {
   const int threads = 2 * P;
   const int grid = (threads + 127) / 128;
   if (kl == 9 && kuu == 38)
-    k_pencil_lanes<9, 38><<<grid, 128, 0, s>>>(P, n, Lg, Ug, pg, b, y, x);
+    k_pencil_lanes<9, 38><<<grid, 128, 0, s>>>(P, n, Lg, Ug, pg, umask, b, y, x);
   else if (kl == 7 && kuu == 29)
-    k_pencil_lanes<7, 29><<<grid, 128, 0, s>>>(P, n, Lg, Ug, pg, b, y, x);
+    k_pencil_lanes<7, 29><<<grid, 128, 0, s>>>(P, n, Lg, Ug, pg, umask, b, y, x);
   else
     return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+__global__ void k_u_mask(int P, int n, int npad, int kuu, int upad, const double* __restrict__ U,
+                         unsigned long long* __restrict__ umask) {
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)P * n) return;
+  const int p = (int)(idx / n), j = (int)(idx - (size_t)p * n);
+  const double* col = U + ((size_t)p * npad + j) * upad;
+  unsigned long long m = 1ull;
+  for (int t = 1; t <= kuu; ++t)
+    if (col[t] != 0.0) m |= 1ull << t;
+  if ((m & ~umask[j]) != 0ull) atomicOr(umask + j, m);
+}
+
+cudaError_t launch_u_mask(cudaStream_t s, int P, int n, int npad, int kuu, int upad, const double* U,
+                          unsigned long long* umask) {
+  if (kuu > 63) return cudaErrorInvalidValue;
+  const size_t total = (size_t)P * n;
+  k_u_mask<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P, n, npad, kuu, upad, U, umask);
   return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ struct BandFactor {
   double* Lg = nullptr;         // [G][n][kl][16]
   double* Ug = nullptr;         // [G][n][kl+ku+1][16]  t=0: 1/U_jj
   uint8_t* pg = nullptr;        // [G][n][16]
+  unsigned long long* umask = nullptr;   // [n] bit t: U_{j-t,j} != 0 in some pencil (bit 0 set)
 };
 
 // Pencils per warp in the lane-per-pencil substitution (two lanes each:
@@ -88,7 +89,7 @@ struct SolveArgs {
   int mode;
   double2* bg; const double2* xg;
   // factor in the lane-interleaved layout (null: not available)
-  const double* Lg; const double* Ug; const uint8_t* pg;
+  const double* Lg; const double* Ug; const uint8_t* pg; const unsigned long long* umask;
 };
 
 // Transform arguments.
@@ -150,7 +151,12 @@ cudaError_t launch_pencil_solve_batched(cudaStream_t s, const SolveArgs* args, c
 // no compiled instance (lanes_supported).
 bool lanes_supported(int kl, int kuu);
 cudaError_t launch_pencil_lanes(cudaStream_t s, int P, int n, int kl, int kuu, const double* Lg, const double* Ug,
-                                const uint8_t* pg, const double2* b, double2* y, double2* x);
+                                const uint8_t* pg, const unsigned long long* umask, const double2* b, double2* y,
+                                double2* x);
+// umask[j] |= bit t for every t <= kuu with U_{j-t,j} != 0 in some pencil
+// (umask zeroed by the caller)
+cudaError_t launch_u_mask(cudaStream_t s, int P, int n, int npad, int kuu, int upad, const double* U,
+                          unsigned long long* umask);
 cudaError_t launch_factor_relayout(cudaStream_t s, int P, int n, int npad, int kl, int kuu, int lpad, int upad,
                                    const BandFactor& f);
 cudaError_t launch_coef_to_solve(cudaStream_t s, int P, int S, int Nz, const double2* xc,
