@@ -119,6 +119,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_rate(units_per_rank, seconds_local, world, device="cpu"):
+    """Whole-job rate of `world` ranks that each processed `units_per_rank`:
+    the units of all ranks divided by the slowest rank's time (all-reduce MAX
+    over the process group; identity for one rank).  Returns (rate, seconds)."""
+    t = float(seconds_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return world * units_per_rank / t, t
+
+
 def solve_flops_bytes(s):
     """Algorithmic FP64 flops and bytes of one pencil-solve launch.
 
@@ -189,11 +203,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     s.sync()
     solve_ms, solve_launches = s.solve_time()
-    if distributed:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.dof * args.steps / (ms * 1e-3)
+    value, secs = job_rate(w.dof * args.steps, ms * 1e-3, world, device="cuda")
+    ms = secs * 1e3
 
     # end to end through the public API with host buffers: upload the state,
     # K steps each followed by a device-to-host read of the buoyancy field
@@ -206,9 +217,9 @@ def run_ours(args):
         s.step(1)
         _ = s.get_field("b")
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_rate, _ = job_rate(w.dof * args.steps, time.perf_counter() - t0, world, device="cuda")
     state_bytes = s.S * s.P * s.Nz * 16
-    e2e = {"value": world * w.dof * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": e2e_rate, "unit": UNIT,
            "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": s.P * s.Nz * 16}
 
     flops, nbytes = solve_flops_bytes(s)
