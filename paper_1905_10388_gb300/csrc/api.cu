@@ -995,6 +995,19 @@ sp_status sp_set_bilinear_rhs(sp_ctx* ctx, int problem, int nterms, const int32_
   }
   if (pr->gfields.size() > 16) return fail(ctx, SP_ERR_ARG, "at most 16 distinct grid fields");
   if (nterms > 16) return fail(ctx, SP_ERR_ARG, "at most 16 bilinear terms");
+  // the product kernel sums each equation's terms in one run: order the
+  // terms by slot (stable, so terms of one equation keep their order)
+  {
+    std::vector<int> order(pr->t_slot.size());
+    for (size_t t = 0; t < order.size(); ++t) order[t] = (int)t;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return pr->t_slot[x] < pr->t_slot[y]; });
+    std::vector<int32_t> sl, fa, fb;
+    std::vector<double> cf;
+    for (int t : order) {
+      sl.push_back(pr->t_slot[t]); fa.push_back(pr->t_fa[t]); fb.push_back(pr->t_fb[t]); cf.push_back(pr->t_coef[t]);
+    }
+    pr->t_slot = sl; pr->t_fa = fa; pr->t_fb = fb; pr->t_coef = cf;
+  }
   return SP_OK;
 }
 

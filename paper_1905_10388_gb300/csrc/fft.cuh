@@ -30,7 +30,24 @@ __device__ __forceinline__ void load_twiddles(C<T>* dst, const C<T>* __restrict_
   for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = src[i];
 }
 
-// One radix-R Stockham pass (R = 2, 3 or 4) over nb sequences.  Ns is
+// z times i (sign > 0) or -i (sign < 0): multiplication by exp(sign i pi / 2)
+template <typename T>
+__device__ __forceinline__ C<T> times_i(C<T> z, int sign) {
+  return (sign < 0) ? mk<T>(z.y, -z.x) : mk<T>(-z.y, z.x);
+}
+
+// 4-point DFT of (c0, c1, c2, c3) with root exp(sign 2 pi i / 4)
+template <typename T>
+__device__ __forceinline__ void dft4(C<T> c0, C<T> c1, C<T> c2, C<T> c3, int sign, C<T>* d) {
+  const C<T> p0 = cadd<T>(c0, c2), p1 = csub<T>(c0, c2), p2 = cadd<T>(c1, c3);
+  const C<T> p3 = times_i<T>(csub<T>(c1, c3), sign);
+  d[0] = cadd<T>(p0, p2);
+  d[1] = cadd<T>(p1, p3);
+  d[2] = csub<T>(p0, p2);
+  d[3] = csub<T>(p1, p3);
+}
+
+// One radix-R Stockham pass (R = 2, 3, 4 or 8) over nb sequences.  Ns is
 // 2^ns_log2 or 3 * 2^ns_log2 (ns_has3); Q = N / R.  Index arithmetic avoids
 // run-time integer division: j / Ns and j mod Ns use shifts and a division
 // by the constant 3; the sequence index comes from one FP32 multiply.
@@ -72,15 +89,31 @@ __device__ __forceinline__ void stockham_pass(const C<T>* __restrict__ x, C<T>* 
         yb[o] = cadd<T>(a[0], cadd<T>(a[1], a[2]));
         yb[o + Ns] = cadd<T>(a[0], cadd<T>(cmul<T>(w1, a[1]), cmul<T>(w2, a[2])));
         yb[o + 2 * Ns] = cadd<T>(a[0], cadd<T>(cmul<T>(w2, a[1]), cmul<T>(w1, a[2])));
+      } else if (R == 4) {
+        C<T> d[4];
+        dft4<T>(a[0], a[1], a[2], a[3], sign, d);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) yb[o + q * Ns] = d[q];
       } else {
-        const C<T> b0 = cadd<T>(a[0], a[2]), b1 = csub<T>(a[0], a[2]), b2 = cadd<T>(a[1], a[3]);
-        const C<T> d = csub<T>(a[1], a[3]);
-        // (a1 - a3) times -i (forward) or +i (inverse)
-        const C<T> b3 = (sign < 0) ? mk<T>(d.y, -d.x) : mk<T>(-d.y, d.x);
-        yb[o] = cadd<T>(b0, b2);
-        yb[o + Ns] = cadd<T>(b1, b3);
-        yb[o + 2 * Ns] = csub<T>(b0, b2);
-        yb[o + 3 * Ns] = csub<T>(b1, b3);
+        // 8-point DFT: X_q = E_{q mod 4} + w^q O_{q mod 4}, X_{q+4} = E_q - w^q O_q,
+        // E / O the 4-point DFTs of the even / odd inputs, w = exp(sign 2 pi i / 8)
+        C<T> e[4], f[4];
+        dft4<T>(a[0], a[2], a[4], a[6], sign, e);
+        dft4<T>(a[1], a[3], a[5], a[7], sign, f);
+        const T h = (T)0.70710678118654752440;
+        const C<T> g1 = (sign < 0) ? mk<T>(h * (f[1].x + f[1].y), h * (f[1].y - f[1].x))
+                                   : mk<T>(h * (f[1].x - f[1].y), h * (f[1].y + f[1].x));   // w f1
+        const C<T> g2 = times_i<T>(f[2], sign);                                             // w^2 f2
+        const C<T> g3 = (sign < 0) ? mk<T>(h * (f[3].y - f[3].x), -h * (f[3].x + f[3].y))
+                                   : mk<T>(-h * (f[3].x + f[3].y), h * (f[3].x - f[3].y));  // w^3 f3
+        yb[o] = cadd<T>(e[0], f[0]);
+        yb[o + 4 * Ns] = csub<T>(e[0], f[0]);
+        yb[o + Ns] = cadd<T>(e[1], g1);
+        yb[o + 5 * Ns] = csub<T>(e[1], g1);
+        yb[o + 2 * Ns] = cadd<T>(e[2], g2);
+        yb[o + 6 * Ns] = csub<T>(e[2], g2);
+        yb[o + 3 * Ns] = cadd<T>(e[3], g3);
+        yb[o + 7 * Ns] = csub<T>(e[3], g3);
       }
     }
   }
@@ -88,9 +121,9 @@ __device__ __forceinline__ void stockham_pass(const C<T>* __restrict__ x, C<T>* 
 }
 
 // Batched FFT of nb contiguous length-N sequences: a radix-3 pass when 3 | N,
-// one radix-2 pass when N/3^{0,1} is an odd power of two, then radix-4
-// passes.  `tw` should point to shared memory.  Returns the buffer holding
-// the result (x or y).  Ends with __syncthreads.
+// then, for the remaining 2^m, one radix-2 (m = 1 mod 3) or radix-4 pass
+// (m = 2 mod 3) and radix-8 passes.  `tw` should point to shared memory.
+// Returns the buffer holding the result (x or y).  Ends with __syncthreads.
 template <typename T>
 __device__ C<T>* fft_batched(C<T>* x, C<T>* y, int N, int radix3, const C<T>* __restrict__ tw,
                              int sign, int nb) {
@@ -104,14 +137,19 @@ __device__ C<T>* fft_batched(C<T>* x, C<T>* y, int N, int radix3, const C<T>* __
   }
   const int M = N / Ns;                 // a power of two
   const int m = 31 - __clz(M);
-  if (m & 1) {
+  if (m % 3 == 1) {
     stockham_pass<T, 2>(x, y, N, Ns, lg, has3, tw, sign, nb);
     C<T>* t = x; x = y; y = t;
     Ns *= 2;
     lg += 1;
-  }
-  for (; Ns < N; Ns *= 4, lg += 2) {
+  } else if (m % 3 == 2) {
     stockham_pass<T, 4>(x, y, N, Ns, lg, has3, tw, sign, nb);
+    C<T>* t = x; x = y; y = t;
+    Ns *= 4;
+    lg += 2;
+  }
+  for (; Ns < N; Ns *= 8, lg += 3) {
+    stockham_pass<T, 8>(x, y, N, Ns, lg, has3, tw, sign, nb);
     C<T>* t = x; x = y; y = t;
   }
   return x;

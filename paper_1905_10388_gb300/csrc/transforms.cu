@@ -190,7 +190,7 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
 
   const T* OUT = G;
   if (mode & 2) {
-    // term tables in shared memory (at most MAX_TERMS terms), equation loop outermost
+    // term tables in shared memory (at most MAX_TERMS terms)
     constexpr int MAX_TERMS = 16;
     __shared__ T tc[MAX_TERMS];
     __shared__ int ta[MAX_TERMS], tb[MAX_TERMS], te[MAX_TERMS];
@@ -200,12 +200,16 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
       tc[tid] = tcoef[tid]; ta[tid] = d.t_fa[tid] * N; tb[tid] = d.t_fb[tid] * N; te[tid] = d.t_eq[tid];
     }
     __syncthreads();
-    for (int e = 0; e < ne; ++e) {
-      for (int i = tid; i < N; i += nt) {
-        T acc = 0;
-        for (int t = 0; t < nterms; ++t)
-          if (te[t] == e) acc += tc[t] * G[ta[t] + i] * G[tb[t] + i];
-        O[(size_t)e * N + i] = acc;
+    // terms are grouped by equation (the host keeps them sorted by slot):
+    // one pass over the terms, writing each equation's sum at its last term
+    for (int i = tid; i < N; i += nt) {
+      T acc = 0;
+      for (int t = 0; t < nterms; ++t) {
+        acc += tc[t] * G[ta[t] + i] * G[tb[t] + i];
+        if (t + 1 == nterms || te[t + 1] != te[t]) {
+          O[(size_t)te[t] * N + i] = acc;
+          acc = 0;
+        }
       }
     }
     __syncthreads();
