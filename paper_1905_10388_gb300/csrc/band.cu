@@ -691,14 +691,90 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, const double
     // entries that are zero in every pencil (most of the band: the pattern
     // of the interleaved tau system) are neither loaded nor applied; an FMA
     // with a zero product would leave w unchanged anyway
-    double u[KUU + 1];
-#pragma unroll
-    for (int t = 1; t <= KUU; ++t) u[t] = ((m >> t) & 1ull) ? Urow[t * LANE_GROUP] : 0.0;
     const double bj = w[0];
     xp[2 * j] = bj * Urow[0];
-#pragma unroll
-    for (int t = 1; t <= KUU; ++t)
-      if ((m >> t) & 1ull) w[t] = fma(-u[t], bj, w[t]);
+    // Only the listed entries issue an FMA.  The mask is the same for the
+    // whole warp, so this loop branches (a predicated-off FP64 instruction
+    // would still hold the FP64 pipe); each entry's value is loaded in its
+    // case (the row was prefetched into L1), so only the window stays live.
+    unsigned long long mm = m & ~1ull;
+    while (mm) {
+      const int t = __ffsll((long long)mm) - 1;
+      mm &= mm - 1;
+      const double ut = Urow[t * LANE_GROUP];
+      switch (t) {
+#define SP_LANE_CASE(T)                          \
+  case T:                                        \
+    if (T <= KUU) w[T] = fma(-ut, bj, w[T]);    \
+    break;
+        SP_LANE_CASE(1)
+        SP_LANE_CASE(2)
+        SP_LANE_CASE(3)
+        SP_LANE_CASE(4)
+        SP_LANE_CASE(5)
+        SP_LANE_CASE(6)
+        SP_LANE_CASE(7)
+        SP_LANE_CASE(8)
+        SP_LANE_CASE(9)
+        SP_LANE_CASE(10)
+        SP_LANE_CASE(11)
+        SP_LANE_CASE(12)
+        SP_LANE_CASE(13)
+        SP_LANE_CASE(14)
+        SP_LANE_CASE(15)
+        SP_LANE_CASE(16)
+        SP_LANE_CASE(17)
+        SP_LANE_CASE(18)
+        SP_LANE_CASE(19)
+        SP_LANE_CASE(20)
+        SP_LANE_CASE(21)
+        SP_LANE_CASE(22)
+        SP_LANE_CASE(23)
+        SP_LANE_CASE(24)
+        SP_LANE_CASE(25)
+        SP_LANE_CASE(26)
+        SP_LANE_CASE(27)
+        SP_LANE_CASE(28)
+        SP_LANE_CASE(29)
+        SP_LANE_CASE(30)
+        SP_LANE_CASE(31)
+        SP_LANE_CASE(32)
+        SP_LANE_CASE(33)
+        SP_LANE_CASE(34)
+        SP_LANE_CASE(35)
+        SP_LANE_CASE(36)
+        SP_LANE_CASE(37)
+        SP_LANE_CASE(38)
+        SP_LANE_CASE(39)
+        SP_LANE_CASE(40)
+        SP_LANE_CASE(41)
+        SP_LANE_CASE(42)
+        SP_LANE_CASE(43)
+        SP_LANE_CASE(44)
+        SP_LANE_CASE(45)
+        SP_LANE_CASE(46)
+        SP_LANE_CASE(47)
+        SP_LANE_CASE(48)
+        SP_LANE_CASE(49)
+        SP_LANE_CASE(50)
+        SP_LANE_CASE(51)
+        SP_LANE_CASE(52)
+        SP_LANE_CASE(53)
+        SP_LANE_CASE(54)
+        SP_LANE_CASE(55)
+        SP_LANE_CASE(56)
+        SP_LANE_CASE(57)
+        SP_LANE_CASE(58)
+        SP_LANE_CASE(59)
+        SP_LANE_CASE(60)
+        SP_LANE_CASE(61)
+        SP_LANE_CASE(62)
+        SP_LANE_CASE(63)
+#undef SP_LANE_CASE
+        default:
+          break;
+      }
+    }
 #pragma unroll
     for (int t = 0; t < KUU; ++t) w[t] = w[t + 1];
     w[KUU] = (j - KUU - 1 >= 0) ? yp[(size_t)2 * (j - KUU - 1) * LANE_GROUP] : 0.0;
