@@ -291,6 +291,68 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     // epilogue only: X~ (already divided by U_jj) from the substitution kernel
     for (int r = tid; active && r < n; r += nt) sm.B[r] = a.xg[prow + r];
     __syncthreads();
+  } else if (mode == 1) {
+  // assembly only, one pass per row straight to global memory: stored
+  // vectors, matvec, then the row's F~ entry (the left-preconditioned
+  // right-hand side of equation e, mode m, through the inverse row map) or
+  // its boundary value
+  for (int r = tid; active && r < n; r += nt) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < a.nvec; ++k) {
+      const double2 v = a.vec[k][prow + r];
+      acc.x = fma(a.vec_coef[k], v.x, acc.x);
+      acc.y = fma(a.vec_coef[k], v.y, acc.y);
+    }
+    if (a.mv_x != nullptr) {
+      double2 s = make_double2(0.0, 0.0);
+      const double* vals = a.mv_vals + (size_t)p * a.mv_nnz;
+      for (int e = a.mv_indptr[r]; e < a.mv_indptr[r + 1]; ++e) {
+        const double m = vals[e];
+        const double2 x = a.mv_x[prow + a.mv_indices[e]];
+        s.x = fma(m, x.x, s.x);
+        s.y = fma(m, x.y, s.y);
+      }
+      if (a.mv_store != nullptr) a.mv_store[prow + r] = s;
+      acc.x = fma(a.mv_coef, s.x, acc.x);
+      acc.y = fma(a.mv_coef, s.y, acc.y);
+    }
+    const int fi = a.n_nl > 0 ? a.row_f[r] : -1;
+    if (fi >= 0) {
+      const int sl = fi / Nz, m = fi - sl * Nz;
+      const int e = a.nl_eq[sl];
+      double2 f0 = make_double2(0.0, 0.0), f2 = make_double2(0.0, 0.0);
+      for (int k = 0; k < a.nfc; ++k) {
+        const double2* F = a.fc[k] + ((size_t)sl * a.P + p) * Nz;
+        const double2 v0 = F[m];
+        f0.x = fma(a.fc_coef[k], v0.x, f0.x);
+        f0.y = fma(a.fc_coef[k], v0.y, f0.y);
+        if (m + 2 < Nz) {
+          const double2 v2 = F[m + 2];
+          f2.x = fma(a.fc_coef[k], v2.x, f2.x);
+          f2.y = fma(a.fc_coef[k], v2.y, f2.y);
+        }
+      }
+      double2 u;
+      if (a.eq_differential[e]) {
+        const double c0 = (m == 0) ? 1.0 : 0.5;
+        u.x = fma(c0, f0.x, -0.5 * f2.x);
+        u.y = fma(c0, f0.y, -0.5 * f2.y);
+      } else {
+        u = f0;
+      }
+      u = cipow_d(u, -a.eq_phase[e]);
+      acc.x += u.x;
+      acc.y += u.y;
+    }
+    const int q = a.nbc > 0 ? a.row_bc[r] : -1;
+    if (q >= 0) {
+      const double2 g = a.bc_values[(size_t)p * a.nbc + q];
+      acc.x = fma(a.bc_coef, g.x, acc.x);
+      acc.y = fma(a.bc_coef, g.y, acc.y);
+    }
+    a.bg[prow + r] = acc;         // B~ for the substitution kernel
+  }
+  return;
   } else {
   for (int r = tid; active && r < n; r += nt) {
     double2 acc = make_double2(0.0, 0.0);
@@ -357,11 +419,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   }
   __syncthreads();
   }
-  if (mode == 1) {
-    // prologue only: hand B~ to the substitution kernel
-    for (int r = tid; active && r < n; r += nt) a.bg[prow + r] = sm.B[r];
-    return;
-  }
+
 
   // ---- substitution, over the padded columns [0, npad): padding columns
   //      carry zero factors, so they pass zeros through.  Warp 0 solves the
@@ -533,6 +591,12 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
         }
         s.x = fma(m, x.x, s.x);
         s.y = fma(m, x.y, s.y);
+      }
+      if (mode == 2 && a.ep_from_b != 0.0) {
+        // L~ X~ = (B~ - alpha M~ X~) / beta for the stage matrix alpha M~ + beta L~
+        const double2 bb = a.bg[prow + r];
+        s.x = (bb.x - a.ep_alpha * s.x) * a.ep_from_b;
+        s.y = (bb.y - a.ep_alpha * s.y) * a.ep_from_b;
       }
       a.ep_mv_store[prow + r] = s;
     }

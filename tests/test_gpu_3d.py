@@ -173,7 +173,9 @@ def test_full_size_one_step_properties(ctx):
 def test_lane_substitution_equals_window(ctx, case):
     """The lane-per-pencil substitution (one lane per pencil and real or
     imaginary part) performs the window kernel's FMAs in the same order, so
-    states after several steps agree bit for bit."""
+    SBDF2 states after several steps agree bit for bit.  For RK222 the lane
+    path takes L~X~ of the first stage from that stage's right-hand side,
+    (B~ - M~X~) / (gamma dt), instead of a matvec: equal to rounding."""
     from paper_1905_10388_gb300.solver import RBSolver
     dim, scheme = case.split("-")[:2]
     prec = "mixed" if case.endswith("mixed") else "fp64"
@@ -193,4 +195,8 @@ def test_lane_substitution_equals_window(ctx, case):
         s.sync()
         out.append(s.get_state())
     assert np.isfinite(out[0]).all()
-    assert np.array_equal(out[0], out[1])
+    if scheme == "SBDF2":
+        assert np.array_equal(out[0], out[1])
+    else:
+        for i in range(out[0].shape[0]):
+            assert rel_err(out[1][i], out[0][i]) < 1e-12, i
