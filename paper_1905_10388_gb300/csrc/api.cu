@@ -351,7 +351,6 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
     BandFactor& f = pr->fac[fi];
     if (pr->lanes) {
       CK(dalloc(&f.Lg, ngroups * pr->n * pr->kl * LANE_GROUP));
-      CK(dalloc(&f.Ug, ngroups * pr->n * (kuu + 1) * LANE_GROUP));
       CK(dalloc(&f.pg, ngroups * pr->n * LANE_GROUP));
       CK(dalloc(&f.umask, (size_t)pr->n));
     }
@@ -469,6 +468,7 @@ SolveArgs base_args(Problem* pr, sp_ctx* ctx, int fac) {
   a.status = ctx->d_status;
   a.xc32_out = pr->d_Xc32;   // null unless mixed precision
   a.Lg = pr->fac[fac].Lg; a.Ug = pr->fac[fac].Ug; a.pg = pr->fac[fac].pg;   // null unless lane mode
+  a.cmax = pr->fac[fac].cmax;
   a.umask = pr->fac[fac].umask;
   return a;
 }
@@ -491,7 +491,8 @@ sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
     SolveArgs a1 = a;
     a1.mode = 1; a1.bg = pr->d_bg;
     CK(launch_pencil_solve(s, a1));
-    CK(launch_pencil_lanes(s, pr->P, pr->n, a.kl, a.kuu, a.Lg, a.Ug, a.pg, a.umask, pr->d_bg, pr->d_yg, pr->d_xg));
+    CK(launch_pencil_lanes(s, pr->P, pr->n, a.kl, a.kuu, a.Lg, a.Ug, a.cmax, a.pg, a.umask, pr->d_bg, pr->d_yg,
+                           pr->d_xg));
     SolveArgs a2 = a;
     a2.mode = 2; a2.xg = pr->d_xg; a2.bg = pr->d_bg;
     if (a2.ep_mv_vals == pr->d_Lv) {
@@ -1062,15 +1063,34 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
     cudaError_t e = launch_band_factor(ctx->stream, pr->P, pr->n, (int)pr->nnz, pr->kl, pr->ku, pr->d_indptr,
                                        pr->d_indices, pr->d_Mv, pr->d_Lv, ab[f][0], ab[f][1], work, pr->fac[f],
                                        pr->npad, pr->lpad, pr->upad, ctx->d_status);
-    if (e == cudaSuccess && pr->lanes)
-      e = launch_factor_relayout(ctx->stream, pr->P, pr->n, pr->npad, pr->kl, pr->kl + pr->ku, pr->lpad, pr->upad,
-                                 pr->fac[f]);
-    if (e == cudaSuccess && pr->lanes)
-      e = cudaMemsetAsync(pr->fac[f].umask, 0, (size_t)pr->n * sizeof(unsigned long long), ctx->stream);
-    if (e == cudaSuccess && pr->lanes)
-      e = launch_u_mask(ctx->stream, pr->P, pr->n, pr->npad, pr->kl + pr->ku, pr->upad, pr->fac[f].U,
-                        pr->fac[f].umask);
     if (e != cudaSuccess) { cudaFree(work); CK(e); }
+    if (pr->lanes) {
+      // lane layout: the union pattern of U over pencils, then the copy with
+      // only the listed entries
+      BandFactor& bf = pr->fac[f];
+      e = cudaMemsetAsync(bf.umask, 0, (size_t)pr->n * sizeof(unsigned long long), ctx->stream);
+      if (e == cudaSuccess)
+        e = launch_u_mask(ctx->stream, pr->P, pr->n, pr->npad, pr->kl + pr->ku, pr->upad, bf.U, bf.umask);
+      std::vector<unsigned long long> hm(pr->n);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hm.data(), bf.umask, hm.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) { cudaFree(work); CK(e); }
+      int cmax = 1;
+      for (unsigned long long m : hm) cmax = std::max(cmax, __builtin_popcountll(m));
+      if (cmax != bf.cmax || !bf.Ug) {
+        if (bf.Ug) cudaFree(bf.Ug);
+        bf.Ug = nullptr;
+        const size_t ngroups = (pr->P + LANE_GROUP - 1) / LANE_GROUP;
+        e = cudaMalloc((void**)&bf.Ug, ngroups * pr->n * cmax * LANE_GROUP * sizeof(double));
+        if (e != cudaSuccess) { cudaFree(work); CK(e); }
+        bf.cmax = cmax;
+      }
+      e = launch_factor_relayout(ctx->stream, pr->P, pr->n, pr->npad, pr->kl, pr->kl + pr->ku, pr->lpad, pr->upad,
+                                 bf);
+      if (e != cudaSuccess) { cudaFree(work); CK(e); }
+    }
   }
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   cudaFree(work);

@@ -683,89 +683,90 @@ cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a) {
 // by pencil within a group, so a warp's load of one factor entry reads 16
 // consecutive doubles.
 // ---------------------------------------------------------------------------
-// L1 prefetch of the line holding p
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
 }
-constexpr int LANE_AHEAD = 8;      // rows prefetched ahead
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int KL, int KUU>
-__global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, const double* __restrict__ Lg,
-                                                      const double* __restrict__ Ug,
+__global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, const double* __restrict__ Lg,
+                                                      const double* __restrict__ Uc,
                                                       const uint8_t* __restrict__ pg,
                                                       const unsigned long long* __restrict__ umask,
                                                       const double2* __restrict__ b, double2* __restrict__ y,
                                                       double2* __restrict__ x) {
+  extern __shared__ __align__(16) double lane_stage[];   // [warp][2][cmax][LANE_GROUP]
   const int gl = blockIdx.x * blockDim.x + threadIdx.x;
   const int comp = gl & 1;
-  const int pen = gl >> 1;                       // pencil
-  if (pen >= P) return;
+  const int pen = gl >> 1;                       // pencil; a warp holds the 16 pencils of one group
+  const bool act = pen < P;                      // idle lanes of the last group keep the warp's rhythm
   const int g = pen / LANE_GROUP, i = pen - g * LANE_GROUP;
-  const double* bp = reinterpret_cast<const double*>(b + (size_t)pen * n) + comp;
+  if (g * LANE_GROUP >= P) return;               // a whole warp past the last group (no storage there)
+  const int lane = threadIdx.x & 31;
+  const double* bp = reinterpret_cast<const double*>(b + (size_t)(act ? pen : 0) * n) + comp;
   double* yp = reinterpret_cast<double*>(y + (size_t)g * n * LANE_GROUP + i) + comp;   // row j at yp[2 j LANE_GROUP]
   const size_t gn = (size_t)g * n;
   // forward: row interchanges and unit-lower multipliers; win[t] = row j + t
-  double win[KL + 1];
+  if (act) {
+    double win[KL + 1];
 #pragma unroll
-  for (int t = 0; t <= KL; ++t) win[t] = (t < n) ? bp[2 * t] : 0.0;
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < n; ++j) {
-    // a lane serves one dependent chain, so few warps share an SM: pull the
-    // rows LANE_AHEAD steps ahead into L1 (the warp's lanes split the lines)
-    if (j + LANE_AHEAD < n) {
-      const size_t ra = gn + j + LANE_AHEAD;
-      if (lane < KL) prefetch_l1(Lg + (ra * KL + lane) * LANE_GROUP);
-      else if (lane == KL && ((j + LANE_AHEAD) & 7) == 0) prefetch_l1(pg + ra * LANE_GROUP);
-      if (((j + LANE_AHEAD) & 1) == 0 && j + LANE_AHEAD + KL + 1 < n) prefetch_l1(bp + 2 * (j + LANE_AHEAD + KL + 1));
+    for (int t = 0; t <= KL; ++t) win[t] = (t < n) ? bp[2 * t] : 0.0;
+    for (int j = 0; j < n; ++j) {
+      const int off = pg[(gn + j) * LANE_GROUP + i];
+      const double* Lrow = Lg + (gn + j) * KL * LANE_GROUP + i;
+      double piv_val = win[0];
+#pragma unroll
+      for (int t = 1; t <= KL; ++t) piv_val = (off == t) ? win[t] : piv_val;
+#pragma unroll
+      for (int t = 1; t <= KL; ++t) win[t] = (off == t) ? win[0] : win[t];
+      const double yj = piv_val;
+      yp[(size_t)2 * j * LANE_GROUP] = yj;
+#pragma unroll
+      for (int t = 1; t <= KL; ++t) win[t] = fma(-Lrow[(t - 1) * LANE_GROUP], yj, win[t]);
+#pragma unroll
+      for (int t = 0; t < KL; ++t) win[t] = win[t + 1];
+      win[KL] = (j + KL + 1 < n) ? bp[2 * (j + KL + 1)] : 0.0;
     }
-    const int off = pg[(gn + j) * LANE_GROUP + i];
-    const double* Lrow = Lg + (gn + j) * KL * LANE_GROUP + i;
-    double piv_val = win[0];
-#pragma unroll
-    for (int t = 1; t <= KL; ++t) piv_val = (off == t) ? win[t] : piv_val;
-#pragma unroll
-    for (int t = 1; t <= KL; ++t) win[t] = (off == t) ? win[0] : win[t];
-    const double yj = piv_val;
-    yp[(size_t)2 * j * LANE_GROUP] = yj;
-#pragma unroll
-    for (int t = 1; t <= KL; ++t) win[t] = fma(-Lrow[(t - 1) * LANE_GROUP], yj, win[t]);
-#pragma unroll
-    for (int t = 0; t < KL; ++t) win[t] = win[t + 1];
-    win[KL] = (j + KL + 1 < n) ? bp[2 * (j + KL + 1)] : 0.0;
   }
-  // back substitution with the scaled columns U_{j-t,j} / U_jj; the rows
-  // of y this lane wrote are read back by this lane only
+  // back substitution with the scaled columns U_{j-t,j} / U_jj.  Only entries
+  // nonzero in some pencil are stored: the k-th set bit t of umask[j] holds
+  // U_{j-t,j} / U_jj at Uc[g][j][k] (k = 0: 1/U_jj).  Each row's entries
+  // are copied into shared memory one row ahead (cp.async, two buffers per
+  // warp), and only the listed entries issue an FMA: the mask is the same for
+  // the whole warp, so the loop branches (a predicated-off FP64 instruction
+  // would still hold the FP64 pipe) and jumps to the FMA of its window
+  // register.  The rows of y this lane wrote are read back by this lane only.
+  double* st = lane_stage + (size_t)(threadIdx.x >> 5) * 2 * cmax * LANE_GROUP;
+  auto stage = [&](int jr) {
+    const int cnt = __popcll(umask[jr]);
+    const double* src = Uc + (gn + jr) * (size_t)cmax * LANE_GROUP;
+    double* dst = st + (jr & 1) * cmax * LANE_GROUP;
+    for (int c = lane; c < cnt * (LANE_GROUP / 2); c += 32) cp_async16(dst + 2 * c, src + 2 * c);
+    cp_async_commit();
+  };
   double w[KUU + 1];                             // w[t] = pending row j - t
 #pragma unroll
-  for (int t = 0; t <= KUU; ++t) w[t] = (n - 1 - t >= 0) ? yp[(size_t)2 * (n - 1 - t) * LANE_GROUP] : 0.0;
-  double* xp = reinterpret_cast<double*>(x + (size_t)pen * n) + comp;
-  unsigned long long m_next = umask[n - 1];
+  for (int t = 0; t <= KUU; ++t) w[t] = (act && n - 1 - t >= 0) ? yp[(size_t)2 * (n - 1 - t) * LANE_GROUP] : 0.0;
+  double* xp = reinterpret_cast<double*>(x + (size_t)(act ? pen : 0) * n) + comp;
+  stage(n - 1);
   for (int j = n - 1; j >= 0; --j) {
-    const unsigned long long m = m_next;            // this row's mask, loaded one row ahead
-    if (j >= 1) m_next = umask[j - 1];
-    if (j - LANE_AHEAD >= 0) {
-      const size_t ra = gn + j - LANE_AHEAD;
-      const unsigned long long ma = umask[j - LANE_AHEAD];
-      for (int t = lane; t <= KUU; t += 32)
-        if ((ma >> t) & 1ull) prefetch_l1(Ug + (ra * (KUU + 1) + t) * LANE_GROUP);
-      const int ry = j - LANE_AHEAD - KUU - 1;
-      if (ry >= 0 && (lane & 15) == 0) prefetch_l1(y + ((size_t)g * n + ry) * LANE_GROUP + (lane >> 4) * 8);
-    }
-    const double* Urow = Ug + (gn + j) * (KUU + 1) * LANE_GROUP + i;
-    // entries that are zero in every pencil (most of the band: the pattern
-    // of the interleaved tau system) are neither loaded nor applied; an FMA
-    // with a zero product would leave w unchanged anyway
+    if (j >= 1) stage(j - 1);
+    else cp_async_commit();                      // one group per row keeps wait_group 1 exact
+    cp_async_wait1();
+    __syncwarp();
+    const double* vals = st + (j & 1) * cmax * LANE_GROUP + i;
+    const unsigned long long m = umask[j];
     const double bj = w[0];
-    xp[2 * j] = bj * Urow[0];
-    // Only the listed entries issue an FMA.  The mask is the same for the
-    // whole warp, so this loop branches (a predicated-off FP64 instruction
-    // would still hold the FP64 pipe); each entry's value is loaded in its
-    // case (the row was prefetched into L1), so only the window stays live.
+    if (act) xp[2 * j] = bj * vals[0];
     unsigned long long mm = m & ~1ull;
+    int k = 1;
     while (mm) {
       const int t = __ffsll((long long)mm) - 1;
       mm &= mm - 1;
-      const double ut = Urow[t * LANE_GROUP];
+      const double ut = vals[(k++) * LANE_GROUP];
       switch (t) {
 #define SP_LANE_CASE(T)                          \
   case T:                                        \
@@ -841,25 +842,34 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, const double
     }
 #pragma unroll
     for (int t = 0; t < KUU; ++t) w[t] = w[t + 1];
-    w[KUU] = (j - KUU - 1 >= 0) ? yp[(size_t)2 * (j - KUU - 1) * LANE_GROUP] : 0.0;
+    const int row = j - KUU - 1;
+    w[KUU] = (act && row >= 0) ? yp[(size_t)2 * row * LANE_GROUP] : 0.0;
+    __syncwarp();                                // buffer j & 1 is refilled for row j - 2 next
   }
+  cp_async_wait0();
 }
 
-// The (kl, kl + ku) pairs compiled: the 3D Rayleigh-Benard pencil (9, 38)
-// and the 2D one (7, 29).
 bool lanes_supported(int kl, int kuu) { return (kl == 9 && kuu == 38) || (kl == 7 && kuu == 29); }
 
-cudaError_t launch_pencil_lanes(cudaStream_t s, int P, int n, int kl, int kuu, const double* Lg, const double* Ug,
-                                const uint8_t* pg, const unsigned long long* umask, const double2* b, double2* y,
-                                double2* x) {
+cudaError_t launch_pencil_lanes(cudaStream_t s, int P, int n, int kl, int kuu, const double* Lg, const double* Uc,
+                                int cmax, const uint8_t* pg, const unsigned long long* umask, const double2* b,
+                                double2* y, double2* x) {
   const int threads = 2 * P;
   const int grid = (threads + 127) / 128;
-  if (kl == 9 && kuu == 38)
-    k_pencil_lanes<9, 38><<<grid, 128, 0, s>>>(P, n, Lg, Ug, pg, umask, b, y, x);
-  else if (kl == 7 && kuu == 29)
-    k_pencil_lanes<7, 29><<<grid, 128, 0, s>>>(P, n, Lg, Ug, pg, umask, b, y, x);
-  else
+  const size_t smem = (size_t)4 * 2 * cmax * LANE_GROUP * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (kl == 9 && kuu == 38) {
+    if ((e = cudaFuncSetAttribute(k_pencil_lanes<9, 38>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ==
+        cudaSuccess)
+      k_pencil_lanes<9, 38><<<grid, 128, smem, s>>>(P, n, cmax, Lg, Uc, pg, umask, b, y, x);
+  } else if (kl == 7 && kuu == 29) {
+    if ((e = cudaFuncSetAttribute(k_pencil_lanes<7, 29>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ==
+        cudaSuccess)
+      k_pencil_lanes<7, 29><<<grid, 128, smem, s>>>(P, n, cmax, Lg, Uc, pg, umask, b, y, x);
+  } else {
     return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -883,26 +893,31 @@ cudaError_t launch_u_mask(cudaStream_t s, int P, int n, int npad, int kuu, int u
   return cudaGetLastError();
 }
 
-// Copy a factor into the lane-interleaved layout (one thread per pencil row).
-__global__ void k_factor_relayout(int P, int n, int npad, int kl, int kuu, int lpad, int upad,
+// Copy a factor into the lane layout (one thread per pencil row): dense
+// multipliers and pivots, and the U entries listed in umask[j] in order of t.
+__global__ void k_factor_relayout(int P, int n, int npad, int kl, int kuu, int lpad, int upad, int cmax,
                                   const double* __restrict__ L, const uint8_t* __restrict__ piv,
-                                  const double* __restrict__ U, double* __restrict__ Lg, double* __restrict__ Ug,
-                                  uint8_t* __restrict__ pg) {
+                                  const double* __restrict__ U, const unsigned long long* __restrict__ umask,
+                                  double* __restrict__ Lg, double* __restrict__ Uc, uint8_t* __restrict__ pg) {
   const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (idx >= (size_t)P * n) return;
   const int p = (int)(idx / n), j = (int)(idx - (size_t)p * n);
   const int g = p / LANE_GROUP, i = p - g * LANE_GROUP;
   const size_t row = (size_t)g * n + j;
   for (int t = 0; t < kl; ++t) Lg[(row * kl + t) * LANE_GROUP + i] = L[((size_t)p * npad + j) * lpad + t];
-  for (int t = 0; t <= kuu; ++t) Ug[(row * (kuu + 1) + t) * LANE_GROUP + i] = U[((size_t)p * npad + j) * upad + t];
+  const double* col = U + ((size_t)p * npad + j) * upad;
+  const unsigned long long m = umask[j];
+  int k = 0;
+  for (int t = 0; t <= kuu && k < cmax; ++t)
+    if ((m >> t) & 1ull) Uc[(row * cmax + k++) * LANE_GROUP + i] = col[t];
   pg[row * LANE_GROUP + i] = piv[(size_t)p * npad + j];
 }
 
 cudaError_t launch_factor_relayout(cudaStream_t s, int P, int n, int npad, int kl, int kuu, int lpad, int upad,
                                    const BandFactor& f) {
   const size_t total = (size_t)P * n;
-  k_factor_relayout<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P, n, npad, kl, kuu, lpad, upad, f.L, f.piv,
-                                                                   f.U, f.Lg, f.Ug, f.pg);
+  k_factor_relayout<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(P, n, npad, kl, kuu, lpad, upad, f.cmax, f.L,
+                                                                   f.piv, f.U, f.umask, f.Lg, f.Ug, f.pg);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,8 @@ struct BandFactor {
   double* rd = nullptr;         // [P][npad]        1/U_jj (0 on padding columns)
   // lane-interleaved copies for k_pencil_lanes (groups of LANE_GROUP pencils):
   double* Lg = nullptr;         // [G][n][kl][16]
-  double* Ug = nullptr;         // [G][n][kl+ku+1][16]  t=0: 1/U_jj
+  double* Ug = nullptr;         // [G][n][cmax][16]  the listed U entries of column j (k = 0: 1/U_jj)
+  int cmax = 0;                 // most entries listed for one column
   uint8_t* pg = nullptr;        // [G][n][16]
   unsigned long long* umask = nullptr;   // [n] bit t: U_{j-t,j} != 0 in some pencil (bit 0 set)
 };
@@ -95,7 +96,7 @@ struct SolveArgs {
   // (or -1), row_bc[r] = boundary row index q (or -1)
   const int32_t* row_f; const int32_t* row_bc;
   // factor in the lane-interleaved layout (null: not available)
-  const double* Lg; const double* Ug; const uint8_t* pg; const unsigned long long* umask;
+  const double* Lg; const double* Ug; const uint8_t* pg; const unsigned long long* umask; int cmax;
 };
 
 // Transform arguments.
@@ -156,9 +157,9 @@ cudaError_t launch_pencil_solve_batched(cudaStream_t s, const SolveArgs* args, c
 // [G][n][16] complex.  Returns cudaErrorInvalidValue when (kl, kl + ku) has
 // no compiled instance (lanes_supported).
 bool lanes_supported(int kl, int kuu);
-cudaError_t launch_pencil_lanes(cudaStream_t s, int P, int n, int kl, int kuu, const double* Lg, const double* Ug,
-                                const uint8_t* pg, const unsigned long long* umask, const double2* b, double2* y,
-                                double2* x);
+cudaError_t launch_pencil_lanes(cudaStream_t s, int P, int n, int kl, int kuu, const double* Lg, const double* Uc,
+                                int cmax, const uint8_t* pg, const unsigned long long* umask, const double2* b,
+                                double2* y, double2* x);
 // umask[j] |= bit t for every t <= kuu with U_{j-t,j} != 0 in some pencil
 // (umask zeroed by the caller)
 cudaError_t launch_u_mask(cudaStream_t s, int P, int n, int npad, int kuu, int upad, const double* U,
