@@ -691,6 +691,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// doubles of shared memory per warp: two forward buffers (multipliers and
+// pivots) or two backward buffers (listed U entries), whichever is larger
+__host__ __device__ inline int lane_stride(int kl, int cmax) {
+  const int fw = 2 * (kl * LANE_GROUP + 2), bw = 2 * cmax * LANE_GROUP;
+  return fw > bw ? fw : bw;
+}
+
 template <int KL, int KUU>
 __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, const double* __restrict__ Lg,
                                                       const double* __restrict__ Uc,
@@ -709,14 +716,32 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, co
   const double* bp = reinterpret_cast<const double*>(b + (size_t)(act ? pen : 0) * n) + comp;
   double* yp = reinterpret_cast<double*>(y + (size_t)g * n * LANE_GROUP + i) + comp;   // row j at yp[2 j LANE_GROUP]
   const size_t gn = (size_t)g * n;
-  // forward: row interchanges and unit-lower multipliers; win[t] = row j + t
-  if (act) {
+  // per-warp staging area (lane_stride doubles): forward rows, then backward rows
+  double* st = lane_stage + (size_t)(threadIdx.x >> 5) * lane_stride(KL, cmax);
+  // forward: row interchanges and unit-lower multipliers; win[t] = row j + t.
+  // Each row's multipliers and pivot offsets for the warp's 16 pencils are
+  // copied into shared memory one row ahead (cp.async, two buffers).
+  constexpr int FW = KL * LANE_GROUP + 2;        // doubles per forward buffer (+16 bytes of pivots)
+  auto fstage = [&](int jr) {
+    const double* src = Lg + (gn + jr) * KL * LANE_GROUP;
+    double* dst = st + (jr & 1) * FW;
+    for (int c = lane; c < KL * (LANE_GROUP / 2); c += 32) cp_async16(dst + 2 * c, src + 2 * c);
+    if (lane == 31) cp_async16(dst + KL * LANE_GROUP, pg + (gn + jr) * LANE_GROUP);
+    cp_async_commit();
+  };
+  {
     double win[KL + 1];
 #pragma unroll
-    for (int t = 0; t <= KL; ++t) win[t] = (t < n) ? bp[2 * t] : 0.0;
+    for (int t = 0; t <= KL; ++t) win[t] = (act && t < n) ? bp[2 * t] : 0.0;
+    fstage(0);
     for (int j = 0; j < n; ++j) {
-      const int off = pg[(gn + j) * LANE_GROUP + i];
-      const double* Lrow = Lg + (gn + j) * KL * LANE_GROUP + i;
+      if (j + 1 < n) fstage(j + 1);
+      else cp_async_commit();
+      cp_async_wait1();
+      __syncwarp();
+      const double* Ls = st + (j & 1) * FW;
+      const int off = reinterpret_cast<const uint8_t*>(Ls + KL * LANE_GROUP)[i];
+      const double* Lrow = Ls + i;
       double piv_val = win[0];
 #pragma unroll
       for (int t = 1; t <= KL; ++t) piv_val = (off == t) ? win[t] : piv_val;
@@ -728,8 +753,11 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, co
       for (int t = 1; t <= KL; ++t) win[t] = fma(-Lrow[(t - 1) * LANE_GROUP], yj, win[t]);
 #pragma unroll
       for (int t = 0; t < KL; ++t) win[t] = win[t + 1];
-      win[KL] = (j + KL + 1 < n) ? bp[2 * (j + KL + 1)] : 0.0;
+      win[KL] = (act && j + KL + 1 < n) ? bp[2 * (j + KL + 1)] : 0.0;
+      __syncwarp();                              // buffer j & 1 is refilled for row j + 2 next
     }
+    cp_async_wait0();
+    __syncwarp();
   }
   // back substitution with the scaled columns U_{j-t,j} / U_jj.  Only entries
   // nonzero in some pencil are stored: the k-th set bit t of umask[j] holds
@@ -739,7 +767,6 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, co
   // the whole warp, so the loop branches (a predicated-off FP64 instruction
   // would still hold the FP64 pipe) and jumps to the FMA of its window
   // register.  The rows of y this lane wrote are read back by this lane only.
-  double* st = lane_stage + (size_t)(threadIdx.x >> 5) * 2 * cmax * LANE_GROUP;
   auto stage = [&](int jr) {
     const int cnt = __popcll(umask[jr]);
     const double* src = Uc + (gn + jr) * (size_t)cmax * LANE_GROUP;
@@ -856,7 +883,7 @@ cudaError_t launch_pencil_lanes(cudaStream_t s, int P, int n, int kl, int kuu, c
                                 double2* y, double2* x) {
   const int threads = 2 * P;
   const int grid = (threads + 127) / 128;
-  const size_t smem = (size_t)4 * 2 * cmax * LANE_GROUP * sizeof(double);
+  const size_t smem = (size_t)4 * lane_stride(kl, cmax) * sizeof(double);
   cudaError_t e = cudaSuccess;
   if (kl == 9 && kuu == 38) {
     if ((e = cudaFuncSetAttribute(k_pencil_lanes<9, 38>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ==
