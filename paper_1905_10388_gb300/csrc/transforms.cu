@@ -130,12 +130,17 @@ __device__ __forceinline__ void cheb_forward_body(const ZDesc& d, int bx, int e,
 //   mode & 2: evaluate the bilinear terms (else pass the fields through)
 //   mode & 4: output spectra to h (else real rows to grid_out)
 // ---------------------------------------------------------------------------
+// Field pairs transformed at once in the x-row kernel: the FFT buffers hold
+// this many pairs, so many-field rows (3D: 15 fields) keep shared memory low
+// enough for several CTAs per SM.
+constexpr int X_PAIRS = 2;
+
 template <typename T>
 __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsigned char* smem_raw) {
   const int N = d.N, K = d.K, rows = d.rows, mode = d.mode, nf = d.nf, ne = d.ne;
   const int nout = (mode & 2) ? ne : nf;
   const int nbi = (nf + 1) / 2, nbo = (nout + 1) / 2;
-  const int nbmax = max(nbi, nbo);
+  const int nbmax = max(min(nbi, X_PAIRS), nbo);
   C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* b1 = b0 + (size_t)nbmax * N;
   C<T>* tws = b1 + (size_t)nbmax * N;
@@ -147,8 +152,10 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
   const int tid = threadIdx.x, nt = blockDim.x;
 
   if (mode & 1) {
-    for (int idx = tid; idx < nbi * N; idx += nt) {
-      const int q = idx / N, k = idx - q * N;
+   for (int q0 = 0; q0 < nbi; q0 += X_PAIRS) {
+    const int nb = min(X_PAIRS, nbi - q0);
+    for (int idx = tid; idx < nb * N; idx += nt) {
+      const int q = q0 + idx / N, k = idx - (idx / N) * N;
       const int fa = 2 * q, fb = 2 * q + 1;
       auto spec = [&](int f, int kk) -> C<T> {
         if (f >= nf) return mk<T>(0, 0);
@@ -174,12 +181,14 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
       b0[idx] = z;
     }
     __syncthreads();
-    C<T>* res = fft_batched<T>(b0, b1, N, d.radix3, tws, +1, nbi);
-    for (int idx = tid; idx < nbi * N; idx += nt) {
-      const int q = idx / N, i = idx - q * N;
+    C<T>* res = fft_batched<T>(b0, b1, N, d.radix3, tws, +1, nb);
+    for (int idx = tid; idx < nb * N; idx += nt) {
+      const int q = q0 + idx / N, i = idx - (idx / N) * N;
       G[(size_t)(2 * q) * N + i] = res[idx].x;
       if (2 * q + 1 < nf) G[(size_t)(2 * q + 1) * N + i] = res[idx].y;
     }
+    __syncthreads();                             // b0 / b1 are reused by the next pairs
+   }
   } else {
     for (int idx = tid; idx < nf * N; idx += nt) {
       const int f = idx / N, i = idx - f * N;
@@ -482,7 +491,7 @@ size_t z_smem_bytes(int prec, int Ng, int tile) {
 }
 size_t x_smem_bytes(int prec, int N, int mode, int nf, int ne) {
   const int nout = (mode & 2) ? ne : nf;
-  const int nbmax = std::max((nf + 1) / 2, (nout + 1) / 2);
+  const int nbmax = std::max(std::min((nf + 1) / 2, X_PAIRS), (nout + 1) / 2);
   const size_t esz = prec ? sizeof(float) : sizeof(double);
   size_t smem = (2ull * nbmax + 1) * N * 2 * esz + (size_t)nf * N * esz;
   if (mode & 2) smem += (size_t)ne * N * esz;
