@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_cheb_forward_batched(const ZDesc*
   const int4 w = work[blockIdx.x];
   cheb_forward_body<T, TP>(ds[w.x], w.y, w.z, smem_raw);
 }
-constexpr int Y_TILE = 8;
+constexpr int Y_TILE = 4;
 template <typename T>
 __global__ void __launch_bounds__(Z_THREADS) k_fourier_y(YDesc d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -507,7 +507,9 @@ static cudaError_t set_smem(K kernel, size_t smem) {
 // Pencil columns per CTA for a single-problem z launch: the widest tile that
 // still gives at least two CTAs per SM (152 SMs).
 static int z_tile_for(int P, int nfields) {
-  for (int t : {16, 8}) if ((long long)((P + t - 1) / t) * nfields >= 2 * 152) return t;
+  // 8 columns: (2 * 8 + 1) N_gz complex of shared memory, up to eight
+  // 256-thread CTAs per SM at N_gz = 192 in FP32
+  if ((long long)((P + 7) / 8) * nfields >= 2 * 152) return 8;
   return 4;
 }
 
