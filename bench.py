@@ -230,7 +230,8 @@ def run_ours(args):
     factor_mb = s.P * n_ * (2 * kl_ + ku_ + 1) * 8 / 1e6
     achieved = flops / (solve_ms * 1e-3) / 1e12
     peaks = measured_peaks()
-    roof = {"kernel": "k_pencil_solve", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+    kernel = "k_pencil_stage<1> + k_pencil_lanes + k_pencil_stage<2>" if lanes else "k_pencil_solve"
+    roof = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": solve_traffic(args.workload, args.precision), "algorithmic_bytes": nbytes,
             "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/cycle x 2.07 GHz)",

@@ -215,20 +215,21 @@ __host__ __device__ inline size_t solve_smem_bytes(int npad, int lpad, int upad)
   return off;
 }
 
-// PPC pencils per CTA of 128 threads (1 or 2); with PPC = 2 threads
-// [0, 64) serve pencil 2b and [64, 128) pencil 2b + 1, each half with its own
-// shared-memory region.
-template <int RU, int PPC, int MODE = -1>
+// PPC pencils per CTA of NT threads (1 or 2); with PPC = 2 threads
+// [0, NT/2) serve pencil 2b and [NT/2, NT) pencil 2b + 1, each half with its
+// own shared-memory region.  Warps 0 and 1 of a pencil substitute; all NT/PPC
+// threads share the assembly and the epilogue.
+template <int RU, int PPC, int MODE = -1, int NT = 128>
 __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block, unsigned char* smem_raw) {
   // MODE >= 0 fixes the stage at compile time (assembly-only and
   // epilogue-only kernels carry neither the factor ring nor the substitution)
   const int mode = MODE >= 0 ? MODE : a.mode;
   const int lp = mode == 0 ? a.lpad : 0, up = mode == 0 ? a.upad : 0;
-  const int half = (PPC == 2) ? (threadIdx.x >> 6) : 0;
+  const int half = (PPC == 2) ? (int)(threadIdx.x / (NT / 2)) : 0;
   const int p = block * PPC + half;
   const bool active = p < a.P;
-  const int tid = (PPC == 2) ? (threadIdx.x & 63) : threadIdx.x;
-  const int nt = 128 / PPC;
+  const int tid = (PPC == 2) ? (int)(threadIdx.x % (NT / 2)) : (int)threadIdx.x;
+  const int nt = NT / PPC;
   const int n = a.n;
   SolveSmem sm;
   {
@@ -604,10 +605,14 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   if (!finite) raise_status(a.status, SP_ERR_NONFINITE, p);
 }
 
+// 256 threads: two pencils' CTAs fit on one SM (registers capped at 128 per
+// thread), and the assembly and epilogue, bound by dependent global loads,
+// run twice as wide as with the two substituting warps' 128
+constexpr int SOLVE_THREADS = 256;
 template <int RU, int PPC>
-__global__ void __launch_bounds__(128, 1) k_pencil_solve(SolveArgs a) {
+__global__ void __launch_bounds__(SOLVE_THREADS, 2) k_pencil_solve(SolveArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  pencil_solve_body<RU, PPC>(a, blockIdx.x, smem_raw);
+  pencil_solve_body<RU, PPC, -1, SOLVE_THREADS>(a, blockIdx.x, smem_raw);
 }
 
 // right-hand-side assembly only (MODE 1) or epilogue only (MODE 2), around
@@ -661,10 +666,10 @@ cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a) {
   const int grid = (a.P + PPC - 1) / PPC;
   if (a.kuu <= 31) {
     cudaFuncSetAttribute(k_pencil_solve<1, PPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_pencil_solve<1, PPC><<<grid, 128, smem, s>>>(a);
+    k_pencil_solve<1, PPC><<<grid, SOLVE_THREADS, smem, s>>>(a);
   } else {
     cudaFuncSetAttribute(k_pencil_solve<2, PPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_pencil_solve<2, PPC><<<grid, 128, smem, s>>>(a);
+    k_pencil_solve<2, PPC><<<grid, SOLVE_THREADS, smem, s>>>(a);
   }
   return cudaGetLastError();
 }
