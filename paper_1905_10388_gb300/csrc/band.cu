@@ -485,8 +485,9 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
       }
     }
     // backward: scaled U columns (U_{j-t,j}/U_jj), window of 32*RU entries;
-    // x_j = b_j / U_jj is applied in the epilogue
+    // x_j = b_j / U_jj is applied once per chunk, lane l to row j0 + l
     constexpr int W = 32 * RU;
+    const double* rdp = a.rd + (size_t)pp * a.npad;
     const int npad = a.npad;
     double w[RU], nw[RU];
 #pragma unroll
@@ -508,6 +509,8 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
       }
       const double* Uc = sm.Uring + (size_t)s * SOLVE_CHUNK * a.upad;
       const int j0 = (nchunks - 1 - k) * SOLVE_CHUNK;
+      const double rdl = rdp[j0 + lane];   // used after the chunk: off the chain
+      double xo = 0.0;
 #pragma unroll
       for (int jj = 31; jj >= 0; --jj) {
         const int j = j0 + jj;
@@ -525,7 +528,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
         }
         const double nxt = (j - 2 * W >= 0) ? Bd[2 * (j - 2 * W)] : 0.0;   // same address in every lane
         const bool own = (lane == jj);
-        if (own) Bd[2 * j] = bj;
+        xo = own ? bj : xo;
 #pragma unroll
         for (int r = 0; r < RU; ++r) {
           const bool take = own && (oreg == r);
@@ -533,6 +536,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
           nw[r] = take ? nxt : nw[r];
         }
       }
+      Bd[2 * (j0 + lane)] = xo * rdl;
     }
     if (!ok && tid == 0) {
       // report, then let every copy in flight land before the CTA exits
@@ -547,17 +551,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   __syncthreads();
   const bool work = active && !*sm.abort_flag;
 
-  // ---- epilogue: x_j = b_j / U_jj, store X~, recombine to T
-  //      coefficients, optional M~ X~
-  {
-    const double* rdp = a.rd + (size_t)pp * a.npad;
-    for (int r = tid; work && mode == 0 && r < n; r += nt) {
-      const double q = rdp[r];
-      const double2 b = sm.B[r];
-      sm.B[r] = make_double2(b.x * q, b.y * q);
-    }
-    __syncthreads();
-  }
+  // ---- epilogue: store X~, recombine to T coefficients, optional M~ X~
   bool finite = true;
   for (int r = tid; work && r < n; r += nt) {
     const double2 x = sm.B[r];
