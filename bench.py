@@ -54,8 +54,8 @@ FP64_PEAK_TFLOPS = 1.25
 # k_pencil_solve launch of the 512x256 SBDF2 mixed-precision step, from one
 # ncu capture of `bench.py --steps 3 --warmup 3 --no-cpu-baseline`.  It is
 # reported only while the kernel's sources hash to the captured ones.
-SOLVE_TRAFFIC = {"workload": "rb2d_512x256_sbdf2", "precision": "mixed", "bytes": 180.246272e6,
-                 "sources_sha256": "572ce4ef08833199e8f2a1c02a76d1d5bc7cf8dccee8e403476de8ad401058b4"}
+SOLVE_TRAFFIC = {"workload": "rb2d_512x256_sbdf2", "precision": "mixed", "bytes": 180.793344e6,
+                 "sources_sha256": "f922839f2b894bdcc4456e75f6a0410f8c7cc03c084d6b583782815d9529630d"}
 SOLVE_SOURCES = ("paper_1905_10388_gb300/csrc/band.cu", "paper_1905_10388_gb300/csrc/internal.h",
                  "paper_1905_10388_gb300/csrc/common.cuh")
 
@@ -137,22 +137,26 @@ def solve_flops_bytes(s):
     """Algorithmic FP64 flops and bytes of one pencil-solve launch.
 
     Per pencil and per real right-hand side (real and imaginary parts share
-    the real factor): forward substitution kl FMAs per row, back
-    substitution kl + ku FMAs per row and one multiply by 1/U_jj; plus the
-    right-hand-side assembly (one CSR matvec with the pattern's nnz, the
-    combination of stored vectors) and the epilogue matvec M~ X~.
-    Bytes: the factor (L multipliers, pivots, U band) plus the vectors read
+    the real factor): the substitution's multiply-adds per row as the
+    library reports them (sp_get_solve_work: kl forward plus kl + ku back
+    for the window kernel, which multiplies every band entry; kl plus the
+    listed U entries for the lane kernel, which skips the band's structural
+    zeros) and one multiply by 1/U_jj; plus the right-hand-side assembly
+    (one CSR matvec with the pattern's nnz, the combination of stored
+    vectors) and the epilogue matvec M~ X~.
+    Bytes: the stored factor as the kernel reads it plus the vectors read
     and written, all FP64.
     """
     n, kl, ku = s.band()
+    fma_row, factor_pencil = s.solve_work()
     P = s.P
     M1 = s.assembly["M"][1] if "M" in s.assembly else s.assembly["values"](1, 2)[0][0]
     nnz_M = int(np.count_nonzero(M1))
     ne = len(s.nl_eqs)
-    solve = 2 * (2 * kl + ku) * n + n                  # per real RHS
+    solve = 2 * fma_row * n + n                        # per real RHS
     flops = P * 2 * solve + P * 2 * 2 * nnz_M          # + epilogue M~ X~ (complex vector)
     flops += P * 2 * 2 * 3 * n                         # prologue combination of 2 vectors + F rows
-    factor_bytes = P * n * (kl + (kl + ku + 1)) * 8 + P * n
+    factor_bytes = P * factor_pencil
     vec_bytes = P * n * 16 * 5                         # 2 stored vectors in, X~, X, M~X~ out
     vec_bytes += P * nnz_M * 8 + ne * P * s.Nz * 16 * 2  # M~ values, two F coefficient arrays
     return flops, factor_bytes + vec_bytes

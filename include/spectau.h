@@ -259,6 +259,21 @@ sp_status sp_eval_rhs(sp_ctx* ctx, int problem, void* out_host, int* n_eq);
  * superdiagonals after pivoting). */
 sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku);
 
+/* Work of one pencil substitution as the problem's solve kernel performs it
+ * (Sec. "Matrix solvers": forward substitution with L, back substitution
+ * with U), for the factor that the steady steps use (the last one of
+ * sp_factor: SBDF2's, not its SBDF1 start):
+ *   fma_per_row   multiply-adds per row and real right-hand side, forward
+ *                 plus back.  Window kernel: kl + (kl + ku), every band
+ *                 entry.  Lane kernel: kl + the mean number of listed
+ *                 superdiagonal entries of U per column (the union of the
+ *                 pencils' nonzero patterns); one multiply by 1/U_jj per row
+ *                 comes on top in both.
+ *   factor_bytes  bytes of stored factor one pencil's substitution reads
+ *                 (multipliers, U entries including 1/U_jj, pivot bytes).
+ * Either pointer may be NULL.  SP_ERR_NOT_FACTORED before sp_factor. */
+sp_status sp_get_solve_work(sp_ctx* ctx, int problem, double* fma_per_row, double* factor_bytes);
+
 /* Launch timing of the pencil-solve kernel (the step's dominant kernel):
  * sp_set_timing reserves CUDA-event pairs for up to max_launches solve
  * launches of sp_step (not of graph replays) and restarts the count

@@ -30,7 +30,7 @@ EXPORTS = (
     "sp_dz", "sp_step", "sp_step_graph", "sp_sync_status", "sp_transform", "sp_eval_rhs",
     "sp_get_band", "sp_set_timing", "sp_last_solve_time", "sp_transform_backward_static",
     "sp_step_batched", "sp_batch_tile", "sp_adjoint_init", "sp_step_adjoint", "sp_transform_adjoint",
-    "sp_dz_adjoint", "sp_step_record", "sp_set_solve_kernel",
+    "sp_dz_adjoint", "sp_step_record", "sp_set_solve_kernel", "sp_get_solve_work",
 )
 
 
@@ -72,6 +72,7 @@ _SIGS = {
     "sp_transform": [P, I, P, P, I, I, I, I, I],
     "sp_eval_rhs": [P, I, P, ctypes.POINTER(I)],
     "sp_get_band": [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)],
+    "sp_get_solve_work": [P, I, ctypes.POINTER(D), ctypes.POINTER(D)],
     "sp_set_timing": [P, I, I],
     "sp_last_solve_time": [P, I, ctypes.POINTER(D), ctypes.POINTER(I)],
     "sp_transform_backward_static": [P, P, I, I, I, I, I, P, ctypes.c_char_p, I],

@@ -1078,7 +1078,12 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
       if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
       if (e != cudaSuccess) { cudaFree(work); CK(e); }
       int cmax = 1;
-      for (unsigned long long m : hm) cmax = std::max(cmax, __builtin_popcountll(m));
+      double listed = 0;
+      for (unsigned long long m : hm) {
+        cmax = std::max(cmax, __builtin_popcountll(m));
+        listed += __builtin_popcountll(m) - 1;
+      }
+      bf.u_listed = listed / pr->n;
       if (cmax != bf.cmax || !bf.Ug) {
         if (bf.Ug) cudaFree(bf.Ug);
         bf.Ug = nullptr;
@@ -1746,6 +1751,26 @@ sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku) {
   if (n) *n = pr->n;
   if (kl) *kl = pr->kl;
   if (ku) *ku = pr->ku;
+  return SP_OK;
+}
+
+sp_status sp_get_solve_work(sp_ctx* ctx, int problem, double* fma_per_row, double* factor_bytes) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (!pr->factored) return fail(ctx, SP_ERR_NOT_FACTORED, "sp_factor has not been called");
+  const BandFactor& f = pr->fac[pr->nfac - 1];
+  const double n = pr->n, kl = pr->kl, kuu = pr->kl + pr->ku;
+  double fma, bytes;
+  if (pr->lanes) {
+    fma = kl + f.u_listed;
+    bytes = n * (kl + f.cmax) * 8.0 + n;
+  } else {
+    fma = kl + kuu;
+    bytes = n * (kl + kuu + 1) * 8.0 + n;
+  }
+  if (fma_per_row) *fma_per_row = fma;
+  if (factor_bytes) *factor_bytes = bytes;
   return SP_OK;
 }
 

@@ -27,6 +27,7 @@ struct BandFactor {
   double* Lg = nullptr;         // [G][n][kl][16]
   double* Ug = nullptr;         // [G][n][cmax][16]  the listed U entries of column j (k = 0: 1/U_jj)
   int cmax = 0;                 // most entries listed for one column
+  double u_listed = 0;          // mean listed entries per column, the diagonal excluded
   uint8_t* pg = nullptr;        // [G][n][16]
   unsigned long long* umask = nullptr;   // [n] bit t: U_{j-t,j} != 0 in some pencil (bit 0 set)
 };

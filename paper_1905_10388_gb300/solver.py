@@ -149,6 +149,14 @@ class TauSolver:
         L.check(h, L.lib().sp_get_band(h, self.pid, ctypes.byref(n), ctypes.byref(kl), ctypes.byref(ku)))
         return n.value, kl.value, ku.value
 
+    def solve_work(self):
+        """(multiply-adds per row and real right-hand side, factor bytes per
+        pencil) of the substitution as the solve kernel performs it."""
+        fma, nb = ctypes.c_double(), ctypes.c_double()
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_get_solve_work(h, self.pid, ctypes.byref(fma), ctypes.byref(nb)))
+        return fma.value, nb.value
+
     # -- state -----------------------------------------------------------------
     def set_field(self, name, data, layout="c"):
         h = self.ctx.handle

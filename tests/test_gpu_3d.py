@@ -194,6 +194,13 @@ def test_lane_substitution_equals_window(ctx, case):
         s.step(4)
         s.sync()
         out.append(s.get_state())
+        # work the kernel reports: every band entry (window) or the listed ones
+        n, kl, ku = s.band()
+        fma, nbytes = s.solve_work()
+        if kind == "window":
+            assert fma == 2 * kl + ku and nbytes == n * (2 * kl + ku + 1) * 8 + n
+        else:
+            assert kl < fma < 2 * kl + ku and n * (kl + 1) * 8 < nbytes < n * (2 * kl + ku + 2) * 8
     assert np.isfinite(out[0]).all()
     if scheme == "SBDF2":
         assert np.array_equal(out[0], out[1])
