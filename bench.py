@@ -231,7 +231,7 @@ def run_ours(args):
     # the library's automatic choice of substitution kernel (sp_set_solve_kernel):
     # assembly, lane substitution and epilogue are three launches
     lanes = s.P >= 4096 and (kl_, kl_ + ku_) in ((9, 38), (7, 29))
-    factor_mb = s.P * n_ * (2 * kl_ + ku_ + 1) * 8 / 1e6
+    factor_mb = s.P * s.solve_work()[1] / 1e6
     achieved = flops / (solve_ms * 1e-3) / 1e12
     peaks = measured_peaks()
     kernel = "k_pencil_stage<1> + k_pencil_lanes + k_pencil_stage<2>" if lanes else "k_pencil_solve"
