@@ -191,6 +191,43 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src) {
 // ---------------------------------------------------------------------------
 // pencil solve: prologue (B~ assembly) -> L pass -> U pass -> epilogue
 // ---------------------------------------------------------------------------
+// acc + the left-preconditioned F~ entry of row (slot sl, mode m): the
+// combination sum_k c_k F_k of the stored right-hand sides, through the
+// T-to-U conversion P^L for differential equations (Appendix: row m holds
+// (1 + delta_m0)/2 F_m - F_{m+2}/2) and the phase i^-q of the equation's
+// real-ification.  One FMA per term and component: on GB300 every FP64
+// instruction holds the sub-partition's FP64 pipe for 64 cycles, so the
+// halves come from cH = c/2 and cM = -c/2 and the phase is applied to the
+// loaded values (a sign and swap, no arithmetic).
+__device__ __forceinline__ double2 add_f_row(const SolveArgs& a, int sl, int m, int p, const double* cH,
+                                             const double* cM, double2 acc) {
+  const int Nz = a.Nz;
+  const int e = a.nl_eq[sl];
+  const bool dif = a.eq_differential[e] != 0;
+  const int ph = -a.eq_phase[e];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k >= a.nfc) break;
+    const double2* F = a.fc[k] + ((size_t)sl * a.P + p) * Nz;
+    const double2 v0 = cipow_d(F[m], ph);
+    const double c = (dif && m > 0) ? cH[k] : a.fc_coef[k];
+    acc.x = fma(c, v0.x, acc.x);
+    acc.y = fma(c, v0.y, acc.y);
+    if (dif && m + 2 < Nz) {
+      const double2 v2 = cipow_d(F[m + 2], ph);
+      acc.x = fma(cM[k], v2.x, acc.x);
+      acc.y = fma(cM[k], v2.y, acc.y);
+    }
+  }
+  return acc;
+}
+
+// c v, exactly v when c = 1 (tested on the bit pattern: no FP64 compare)
+__device__ __forceinline__ double2 scale_first(double c, double2 v) {
+  if (__double_as_longlong(c) == 0x3FF0000000000000LL) return v;
+  return make_double2(c * v.x, c * v.y);
+}
+
 struct SolveSmem {
   double2* B;
   double* Lring;
@@ -288,6 +325,14 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   //      boundary values
   const size_t prow = (size_t)pp * n;
   const int Nz = a.Nz;
+  // halves of the F~ coefficients for the T-to-U rows (exact scalings,
+  // once per thread rather than once per row)
+  double cH[3], cM[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    cH[k] = 0.5 * a.fc_coef[k];
+    cM[k] = -0.5 * a.fc_coef[k];
+  }
   if (mode == 2) {
     // epilogue only: X~ (already divided by U_jj) from the substitution kernel
     for (int r = tid; active && r < n; r += nt) sm.B[r] = a.xg[prow + r];
@@ -299,7 +344,8 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   // its boundary value
   for (int r = tid; active && r < n; r += nt) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int k = 0; k < a.nvec; ++k) {
+    if (a.nvec > 0) acc = scale_first(a.vec_coef[0], a.vec[0][prow + r]);
+    for (int k = 1; k < a.nvec; ++k) {
       const double2 v = a.vec[k][prow + r];
       acc.x = fma(a.vec_coef[k], v.x, acc.x);
       acc.y = fma(a.vec_coef[k], v.y, acc.y);
@@ -320,30 +366,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     const int fi = a.n_nl > 0 ? a.row_f[r] : -1;
     if (fi >= 0) {
       const int sl = fi / Nz, m = fi - sl * Nz;
-      const int e = a.nl_eq[sl];
-      double2 f0 = make_double2(0.0, 0.0), f2 = make_double2(0.0, 0.0);
-      for (int k = 0; k < a.nfc; ++k) {
-        const double2* F = a.fc[k] + ((size_t)sl * a.P + p) * Nz;
-        const double2 v0 = F[m];
-        f0.x = fma(a.fc_coef[k], v0.x, f0.x);
-        f0.y = fma(a.fc_coef[k], v0.y, f0.y);
-        if (m + 2 < Nz) {
-          const double2 v2 = F[m + 2];
-          f2.x = fma(a.fc_coef[k], v2.x, f2.x);
-          f2.y = fma(a.fc_coef[k], v2.y, f2.y);
-        }
-      }
-      double2 u;
-      if (a.eq_differential[e]) {
-        const double c0 = (m == 0) ? 1.0 : 0.5;
-        u.x = fma(c0, f0.x, -0.5 * f2.x);
-        u.y = fma(c0, f0.y, -0.5 * f2.y);
-      } else {
-        u = f0;
-      }
-      u = cipow_d(u, -a.eq_phase[e]);
-      acc.x += u.x;
-      acc.y += u.y;
+      acc = add_f_row(a, sl, m, p, cH, cM, acc);
     }
     const int q = a.nbc > 0 ? a.row_bc[r] : -1;
     if (q >= 0) {
@@ -357,7 +380,8 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   } else {
   for (int r = tid; active && r < n; r += nt) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int k = 0; k < a.nvec; ++k) {
+    if (a.nvec > 0) acc = scale_first(a.vec_coef[0], a.vec[0][prow + r]);
+    for (int k = 1; k < a.nvec; ++k) {
       const double2 v = a.vec[k][prow + r];
       acc.x = fma(a.vec_coef[k], v.x, acc.x);
       acc.y = fma(a.vec_coef[k], v.y, acc.y);
@@ -384,31 +408,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     const int e = a.nl_eq[sl];
     const int row = a.row_map[e * Nz + m];
     if (row < 0) continue;
-    double2 f0 = make_double2(0.0, 0.0), f2 = make_double2(0.0, 0.0);
-    for (int k = 0; k < a.nfc; ++k) {
-      const double2* F = a.fc[k] + ((size_t)sl * a.P + p) * Nz;
-      const double2 v0 = F[m];
-      f0.x = fma(a.fc_coef[k], v0.x, f0.x);
-      f0.y = fma(a.fc_coef[k], v0.y, f0.y);
-      if (m + 2 < Nz) {
-        const double2 v2 = F[m + 2];
-        f2.x = fma(a.fc_coef[k], v2.x, f2.x);
-        f2.y = fma(a.fc_coef[k], v2.y, f2.y);
-      }
-    }
-    double2 u;
-    if (a.eq_differential[e]) {
-      const double c0 = (m == 0) ? 1.0 : 0.5;
-      u.x = fma(c0, f0.x, -0.5 * f2.x);
-      u.y = fma(c0, f0.y, -0.5 * f2.y);
-    } else {
-      u = f0;
-    }
-    u = cipow_d(u, -a.eq_phase[e]);
-    double2 b = sm.B[row];
-    b.x += u.x;
-    b.y += u.y;
-    sm.B[row] = b;
+    sm.B[row] = add_f_row(a, sl, m, p, cH, cM, sm.B[row]);
   }
   for (int q = tid; active && q < a.nbc; q += nt) {
     const int row = a.bc_rows[q];
