@@ -337,47 +337,13 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     // epilogue only: X~ (already divided by U_jj) from the substitution kernel
     for (int r = tid; active && r < n; r += nt) sm.B[r] = a.xg[prow + r];
     __syncthreads();
-  } else if (mode == 1) {
-  // assembly only, one pass per row straight to global memory: stored
-  // vectors, matvec, then the row's F~ entry (the left-preconditioned
-  // right-hand side of equation e, mode m, through the inverse row map) or
-  // its boundary value
-  for (int r = tid; active && r < n; r += nt) {
-    double2 acc = make_double2(0.0, 0.0);
-    if (a.nvec > 0) acc = scale_first(a.vec_coef[0], a.vec[0][prow + r]);
-    for (int k = 1; k < a.nvec; ++k) {
-      const double2 v = a.vec[k][prow + r];
-      acc.x = fma(a.vec_coef[k], v.x, acc.x);
-      acc.y = fma(a.vec_coef[k], v.y, acc.y);
-    }
-    if (a.mv_x != nullptr) {
-      double2 s = make_double2(0.0, 0.0);
-      const double* vals = a.mv_vals + (size_t)p * a.mv_nnz;
-      for (int e = a.mv_indptr[r]; e < a.mv_indptr[r + 1]; ++e) {
-        const double m = vals[e];
-        const double2 x = a.mv_x[prow + a.mv_indices[e]];
-        s.x = fma(m, x.x, s.x);
-        s.y = fma(m, x.y, s.y);
-      }
-      if (a.mv_store != nullptr) a.mv_store[prow + r] = s;
-      acc.x = fma(a.mv_coef, s.x, acc.x);
-      acc.y = fma(a.mv_coef, s.y, acc.y);
-    }
-    const int fi = a.n_nl > 0 ? a.row_f[r] : -1;
-    if (fi >= 0) {
-      const int sl = fi / Nz, m = fi - sl * Nz;
-      acc = add_f_row(a, sl, m, p, cH, cM, acc);
-    }
-    const int q = a.nbc > 0 ? a.row_bc[r] : -1;
-    if (q >= 0) {
-      const double2 g = a.bc_values[(size_t)p * a.nbc + q];
-      acc.x = fma(a.bc_coef, g.x, acc.x);
-      acc.y = fma(a.bc_coef, g.y, acc.y);
-    }
-    a.bg[prow + r] = acc;         // B~ for the substitution kernel
-  }
-  return;
   } else {
+  // modes 0 and 1: two passes over the rows, each with every lane on the
+  // same kind of row, since on GB300 an FP64 warp instruction holds the FP64
+  // pipe for 64 cycles whatever its active mask: stored vectors and matvec
+  // for every row, then the F~ entries by (slot, mode), then the boundary
+  // rows.  Mode 1 (assembly only) then stores B~ for the substitution
+  // kernel.
   for (int r = tid; active && r < n; r += nt) {
     double2 acc = make_double2(0.0, 0.0);
     if (a.nvec > 0) acc = scale_first(a.vec_coef[0], a.vec[0][prow + r]);
@@ -419,6 +385,10 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     sm.B[row] = b;
   }
   __syncthreads();
+  if (mode == 1) {
+    for (int r = tid; active && r < n; r += nt) a.bg[prow + r] = sm.B[r];   // B~ for the substitution kernel
+    return;
+  }
   }
 
 
