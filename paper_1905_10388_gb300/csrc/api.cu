@@ -90,6 +90,8 @@ struct Problem {
   // M~ on its own compact pattern (entries nonzero in at least one pencil)
   int64_t nnzM = 0;
   int32_t *d_indptrM = nullptr, *d_indicesM = nullptr;
+  int32_t* d_mrows = nullptr;   // rows of M~ with entries
+  int nmrows = 0;
   double* d_MvC = nullptr;
   int32_t *d_col_map = nullptr, *d_row_map = nullptr, *d_var_rec = nullptr, *d_var_ph = nullptr;
   int32_t *d_eq_diff = nullptr, *d_eq_ph = nullptr, *d_bc_rows = nullptr, *d_nl_eq = nullptr;
@@ -260,6 +262,12 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
       for (int64_t k = 0; k < pr->nnzM; ++k) mv[(size_t)p * pr->nnzM + k] = pr->Mv[(size_t)p * pr->nnz + src[k]];
     CK(upload(&pr->d_indptrM, ip, s));
     CK(upload(&pr->d_indicesM, ix, s));
+    std::vector<int32_t> mrows;
+    for (int r = 0; r < pr->n; ++r)
+      if (ip[r + 1] > ip[r]) mrows.push_back(r);
+    pr->nmrows = (int)mrows.size();
+    if (mrows.empty()) mrows.push_back(0);
+    CK(upload(&pr->d_mrows, mrows, s));
     CK(upload(&pr->d_MvC, mv, s));
   }
   CK(upload(&pr->d_col_map, pr->col_map, s));
@@ -366,7 +374,7 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
 
 void free_problem(Problem* pr) {
   auto F = [](void* p) { if (p) cudaFree(p); };
-  F(pr->d_indptr); F(pr->d_indices); F(pr->d_Mv); F(pr->d_Lv); F(pr->d_indptrM); F(pr->d_indicesM); F(pr->d_MvC); F(pr->d_col_map); F(pr->d_row_map);
+  F(pr->d_indptr); F(pr->d_indices); F(pr->d_Mv); F(pr->d_Lv); F(pr->d_indptrM); F(pr->d_indicesM); F(pr->d_mrows); F(pr->d_MvC); F(pr->d_col_map); F(pr->d_row_map);
   F(pr->d_var_rec); F(pr->d_var_ph); F(pr->d_eq_diff); F(pr->d_eq_ph); F(pr->d_bc_rows); F(pr->d_nl_eq);
   F(pr->d_row_f); F(pr->d_row_bc);
   F(pr->d_bc_values); F(pr->d_kx); F(pr->d_gvar); F(pr->d_gop); F(pr->d_tslot); F(pr->d_tfa); F(pr->d_tfb);
@@ -478,9 +486,11 @@ void set_mv_M(Problem* pr, SolveArgs& a) {
 }
 void set_ep_M(Problem* pr, SolveArgs& a) {
   a.ep_mv_vals = pr->d_MvC; a.ep_indptr = pr->d_indptrM; a.ep_indices = pr->d_indicesM; a.ep_nnz = (int)pr->nnzM;
+  a.ep_rows = pr->d_mrows; a.ep_nrows = pr->nmrows;
 }
 void set_ep_L(Problem* pr, SolveArgs& a) {
   a.ep_mv_vals = pr->d_Lv; a.ep_indptr = pr->d_indptr; a.ep_indices = pr->d_indices; a.ep_nnz = (int)pr->nnz;
+  a.ep_rows = nullptr; a.ep_nrows = 0;
 }
 
 sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
@@ -652,6 +662,7 @@ SolveArgs transposed_args(Problem* pr, sp_ctx* ctx) {
   a.n_nl = 0; a.nbc = 0; a.bc_coef = 0.0;
   a.xc32_out = nullptr;
   a.Lg = nullptr; a.Ug = nullptr; a.pg = nullptr; a.umask = nullptr;
+  a.ep_rows = nullptr; a.ep_nrows = 0;   // the transposed patterns carry no row list
   return a;
 }
 

@@ -544,7 +544,25 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   }
   if (a.ep_mv_vals) {
     const double* vals = a.ep_mv_vals + (size_t)p * a.ep_nnz;
-    for (int r = tid; work && r < n; r += nt) {
+    const bool listed = a.ep_rows != nullptr;
+    if (listed) {
+      // rows without entries first (zero, or B~/beta for L~X~ from the
+      // stage right-hand side), then the listed rows with every lane on a
+      // row that has entries; the barrier orders the two stores of a row
+      for (int r = tid; work && r < n; r += nt) {
+        double2 s = make_double2(0.0, 0.0);
+        if (mode == 2 && a.ep_from_b != 0.0) {
+          const double2 bb = a.bg[prow + r];
+          s.x = bb.x * a.ep_from_b;
+          s.y = bb.y * a.ep_from_b;
+        }
+        a.ep_mv_store[prow + r] = s;
+      }
+      __syncthreads();
+    }
+    const int nrows = listed ? a.ep_nrows : n;
+    for (int i = tid; work && i < nrows; i += nt) {
+      const int r = listed ? a.ep_rows[i] : i;
       double2 s = make_double2(0.0, 0.0);
       for (int e = a.ep_indptr[r]; e < a.ep_indptr[r + 1]; ++e) {
         const double m = vals[e];

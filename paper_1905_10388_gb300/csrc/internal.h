@@ -77,6 +77,7 @@ struct SolveArgs {
   const double* ep_mv_vals; double2* ep_mv_store;
   const double2* ep_mv_addvec;                 // epilogue matvec acts on (X~ + addvec) if set
   const int32_t* ep_indptr; const int32_t* ep_indices; int ep_nnz;    // pattern of ep_mv_vals
+  const int32_t* ep_rows; int ep_nrows;   // the pattern's non-empty rows (M~), or null: every row
   // tables (device)
   const int32_t* indptr; const int32_t* indices;
   const int32_t* row_map; const int32_t* col_map;
