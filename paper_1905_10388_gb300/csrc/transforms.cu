@@ -30,6 +30,13 @@
 
 namespace spectau {
 
+// floor(idx / n) for 0 <= idx < 2^20 from inv = 1/n in FP32: (idx + 1/2)/n
+// lies at least 1/(2n) from an integer, and the two FP32 roundings (of inv
+// and of the product, relative 2^-24 each) move it by under 2^-23 2^20/n =
+// 2^-3/n, so the truncation is exact (a run-time integer division would
+// cost a dozen instructions per element)
+__device__ __forceinline__ int div_idx(int idx, float inv) { return (int)(((float)idx + 0.5f) * inv); }
+
 constexpr int Z_THREADS = 256;
 constexpr int X_THREADS = 256;
 
@@ -40,6 +47,7 @@ constexpr int X_THREADS = 256;
 template <typename T, int TP>
 __device__ __forceinline__ void cheb_backward_body(const ZDesc& d, int bx, int f, unsigned char* smem_raw) {
   const int Nc = d.Nc, Ng = d.Ng, P = d.P;
+  const float invNg = 1.0f / (float)Ng, invNc = 1.0f / (float)Nc;
   C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* b1 = b0 + TP * Ng;
   C<T>* tws = b1 + TP * Ng;
@@ -65,7 +73,7 @@ __device__ __forceinline__ void cheb_backward_body(const ZDesc& d, int bx, int f
     return mk<T>(s * x.x, s * x.y);
   };
   for (int idx = threadIdx.x; idx < TP * Ng; idx += blockDim.x) {
-    const int c = idx / Ng, k = idx - c * Ng;
+    const int c = div_idx(idx, invNg), k = idx - c * Ng;
     const C<T> a = coef(c, k);
     const C<T> b = (k == 0) ? mk<T>(0, 0) : coef(c, Ng - k);
     // X_k - i X_{N-k}
@@ -90,6 +98,7 @@ __device__ __forceinline__ void cheb_backward_body(const ZDesc& d, int bx, int f
 template <typename T, int TP>
 __device__ __forceinline__ void cheb_forward_body(const ZDesc& d, int bx, int e, unsigned char* smem_raw) {
   const int Nc = d.Nc, Ng = d.Ng, P = d.P;
+  const float invNg = 1.0f / (float)Ng, invNc = 1.0f / (float)Nc;
   C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* b1 = b0 + TP * Ng;
   C<T>* tws = b1 + TP * Ng;
@@ -107,7 +116,7 @@ __device__ __forceinline__ void cheb_forward_body(const ZDesc& d, int bx, int e,
   C<T>* res = fft_batched<T>(b0, b1, Ng, d.radix3, tws, -1, TP);
   const T inv = (T)1 / (T)Ng;
   for (int idx = threadIdx.x; idx < TP * Nc; idx += blockDim.x) {
-    const int c = idx / Nc, k = idx - c * Nc;
+    const int c = div_idx(idx, invNc), k = idx - c * Nc;
     const int p = p0 + c;
     if (p >= P) continue;
     const C<T> Vk = res[c * Ng + k];
@@ -138,6 +147,7 @@ constexpr int X_PAIRS = 2;
 template <typename T>
 __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsigned char* smem_raw) {
   const int N = d.N, K = d.K, rows = d.rows, mode = d.mode, nf = d.nf, ne = d.ne;
+  const float invN = 1.0f / (float)N, invK = 1.0f / (float)K;
   const int nout = (mode & 2) ? ne : nf;
   const int nbi = (nf + 1) / 2, nbo = (nout + 1) / 2;
   const int nbmax = max(min(nbi, X_PAIRS), nbo);
@@ -155,7 +165,8 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
    for (int q0 = 0; q0 < nbi; q0 += X_PAIRS) {
     const int nb = min(X_PAIRS, nbi - q0);
     for (int idx = tid; idx < nb * N; idx += nt) {
-      const int q = q0 + idx / N, k = idx - (idx / N) * N;
+      const int qq = div_idx(idx, invN);
+      const int q = q0 + qq, k = idx - qq * N;
       const int fa = 2 * q, fb = 2 * q + 1;
       auto spec = [&](int f, int kk) -> C<T> {
         if (f >= nf) return mk<T>(0, 0);
@@ -183,7 +194,8 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
     __syncthreads();
     C<T>* res = fft_batched<T>(b0, b1, N, d.radix3, tws, +1, nb);
     for (int idx = tid; idx < nb * N; idx += nt) {
-      const int q = q0 + idx / N, i = idx - (idx / N) * N;
+      const int qq = div_idx(idx, invN);
+      const int q = q0 + qq, i = idx - qq * N;
       G[(size_t)(2 * q) * N + i] = res[idx].x;
       if (2 * q + 1 < nf) G[(size_t)(2 * q + 1) * N + i] = res[idx].y;
     }
@@ -227,7 +239,7 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
 
   if (mode & 4) {
     for (int idx = tid; idx < nbo * N; idx += nt) {
-      const int q = idx / N, i = idx - q * N;
+      const int q = div_idx(idx, invN), i = idx - q * N;
       const T a = OUT[(size_t)(2 * q) * N + i];
       const T b = (2 * q + 1 < nout) ? OUT[(size_t)(2 * q + 1) * N + i] : (T)0;
       b0[idx] = mk<T>(a, b);
@@ -235,7 +247,7 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
     __syncthreads();
     C<T>* res = fft_batched<T>(b0, b1, N, d.radix3, tws, -1, nbo);
     for (int idx = tid; idx < nbo * K; idx += nt) {
-      const int q = idx / K, k = idx - q * K;
+      const int q = div_idx(idx, invK), k = idx - q * K;
       // forward x: 1/N; transpose of backward x: (2 - delta_k0)
       const T s = (d.xscale & 2) ? ((k == 0) ? (T)0.5 : (T)1) : (T)1 / (T)(2 * N);
       const C<T> Z = res[(size_t)q * N + k];
@@ -265,6 +277,7 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
 template <typename T>
 __device__ __forceinline__ void fourier_rows_adjoint_body(const XDesc& d, int row, unsigned char* smem_raw) {
   const int N = d.N, K = d.K, rows = d.rows, nf = d.nf, ne = d.ne;
+  const float invN = 1.0f / (float)N;
   const int nbf = (nf + 1) / 2, nbe = (ne + 1) / 2;
   const int nbmax = max(nbf, nbe);
   C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
@@ -310,7 +323,7 @@ __device__ __forceinline__ void fourier_rows_adjoint_body(const XDesc& d, int ro
     __syncthreads();
     C<T>* res = fft_batched<T>(b0, b1, N, d.radix3, tws, +1, nb);
     for (int idx = tid; idx < nb * N; idx += nt) {
-      const int q = idx / N, i = idx - q * N;
+      const int q = div_idx(idx, invN), i = idx - q * N;
       dst[(size_t)(2 * q) * N + i] = res[idx].x;
       if (2 * q + 1 < nfields) dst[(size_t)(2 * q + 1) * N + i] = res[idx].y;
     }
