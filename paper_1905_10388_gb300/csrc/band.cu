@@ -325,6 +325,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   //      boundary values
   const size_t prow = (size_t)pp * n;
   const int Nz = a.Nz;
+  const float invNz = 1.0f / (float)Nz;
   // halves of the F~ coefficients for the T-to-U rows (exact scalings,
   // once per thread rather than once per row)
   double cH[3], cM[3];
@@ -370,7 +371,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   for (int r = n + tid; active && r < a.npad + 64; r += nt) sm.B[r] = make_double2(0.0, 0.0);
   __syncthreads();
   for (int idx = tid; active && idx < a.n_nl * Nz; idx += nt) {
-    const int sl = idx / Nz, m = idx - sl * Nz;
+    const int sl = div_idx(idx, invNz), m = idx - sl * Nz;
     const int e = a.nl_eq[sl];
     const int row = a.row_map[e * Nz + m];
     if (row < 0) continue;
@@ -530,7 +531,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   }
   if (a.xc_out) {
     for (int idx = tid; work && idx < a.S * Nz; idx += nt) {
-      const int v = idx / Nz, m = idx - v * Nz;
+      const int v = div_idx(idx, invNz), m = idx - v * Nz;
       double2 x = sm.B[a.col_map[idx]];
       if (a.var_recombine[v] && m + 2 < Nz) {
         const double2 x2 = sm.B[a.col_map[idx + 2]];

@@ -48,6 +48,13 @@ __device__ __forceinline__ double dneg(double x) {
 __device__ __forceinline__ bool dfinite(double x) {
   return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
+// floor(idx / n) for 0 <= idx < 2^20 from inv = 1/n in FP32: (idx + 1/2)/n
+// lies at least 1/(2n) from an integer, and the two FP32 roundings (of inv
+// and of the product, relative 2^-24 each) move it by under 2^-23 2^20/n =
+// 2^-3/n, so the truncation is exact (a run-time integer division would
+// cost a dozen instructions per element)
+__device__ __forceinline__ int div_idx(int idx, float inv) { return (int)(((float)idx + 0.5f) * inv); }
+
 // i^q * a for double2 without FP64 instructions
 __device__ __forceinline__ double2 cipow_d(double2 a, int q) {
   switch (q & 3) {

@@ -30,12 +30,6 @@
 
 namespace spectau {
 
-// floor(idx / n) for 0 <= idx < 2^20 from inv = 1/n in FP32: (idx + 1/2)/n
-// lies at least 1/(2n) from an integer, and the two FP32 roundings (of inv
-// and of the product, relative 2^-24 each) move it by under 2^-23 2^20/n =
-// 2^-3/n, so the truncation is exact (a run-time integer division would
-// cost a dozen instructions per element)
-__device__ __forceinline__ int div_idx(int idx, float inv) { return (int)(((float)idx + 0.5f) * inv); }
 
 constexpr int Z_THREADS = 256;
 constexpr int X_THREADS = 256;
