@@ -54,8 +54,8 @@ FP64_PEAK_TFLOPS = 1.25
 # k_pencil_solve launch of the 512x256 SBDF2 mixed-precision step, from one
 # ncu capture of `bench.py --steps 3 --warmup 3 --no-cpu-baseline`.  It is
 # reported only while the kernel's sources hash to the captured ones.
-SOLVE_TRAFFIC = {"workload": "rb2d_512x256_sbdf2", "precision": "mixed", "bytes": 180.793344e6,
-                 "sources_sha256": "f922839f2b894bdcc4456e75f6a0410f8c7cc03c084d6b583782815d9529630d"}
+SOLVE_TRAFFIC = {"workload": "rb2d_512x256_sbdf2", "precision": "mixed", "bytes": 180.167424e6,
+                 "sources_sha256": "6e1faf7afac97e168c6b898896ba0d11584f537a2c2b681e09e6b6babf466739"}
 SOLVE_SOURCES = ("paper_1905_10388_gb300/csrc/band.cu", "paper_1905_10388_gb300/csrc/internal.h",
                  "paper_1905_10388_gb300/csrc/common.cuh")
 
