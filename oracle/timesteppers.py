@@ -18,10 +18,18 @@ scheme of Ascher, Ruuth & Spiteri (1997), cited but not printed:
     H = [[0,0,0],[0,gamma,0],[0,1-gamma,gamma]]
     A = [[0,0,0],[gamma,0,0],[delta,1-delta,0]],  c = [0, gamma, 1]
 RK111 (first order, one stage): H = [[0,0],[0,1]], A = [[0,0],[1,0]].
+RK443 is the third-order, four-stage ARS(4,4,3) scheme of the same paper
+(the method of the paper's MHD and annulus examples), also not printed
+there: implicit diagonal 1/2 throughout, c = [0, 1/2, 2/3, 1/2, 1],
+    H rows 1-4: [0,1/2], [0,1/6,1/2], [0,-1/2,1/2,1/2], [0,3/2,-3/2,1/2,1/2]
+    A rows 1-4: [1/2], [11/18,1/18], [5/6,-5/6,1/2], [1/4,7/4,3/4,-7/4]
 
 Pins: ``tests/test_oracle_timesteppers.py`` (amplification factors of the
 linear test equation, exact decay of polynomial diffusion modes, second-order
-convergence, SBDF two-term recurrence).
+convergence, SBDF two-term recurrence; for RK443 the third-order conditions
+of both tableaux and of their coupling, third-order convergence of a
+diffusion mode and of a stiff-linear / quadratic-explicit scalar problem with
+a closed-form solution).
 
 A "system" provides: P (pencil count), matrices() -> [(M_p, L_p)],
 rhs_vectors(X) -> [F~_p], to_pencil(X, p), from_pencils(vectors).
@@ -44,6 +52,20 @@ RK111 = dict(
     H=np.array([[0, 0], [0, 1]], dtype=np.float64),
     A=np.array([[0, 0], [1, 0]], dtype=np.float64),
     c=np.array([0.0, 1.0]),
+)
+
+RK443 = dict(
+    H=np.array([[0, 0, 0, 0, 0],
+                [0, 1 / 2, 0, 0, 0],
+                [0, 1 / 6, 1 / 2, 0, 0],
+                [0, -1 / 2, 1 / 2, 1 / 2, 0],
+                [0, 3 / 2, -3 / 2, 1 / 2, 1 / 2]], dtype=np.float64),
+    A=np.array([[0, 0, 0, 0, 0],
+                [1 / 2, 0, 0, 0, 0],
+                [11 / 18, 1 / 18, 0, 0, 0],
+                [5 / 6, -5 / 6, 1 / 2, 0, 0],
+                [1 / 4, 7 / 4, 3 / 4, -7 / 4, 0]], dtype=np.float64),
+    c=np.array([0.0, 1 / 2, 2 / 3, 1 / 2, 1.0]),
 )
 
 DENSE_LIMIT = 1000

@@ -124,3 +124,79 @@ def test_neumann_diffusion_conserves_mean_even_N():
         X = st.step(X, 0.05)
     assert abs(integ @ X[0, 0] - m0) < 1e-14
     assert abs(m0 - 2.0) < 1e-11          # truncation of cos(pi z) at N = 16
+
+
+# ---------------------------------------------------------------------------
+# RK443 (ARS(4,4,3))
+
+
+def test_ars443_tableau_third_order_conditions():
+    """Third-order conditions of the implicit and explicit tableaux and of
+    their coupling (additive Runge-Kutta), with the weights the last rows
+    (X^{n+1} = X^s)."""
+    H, A, c = ts.RK443["H"], ts.RK443["A"], ts.RK443["c"]
+    assert np.allclose(H.sum(axis=1), c) and np.allclose(A.sum(axis=1), c)
+    assert np.all(np.triu(A) == 0) and np.all(np.triu(H, 1) == 0)
+    assert np.allclose(np.diag(H)[1:], 0.5)            # one factor for every stage
+    for b in (H[-1], A[-1]):
+        assert np.isclose(b.sum(), 1.0)
+        assert np.isclose(b @ c, 1 / 2)
+        assert np.isclose(b @ (c * c), 1 / 3)
+        assert np.isclose(b @ (A @ c), 1 / 6) and np.isclose(b @ (H @ c), 1 / 6)
+
+
+def test_rk443_dirichlet_mode_third_order():
+    N = 32
+    kx = 2 * np.pi * np.arange(3) / L_X
+    sysm = LinearPencilSystem(diffusion(N, "dirichlet"), kx)
+    lam = KAPPA * (kx[1] ** 2 + np.pi ** 2)
+    T = 1.0
+    errs = []
+    for nsteps in (5, 10, 20):
+        dt = T / nsteps
+        X = _mode_state(sysm, N, 1, lambda z: np.sin(np.pi * z), lambda z: np.pi * np.cos(np.pi * z))
+        a0 = X[0, 1].copy()
+        st = ts.RungeKuttaIMEX(sysm, ts.RK443)
+        for _ in range(nsteps):
+            X = st.step(X, dt)
+        errs.append(np.abs(X[0, 1] - a0 * np.exp(-lam * T)).max())
+    r = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all((r > 7.0) & (r < 9.0)), r
+
+
+class _Scalar:
+    """x' = -lam x - x^2 as a one-pencil system: M = 1, L = lam, F = -x^2."""
+
+    def __init__(self, lam):
+        import scipy.sparse as sps
+        self.P = 1
+        self._m = [(sps.csr_matrix(np.array([[1.0]])), sps.csr_matrix(np.array([[lam]])))]
+
+    def matrices(self):
+        return self._m
+
+    def rhs_vectors(self, X):
+        return [-X * X]
+
+    def to_pencil(self, X, p):
+        return X
+
+    def from_pencils(self, vecs):
+        return vecs[0]
+
+
+@pytest.mark.parametrize("name,order", [("RK222", 2), ("RK443", 3)])
+def test_imex_order_on_stiff_linear_quadratic_scalar(name, order):
+    """Both parts of the scheme at once: x(t) = lam x0 e^{-lam t} / (lam +
+    x0 (1 - e^{-lam t})) solves x' = -lam x - x^2."""
+    lam, x0, T = 2.0, 1.0, 1.0
+    exact = lam * x0 * np.exp(-lam * T) / (lam + x0 * (1 - np.exp(-lam * T)))
+    errs = []
+    for nsteps in (10, 20, 40):
+        st = ts.RungeKuttaIMEX(_Scalar(lam), getattr(ts, name))
+        X = np.array([x0])
+        for _ in range(nsteps):
+            X = st.step(X, T / nsteps)
+        errs.append(abs(X[0] - exact))
+    r = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(np.abs(np.log2(r) - order) < 0.3), r
