@@ -49,6 +49,9 @@ def measured_peaks():
 # sub-partitions x one 32-lane DFMA per 64 cycles x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 1.25
 
+# implicit stage solves per step of each scheme
+STAGES = {"RK222": 2, "RK443": 4, "RK111": 1, "SBDF1": 1, "SBDF2": 1}
+
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
 # k_pencil_solve launch of the 512x256 SBDF2 mixed-precision step, from one
@@ -187,7 +190,7 @@ def run_ours(args):
     s.set_initial_state(xi)
     s.step(args.warmup)
     s.sync()
-    stages = 2 if w.scheme == "RK222" else 1
+    stages = STAGES.get(w.scheme, 1)
     s.set_timing(args.steps * stages)
     stream = torch.cuda.current_stream(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -393,7 +396,7 @@ def oracle_rate(workload, steps_timed, warm):
     w = si.WORKLOADS[workload]
     sysr = orb.RB2D(w.n_x, w.n_z, w.Ra, w.Pr, w.L_x)
     X = sysr.initial_state(si.rb_noise(w.seed, w.n_z, w.n_x))
-    st = ots.RungeKuttaIMEX(sysr) if w.scheme == "RK222" else ots.SBDF(sysr, 2)
+    st = ots.RungeKuttaIMEX(sysr, getattr(ots, w.scheme)) if w.scheme.startswith("RK") else ots.SBDF(sysr, 2)
     for _ in range(warm):
         X = st.step(X, w.dt)
     t0 = time.perf_counter()
@@ -430,7 +433,7 @@ def oracle_rate_3d(workload, sample_pencils=16):
         lu.solve(b)
         t_solve += time.perf_counter() - t1
     t_solve /= sample_pencils
-    stages = 2 if w.scheme == "RK222" else 1
+    stages = STAGES.get(w.scheme, 1)
     step = stages * (t_rhs + sysr.P * t_solve)
     desc = (f"extrapolated: one full-size right-hand side ({t_rhs:.1f} s) and {sample_pencils} sampled pencil "
             f"solves ({t_solve * 1e3:.2f} ms each, stored SuperLU factors); step = {stages} x (RHS + "

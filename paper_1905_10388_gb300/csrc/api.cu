@@ -23,8 +23,8 @@ namespace {
 // implicit H and explicit A tableaux with an explicit first stage.
 struct Tableau {
   int s;
-  double H[4][4];
-  double A[4][4];
+  double H[5][5];
+  double A[5][5];
 };
 
 Tableau make_tableau(int scheme) {
@@ -38,6 +38,17 @@ Tableau make_tableau(int scheme) {
     t.A[1][0] = g;
     t.A[2][0] = d;
     t.A[2][1] = 1.0 - d;
+  } else if (scheme == SP_RK443) {
+    // ARS(4,4,3): implicit diagonal 1/2, c = (0, 1/2, 2/3, 1/2, 1)
+    t.s = 4;
+    t.H[1][1] = 0.5;
+    t.H[2][1] = 1.0 / 6.0; t.H[2][2] = 0.5;
+    t.H[3][1] = -0.5; t.H[3][2] = 0.5; t.H[3][3] = 0.5;
+    t.H[4][1] = 1.5; t.H[4][2] = -1.5; t.H[4][3] = 0.5; t.H[4][4] = 0.5;
+    t.A[1][0] = 0.5;
+    t.A[2][0] = 11.0 / 18.0; t.A[2][1] = 1.0 / 18.0;
+    t.A[3][0] = 5.0 / 6.0; t.A[3][1] = -5.0 / 6.0; t.A[3][2] = 0.5;
+    t.A[4][0] = 0.25; t.A[4][1] = 1.75; t.A[4][2] = 0.75; t.A[4][3] = -1.75;
   } else {  // RK111
     t.s = 1;
     t.H[1][1] = 1.0;
@@ -45,6 +56,8 @@ Tableau make_tableau(int scheme) {
   }
   return t;
 }
+
+bool is_rk(int scheme) { return scheme == SP_RK222 || scheme == SP_RK111 || scheme == SP_RK443; }
 
 bool is_smooth_length(int N) {  // 2^k or 3 * 2^k
   if (N <= 0) return false;
@@ -107,8 +120,8 @@ struct Problem {
   float* d_tcoef32 = nullptr;
   bool xc32_valid = false;
   double2* d_MX[2] = {nullptr, nullptr};
-  double2* d_LX[3] = {nullptr, nullptr, nullptr};
-  double2* d_Fc[3] = {nullptr, nullptr, nullptr};
+  double2* d_LX[4] = {nullptr, nullptr, nullptr, nullptr};   // L~X~^j, j = 1 .. s - 1
+  double2* d_Fc[4] = {nullptr, nullptr, nullptr, nullptr};   // F~ slots (RK: F^j, j < s)
   void* d_gz = nullptr;
   void* d_gy = nullptr;            // 3D: y-transformed fields [f][zg][yg][i_x]
   void* d_h = nullptr;
@@ -324,9 +337,11 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
   }
   CK(cudaMemsetAsync(pr->d_Xc, 0, nvec * sizeof(double2), s));
   for (auto& b : pr->d_MX) CK(dalloc(&b, nvec));
-  for (auto& b : pr->d_LX) CK(dalloc(&b, nvec));
+  // RK443 keeps three L~X~^j and four F~^j; the other schemes two and three
+  const int nlx = pr->scheme == SP_RK443 ? 4 : 3, nfc = pr->scheme == SP_RK443 ? 4 : 3;
+  for (int j = 0; j < nlx; ++j) CK(dalloc(&pr->d_LX[j], nvec));
   const int nl = std::max<int>(1, (int)pr->nl_eqs.size());
-  for (auto& b : pr->d_Fc) CK(dalloc(&b, (size_t)nl * pr->P * pr->Nz));
+  for (int j = 0; j < nfc; ++j) CK(dalloc(&pr->d_Fc[j], (size_t)nl * pr->P * pr->Nz));
   const size_t esz = pr->prec ? sizeof(float2) : sizeof(double2);
   const int nf = std::max<int>(1, (int)pr->gfields.size());
   const size_t rows = (size_t)pr->Ngz * pr->Ngy;   // x rows of the dealiased grid
@@ -535,7 +550,7 @@ struct StagePlan {
 // current state, without touching that state.  Valid when xt_valid.
 std::vector<StagePlan> plan_step(sp_ctx* ctx, Problem* pr, double dt) {
   std::vector<StagePlan> plan;
-  if (pr->scheme == SP_RK222 || pr->scheme == SP_RK111) {
+  if (is_rk(pr->scheme)) {
     const Tableau tb = make_tableau(pr->scheme);
     for (int i = 1; i <= tb.s; ++i) {
       SolveArgs a = base_args(pr, ctx, 0);
@@ -784,6 +799,7 @@ sp_status build_batch(sp_ctx* ctx, const std::vector<Problem*>& ps, const std::v
       xv.push_back(xdesc_rows(ps[q]));
       zfv.push_back(zdesc_forward(ps[q], plans[q][i].fc_out));
       av.push_back(plans[q][i].args);
+      fill_f_halves(av.back());
     }
     BatchStage st;
     CK(upload_vec(&st.d_zb, zbv));
@@ -858,7 +874,7 @@ sp_status sp_add_problem(sp_ctx* ctx, int ndim, const sp_basis* bases, int nvars
   if (bx.kind != SP_FOURIER || bz.kind != SP_CHEBYSHEV || (ndim == 3 && bases[1].kind != SP_FOURIER))
     return fail(ctx, SP_ERR_ARG, "bases must be Fourier axes followed by one Chebyshev axis (last)");
   if (nvars < 1 || nvars > 16) return fail(ctx, SP_ERR_ARG, "nvars must be in [1, 16]");
-  if (scheme < SP_RK222 || scheme > SP_RK111) return fail(ctx, SP_ERR_ARG, "unknown scheme %d", scheme);
+  if (scheme < SP_RK222 || scheme > SP_RK443) return fail(ctx, SP_ERR_ARG, "unknown scheme %d", scheme);
   if (precision != SP_PREC_FP64 && precision != SP_PREC_MIXED)
     return fail(ctx, SP_ERR_ARG, "unknown precision %d", precision);
   auto pr = std::make_unique<Problem>();
@@ -1055,9 +1071,9 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
   if (st != SP_OK) return st;
   double ab[2][2];
   int nf = 1;
-  if (pr->scheme == SP_RK222 || pr->scheme == SP_RK111) {
+  if (is_rk(pr->scheme)) {
     const Tableau tb = make_tableau(pr->scheme);
-    ab[0][0] = 1.0; ab[0][1] = dt * tb.H[1][1];
+    ab[0][0] = 1.0; ab[0][1] = dt * tb.H[1][1];   // every stage: H_ii = H_11
   } else if (pr->scheme == SP_SBDF1) {
     ab[0][0] = 1.0; ab[0][1] = dt;
   } else {

@@ -197,26 +197,25 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src) {
 // (1 + delta_m0)/2 F_m - F_{m+2}/2) and the phase i^-q of the equation's
 // real-ification.  One FMA per term and component: on GB300 every FP64
 // instruction holds the sub-partition's FP64 pipe for 64 cycles, so the
-// halves come from cH = c/2 and cM = -c/2 and the phase is applied to the
-// loaded values (a sign and swap, no arithmetic).
-__device__ __forceinline__ double2 add_f_row(const SolveArgs& a, int sl, int m, int p, const double* cH,
-                                             const double* cM, double2 acc) {
+// halves c/2 and -c/2 come precomputed with the arguments and the phase is
+// applied to the loaded values (a sign and swap, no arithmetic).
+__device__ __forceinline__ double2 add_f_row(const SolveArgs& a, int sl, int m, int p, double2 acc) {
   const int Nz = a.Nz;
   const int e = a.nl_eq[sl];
   const bool dif = a.eq_differential[e] != 0;
   const int ph = -a.eq_phase[e];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < SP_MAX_TERMS; ++k) {
     if (k >= a.nfc) break;
     const double2* F = a.fc[k] + ((size_t)sl * a.P + p) * Nz;
     const double2 v0 = cipow_d(F[m], ph);
-    const double c = (dif && m > 0) ? cH[k] : a.fc_coef[k];
+    const double c = (dif && m > 0) ? a.fc_half[k] : a.fc_coef[k];
     acc.x = fma(c, v0.x, acc.x);
     acc.y = fma(c, v0.y, acc.y);
     if (dif && m + 2 < Nz) {
       const double2 v2 = cipow_d(F[m + 2], ph);
-      acc.x = fma(cM[k], v2.x, acc.x);
-      acc.y = fma(cM[k], v2.y, acc.y);
+      acc.x = fma(a.fc_mhalf[k], v2.x, acc.x);
+      acc.y = fma(a.fc_mhalf[k], v2.y, acc.y);
     }
   }
   return acc;
@@ -326,14 +325,6 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   const size_t prow = (size_t)pp * n;
   const int Nz = a.Nz;
   const float invNz = 1.0f / (float)Nz;
-  // halves of the F~ coefficients for the T-to-U rows (exact scalings,
-  // once per thread rather than once per row)
-  double cH[3], cM[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    cH[k] = 0.5 * a.fc_coef[k];
-    cM[k] = -0.5 * a.fc_coef[k];
-  }
   if (mode == 2) {
     // epilogue only: X~ (already divided by U_jj) from the substitution kernel
     for (int r = tid; active && r < n; r += nt) sm.B[r] = a.xg[prow + r];
@@ -375,7 +366,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     const int e = a.nl_eq[sl];
     const int row = a.row_map[e * Nz + m];
     if (row < 0) continue;
-    sm.B[row] = add_f_row(a, sl, m, p, cH, cM, sm.B[row]);
+    sm.B[row] = add_f_row(a, sl, m, p, sm.B[row]);
   }
   for (int q = tid; active && q < a.nbc; q += nt) {
     const int row = a.bc_rows[q];
@@ -630,7 +621,9 @@ cudaError_t launch_pencil_solve_batched(cudaStream_t s, const SolveArgs* args, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a) {
+cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& args) {
+  SolveArgs a = args;
+  fill_f_halves(a);
   if (a.mode == 1 || a.mode == 2) {
     const size_t smem = solve_smem_bytes(a.npad, 0, 0);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;

@@ -61,16 +61,22 @@ cudaError_t launch_adj_tinvh(cudaStream_t s, int P, int Nz, int S, int n, const 
 cudaError_t launch_dz_adjoint(cudaStream_t s, int P, int Nz, double scale, const double2* dst_bar,
                               double2* src_bar);
 
+// Stored vectors and right-hand sides one stage combines: RK443's fourth
+// stage takes M~X~^0 and three L~X~^j, and four F~^j.
+constexpr int SP_MAX_TERMS = 4;
+
 // Arguments of the pencil right-hand-side assembly + solve + epilogue kernel.
 struct SolveArgs {
   int P, n, Nz, S, nbc, nnz;
   int kl, kuu, npad, lpad, upad;
   const double* Lf; const uint8_t* piv; const double* Uf; const double* rd;
   // prologue: B = sum_k vec_coef[k] vec[k] + mv_coef (Mat x) + sum_k fc_coef[k] P^L Fc_k + bc_coef g
-  int nvec; const double2* vec[3]; double vec_coef[3];
+  int nvec; const double2* vec[SP_MAX_TERMS]; double vec_coef[SP_MAX_TERMS];
   const double2* mv_x; const double* mv_vals; double mv_coef; double2* mv_store;
   const int32_t* mv_indptr; const int32_t* mv_indices; int mv_nnz;   // pattern of mv_vals
-  int nfc; const double2* fc[3]; double fc_coef[3];
+  int nfc; const double2* fc[SP_MAX_TERMS]; double fc_coef[SP_MAX_TERMS];
+  // fc_coef / 2 and -fc_coef / 2 for the T-to-U rows, filled by the launcher
+  double fc_half[SP_MAX_TERMS], fc_mhalf[SP_MAX_TERMS];
   double bc_coef;
   // epilogue
   double2* xt_out; double2* xc_out; float2* xc32_out;   // xc32_out: FP32 copy (mixed precision)
@@ -100,6 +106,14 @@ struct SolveArgs {
   // factor in the lane-interleaved layout (null: not available)
   const double* Lg; const double* Ug; const uint8_t* pg; const unsigned long long* umask; int cmax;
 };
+
+// fc_half / fc_mhalf from fc_coef (exact scalings), before a launch
+inline void fill_f_halves(SolveArgs& a) {
+  for (int k = 0; k < SP_MAX_TERMS; ++k) {
+    a.fc_half[k] = 0.5 * a.fc_coef[k];
+    a.fc_mhalf[k] = -0.5 * a.fc_coef[k];
+  }
+}
 
 // Transform arguments.
 struct GridField { int var; int op; };

@@ -54,6 +54,9 @@ WORKLOADS = {
                                          scheme="RK222", dt=5e-4, steps=200, n_y=256),
     "rb2d_256x128_rk222_adjoint": RBWorkload("rb2d_256x128_rk222_adjoint", 256, 128, 1e6,
                                              scheme="RK222", dt=1e-3, steps=500),
+    # the benchmarked 2D workload with the third-order four-stage RK443
+    "rb2d_512x256_rk443": RBWorkload("rb2d_512x256_rk443", 512, 256, 1e8, scheme="RK443",
+                                     dt=1e-4, steps=1000),
     # profiling slab of the 3D workload: the same 32768 pencils with 16
     # Chebyshev modes (about 2.5 GB on the device instead of about 25 GB)
     "rb3d_256x256x16_rk222": RBWorkload("rb3d_256x256x16_rk222", 256, 16, 1e7,

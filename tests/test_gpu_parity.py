@@ -43,8 +43,8 @@ def ctx():
 def _oracle_run(sysr, X, scheme, dt, nsteps):
     if scheme == "RK222":
         st = ots.RungeKuttaIMEX(sysr)
-    elif scheme == "RK111":
-        st = ots.RungeKuttaIMEX(sysr, ots.RK111)
+    elif scheme in ("RK111", "RK443"):
+        st = ots.RungeKuttaIMEX(sysr, getattr(ots, scheme))
     else:
         st = ots.SBDF(sysr, 2 if scheme == "SBDF2" else 1)
     for _ in range(nsteps):
@@ -151,7 +151,7 @@ def test_rb_64x32_rk222_100_steps(ctx, prec):
     _check(s.get_state(), ref, floor, TOL[prec])
 
 
-@pytest.mark.parametrize("scheme", ["SBDF2", "SBDF1", "RK111"])
+@pytest.mark.parametrize("scheme", ["SBDF2", "SBDF1", "RK111", "RK443"])
 def test_rb_small_other_schemes(ctx, scheme):
     Nx, Nz, Ra, dt = 32, 32, 1e5, 2e-3
     xi = si.rb_noise(9, Nz, Nx)
@@ -176,6 +176,22 @@ def test_rb_512x256_sbdf2_full_size(ctx, prec):
     s.step(nsteps)
     s.sync()
     ref, floor = _reference(w.n_x, w.n_z, w.Ra, xi, "SBDF2", w.dt, nsteps, w.Pr, w.L_x)
+    _check(s.get_state(), ref, floor, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_rb_512x256_rk443_full_size(ctx, prec):
+    """The benchmarked 2D size with the four-stage RK443: two steps (eight
+    stage solves with one factor, L~X~^j of three stages carried)."""
+    w = si.WORKLOADS["rb2d_512x256_rk443"]
+    nsteps = 2
+    xi = si.rb_noise(w.seed, w.n_z, w.n_x)
+    s = RBSolver(ctx, w.n_x, w.n_z, w.Ra, w.Pr, w.L_x, scheme="RK443", precision=prec)
+    s.factor(w.dt)
+    s.set_initial_state(xi)
+    s.step(nsteps)
+    s.sync()
+    ref, floor = _reference(w.n_x, w.n_z, w.Ra, xi, "RK443", w.dt, nsteps, w.Pr, w.L_x)
     _check(s.get_state(), ref, floor, TOL[prec])
 
 
