@@ -176,10 +176,14 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     from paper_1905_10388_gb300 import build as _b  # noqa: F401
-    from paper_1905_10388_gb300.solver import Context, RB3DSolver, RBSolver
+    from paper_1905_10388_gb300.solver import Context, FisherKPPSolver, RB3DSolver, RBSolver
     w = si.WORKLOADS[args.workload]
     ctx = Context(local, torch.cuda.current_stream(local).cuda_stream)
-    if w.n_y > 1:
+    fisher = isinstance(w, si.FisherWorkload)
+    if fisher:
+        s = FisherKPPSolver(ctx, w.n_x, w.n_z, w.D, w.R, w.L_x, scheme=w.scheme, precision=args.precision)
+        xi = si.fisher_noise(w.seed + rank, w.n_z, w.n_x)
+    elif w.n_y > 1:
         s = RB3DSolver(ctx, w.n_x, w.n_y, w.n_z, w.Ra, w.Pr, w.L_x, w.L_y, scheme=w.scheme,
                        precision=args.precision)
         xi = si.rb_noise3(w.seed + rank, w.n_z, w.n_y, w.n_x)
@@ -214,15 +218,16 @@ def run_ours(args):
     ms = secs * 1e3
 
     # end to end through the public API with host buffers: upload the state,
-    # K steps each followed by a device-to-host read of the buoyancy field
+    # K steps each followed by a device-to-host read of the first field (b or u)
     X0 = s.get_state()
     host_state = [np.ascontiguousarray(X0[i]) for i in range(s.S)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s.set_state(host_state)
+    probe = "u" if fisher else "b"              # the step's result read back every step
     for _ in range(args.steps):
         s.step(1)
-        _ = s.get_field("b")
+        _ = s.get_field(probe)
     torch.cuda.synchronize()
     e2e_rate, _ = job_rate(w.dof * args.steps, time.perf_counter() - t0, world, device="cuda")
     state_bytes = s.S * s.P * s.Nz * 16
@@ -252,11 +257,14 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-            "data": "synthetic (seeded Rayleigh-Benard initial state)",
-            "config": {"workload": args.workload, "n_x": w.n_x, "n_y": w.n_y, "n_z": w.n_z, "Ra": w.Ra,
-                       "Pr": w.Pr, "scheme": w.scheme, "dt": w.dt, "dof": w.dof, "precision": args.precision,
-                       "parallelism": f"replicas{world}",
-                       "l2": f"working set > L2 (factor {factor_mb:.0f} MB read every solve)"},
+            "data": "synthetic (seeded %s initial state)" % ("Fisher-KPP" if fisher else "Rayleigh-Benard"),
+            "config": dict({"workload": args.workload, "n_x": w.n_x, "n_y": w.n_y, "n_z": w.n_z},
+                           **({"D": w.D, "R": w.R} if fisher else {"Ra": w.Ra, "Pr": w.Pr}),
+                           **{"scheme": w.scheme, "dt": w.dt, "dof": w.dof, "precision": args.precision,
+                              "parallelism": f"replicas{world}",
+                              "l2": (f"working set > L2 (factor {factor_mb:.0f} MB read every solve)"
+                                     if factor_mb > 129 else
+                                     f"L2-resident (factor {factor_mb:.0f} MB < 129 MB L2; no flush)")}),
             "roofline": roof, "e2e": e2e,
             "gpu_launches": stages * ((5 if w.n_y > 1 else 3) + (3 if lanes else 1)) * args.steps,
             "clocks": clk,
@@ -394,8 +402,13 @@ def oracle_rate(workload, steps_timed, warm):
     from oracle import rb as orb
     from oracle import timesteppers as ots
     w = si.WORKLOADS[workload]
-    sysr = orb.RB2D(w.n_x, w.n_z, w.Ra, w.Pr, w.L_x)
-    X = sysr.initial_state(si.rb_noise(w.seed, w.n_z, w.n_x))
+    if isinstance(w, si.FisherWorkload):
+        from oracle import fisher as ofk
+        sysr = ofk.FisherKPP(w.n_x, w.n_z, w.D, w.R, w.L_x)
+        X = sysr.initial_state(si.fisher_noise(w.seed, w.n_z, w.n_x))
+    else:
+        sysr = orb.RB2D(w.n_x, w.n_z, w.Ra, w.Pr, w.L_x)
+        X = sysr.initial_state(si.rb_noise(w.seed, w.n_z, w.n_x))
     st = ots.RungeKuttaIMEX(sysr, getattr(ots, w.scheme)) if w.scheme.startswith("RK") else ots.SBDF(sysr, 2)
     for _ in range(warm):
         X = st.step(X, w.dt)

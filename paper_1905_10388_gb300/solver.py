@@ -11,6 +11,7 @@ import ctypes
 import numpy as np
 
 from . import _lib as L
+from . import fisher as fkmod
 from . import rb as rbmod
 
 
@@ -251,6 +252,25 @@ class RBSolver(TauSolver):
             self.set_field(v, zero)
         self.set_field("b", b_grid, layout="g")
         self.dz("b", "bz")
+
+
+class FisherKPPSolver(TauSolver):
+    """The Fisher-KPP example (u, uz) in the library: Fourier x on [0, L_x),
+    Chebyshev z on [0, 1], Neumann walls."""
+
+    def __init__(self, ctx, n_x, n_z, D=0.1, R=1.0, L_x=2 * np.pi, scheme="RK222", precision="fp64",
+                 dealias=(3, 2)):
+        problem = fkmod.fisher_pencil_problem(D, R)
+        super().__init__(ctx, problem, n_x, n_z, L_x, scheme=scheme, precision=precision,
+                         dealias=dealias, bilinear=fkmod.bilinear_terms(R))
+        self.state_order = fkmod.VARIABLES
+        self.D, self.R = D, R
+
+    def set_initial_state(self, u_grid):
+        """u from its values on the scale-1 grid [z, x] (transformed on the
+        device), uz = dz u (device recurrence)."""
+        self.set_field("u", np.asarray(u_grid, np.float64), layout="g")
+        self.dz("u", "uz")
 
 
 class RB3DSolver(TauSolver):
