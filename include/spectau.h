@@ -261,6 +261,27 @@ sp_status sp_eval_rhs(sp_ctx* ctx, int problem, void* out_host, int* n_eq);
  * superdiagonals after pivoting). */
 sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku);
 
+/* CFL frequency of the current state (Sec. "Timestep determination"): the
+ * largest over the points of the dealiased grid of
+ *     sum_v |v(x)| / dx_{axes[v]}(x),   v = vars[0 .. nvel),
+ * the velocity fields vars (state indices) along axes (0: x, 1: y on 3D
+ * problems, 2: z), 1 <= nvel <= 3.  Grid spacings: L_x / N_gx, L_y / N_gy,
+ * and on z the centred difference of the dealiased Chebyshev nodes
+ * (one-sided at the two end nodes).  The velocities are transformed in the
+ * problem's precision (FP32 in mixed precision), the sum taken in FP64.
+ * Synchronizes the context's stream; *freq_out is host memory.  Scratch
+ * for three fields is allocated on the first call and kept. */
+sp_status sp_cfl_frequency(sp_ctx* ctx, int problem, int nvel, const int* vars, const int* axes, double* freq_out);
+
+/* CFL timestep from a frequency (Sec. "Timestep determination"), plain
+ * host arithmetic: dt = safety / freq (max_dt when freq = 0), bounded to
+ * [min_dt, max_dt], then, when dt_prev > 0, to [min_change, max_change] x
+ * dt_prev, and kept at dt_prev when |dt - dt_prev| < threshold x dt_prev.
+ * A kept step reuses the stored factorization (sp_factor with a new dt is
+ * the caller's choice).  SP_ERR_ARG for inconsistent bounds. */
+sp_status sp_cfl_dt(double freq, double dt_prev, double safety, double min_dt, double max_dt, double min_change,
+                    double max_change, double threshold, double* dt_out);
+
 /* Work of one pencil substitution as the problem's solve kernel performs it
  * (Sec. "Matrix solvers": forward substitution with L, back substitution
  * with U), for the factor that the steady steps use (the last one of

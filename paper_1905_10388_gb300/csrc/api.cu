@@ -119,6 +119,13 @@ struct Problem {
   float* d_kx32 = nullptr;
   float* d_tcoef32 = nullptr;
   bool xc32_valid = false;
+  // CFL frequency scratch (sp_cfl_frequency), allocated on first use
+  double* d_cfl_grid = nullptr;
+  void *d_cfl_mid1 = nullptr, *d_cfl_mid2 = nullptr;
+  double* d_inv_dz = nullptr;
+  int32_t* d_cfl_args = nullptr;             // vars[3], axes[3]
+  unsigned long long* d_cfl_out = nullptr;
+  int cfl_cap = 0;                           // fields the scratch holds
   double2* d_MX[2] = {nullptr, nullptr};
   double2* d_LX[4] = {nullptr, nullptr, nullptr, nullptr};   // L~X~^j, j = 1 .. s - 1
   double2* d_Fc[4] = {nullptr, nullptr, nullptr, nullptr};   // F~ slots (RK: F^j, j < s)
@@ -392,6 +399,7 @@ void free_problem(Problem* pr) {
   F(pr->d_indptr); F(pr->d_indices); F(pr->d_Mv); F(pr->d_Lv); F(pr->d_indptrM); F(pr->d_indicesM); F(pr->d_mrows); F(pr->d_MvC); F(pr->d_col_map); F(pr->d_row_map);
   F(pr->d_var_rec); F(pr->d_var_ph); F(pr->d_eq_diff); F(pr->d_eq_ph); F(pr->d_bc_rows); F(pr->d_nl_eq);
   F(pr->d_row_f); F(pr->d_row_bc);
+  F(pr->d_cfl_grid); F(pr->d_cfl_mid1); F(pr->d_cfl_mid2); F(pr->d_inv_dz); F(pr->d_cfl_args); F(pr->d_cfl_out);
   F(pr->d_bc_values); F(pr->d_kx); F(pr->d_gvar); F(pr->d_gop); F(pr->d_tslot); F(pr->d_tfa); F(pr->d_tfb);
   F(pr->d_tcoef); F(pr->d_ident); F(pr->d_zero); F(pr->d_Xt); F(pr->d_Xc); F(pr->d_Xc32); F(pr->d_kx32);
   F(pr->d_tcoef32);
@@ -1778,6 +1786,87 @@ sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku) {
   if (n) *n = pr->n;
   if (kl) *kl = pr->kl;
   if (ku) *ku = pr->ku;
+  return SP_OK;
+}
+
+sp_status sp_cfl_frequency(sp_ctx* ctx, int problem, int nvel, const int* vars, const int* axes, double* freq_out) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (nvel < 1 || nvel > 3 || !vars || !axes || !freq_out) return fail(ctx, SP_ERR_ARG, "bad arguments");
+  for (int v = 0; v < nvel; ++v) {
+    if (vars[v] < 0 || vars[v] >= pr->S) return fail(ctx, SP_ERR_ARG, "variable %d out of range", vars[v]);
+    if (axes[v] != 0 && axes[v] != 2 && !(axes[v] == 1 && pr->ndim == 3))
+      return fail(ctx, SP_ERR_ARG, "axis %d is not an axis of the problem", axes[v]);
+  }
+  CK(cudaSetDevice(ctx->device));
+  sp_status st = upload_problem(ctx, pr);
+  if (st != SP_OK) return st;
+  TransformPlan *px, *pz, *py = nullptr;
+  if ((st = make_plan(ctx, pr, pr->Nx, pr->Ngx, &px)) != SP_OK) return st;
+  if ((st = make_plan(ctx, pr, pr->Nz, pr->Ngz, &pz)) != SP_OK) return st;
+  if (pr->ndim == 3 && (st = make_plan(ctx, pr, pr->Ny, pr->Ngy, &py)) != SP_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const int Ngy = pr->ndim == 3 ? pr->Ngy : 1;
+  if (pr->cfl_cap < nvel) {
+    // scratch for three fields, the inverse node spacings, the arguments
+    cudaFree(pr->d_cfl_grid); cudaFree(pr->d_cfl_mid1); cudaFree(pr->d_cfl_mid2);
+    pr->d_cfl_grid = nullptr; pr->d_cfl_mid1 = pr->d_cfl_mid2 = nullptr;
+    const size_t nm = grid_scratch_elems(pr, 3, Ngy, pr->Ngz), esz = pr->prec ? 8 : 16;
+    CK(dalloc(&pr->d_cfl_grid, (size_t)3 * pr->Ngz * Ngy * pr->Ngx));
+    CK(cudaMalloc(&pr->d_cfl_mid1, nm * esz));
+    CK(cudaMalloc(&pr->d_cfl_mid2, nm * esz));
+    if (!pr->d_cfl_args) {
+      CK(cudaMalloc((void**)&pr->d_cfl_args, 6 * sizeof(int32_t)));
+      CK(cudaMalloc((void**)&pr->d_cfl_out, sizeof(unsigned long long)));
+      // node spacing of the dealiased Chebyshev grid: centred differences,
+      // one-sided at the two end nodes
+      const int N = pr->Ngz;
+      std::vector<double> z(N), inv(N);
+      for (int i = 0; i < N; ++i)
+        z[i] = pr->za + (pr->zb - pr->za) * 0.5 * (1.0 - std::cos(M_PI * (i + 0.5) / N));
+      for (int i = 0; i < N; ++i) {
+        const double d = (i == 0) ? z[1] - z[0] : (i == N - 1) ? z[N - 1] - z[N - 2] : 0.5 * (z[i + 1] - z[i - 1]);
+        inv[i] = 1.0 / d;
+      }
+      CK(upload(&pr->d_inv_dz, inv, s));
+    }
+    pr->cfl_cap = 3;
+  }
+  int32_t args[6] = {0, 0, 0, 0, 0, 0};
+  for (int v = 0; v < nvel; ++v) { args[v] = vars[v]; args[3 + v] = axes[v]; }
+  CK(cudaMemcpyAsync(pr->d_cfl_args, args, sizeof(args), cudaMemcpyHostToDevice, s));
+  if (pr->prec && !pr->xc32_valid) {
+    CK(launch_to_f32(s, pr->d_Xc, pr->d_Xc32, (size_t)pr->S * pr->P * pr->Nz));
+    pr->xc32_valid = true;
+  }
+  CK(coef_to_grid(pr, s, pr->prec, nvel, *px, py, *pz, Ngy, pr->Ngz, pr->d_cfl_args, pr->d_Xc,
+                  pr->P * pr->Nz, pr->d_Xc32, pr->d_cfl_grid, pr->d_cfl_mid1, pr->d_cfl_mid2));
+  CK(cudaMemsetAsync(pr->d_cfl_out, 0, sizeof(unsigned long long), s));
+  const double inv_dx = pr->Ngx / pr->Lx, inv_dy = pr->ndim == 3 ? Ngy / pr->Ly : 0.0;
+  CK(launch_cfl_max(s, pr->d_cfl_grid, nvel, pr->d_cfl_args + 3, pr->Ngx, Ngy, pr->Ngz, inv_dx, inv_dy,
+                    pr->d_inv_dz, pr->d_cfl_out));
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, pr->d_cfl_out, sizeof(bits), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double f;
+  std::memcpy(&f, &bits, sizeof f);
+  *freq_out = f;
+  return SP_OK;
+}
+
+sp_status sp_cfl_dt(double freq, double dt_prev, double safety, double min_dt, double max_dt, double min_change,
+                    double max_change, double threshold, double* dt_out) {
+  if (!dt_out || !(safety > 0.0) || !(freq >= 0.0) || !(min_dt >= 0.0) || !(max_dt >= min_dt) ||
+      !(min_change > 0.0) || !(max_change >= min_change) || !(threshold >= 0.0))
+    return SP_ERR_ARG;
+  double dt = freq > 0.0 ? safety / freq : max_dt;
+  dt = std::min(std::max(dt, min_dt), max_dt);
+  if (dt_prev > 0.0) {
+    dt = std::min(std::max(dt, min_change * dt_prev), max_change * dt_prev);
+    if (std::fabs(dt - dt_prev) < threshold * dt_prev) dt = dt_prev;
+  }
+  *dt_out = dt;
   return SP_OK;
 }
 

@@ -209,6 +209,8 @@ cudaError_t launch_fourier_rows_adjoint(cudaStream_t s, int prec, const Transfor
                                         const int32_t* t_fa, const int32_t* t_fb, void* gzadj);
 // dir < 0: slots -> grid, dir > 0: grid -> slots (1/N_gy, Nyquist slot zero);
 // py = plan (N_y, N_gy); buffers [f][zg][slot or yg][K] in the precision.
+cudaError_t launch_cfl_max(cudaStream_t s, const double* grid, int nvel, const int* axes, int Ngx, int Ngy, int Ngz,
+                           double inv_dx, double inv_dy, const double* inv_dz, unsigned long long* out);
 cudaError_t launch_fourier_y(cudaStream_t s, int prec, const TransformPlan& py, int dir, int nf, int nz, int K,
                              const void* src, void* dst);
 size_t z_smem_bytes(int prec, int Ng, int tile);

@@ -699,4 +699,48 @@ cudaError_t launch_fourier_y(cudaStream_t s, int prec, const TransformPlan& py, 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// CFL frequency (Sec. "Timestep determination"): the largest over the grid
+// points of sum_v |g_v| * inv_d(axis_v, point).  grid [v][iz][iy][ix] FP64;
+// inv_dz[iz] the inverse spacing of the Chebyshev nodes; the maximum is
+// accumulated into *out as the bit pattern of a non-negative double (whose
+// integer order is its numeric order).
+// ---------------------------------------------------------------------------
+__global__ void k_cfl_max(const double* __restrict__ grid, int nvel, const int* __restrict__ axes, int Ngx, int Ngy,
+                          int Ngz, double inv_dx, double inv_dy, const double* __restrict__ inv_dz,
+                          unsigned long long* __restrict__ out) {
+  const size_t npts = (size_t)Ngx * Ngy * Ngz;
+  double m = 0.0;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < npts; q += (size_t)gridDim.x * blockDim.x) {
+    const int iz = (int)(q / ((size_t)Ngx * Ngy));
+    double f = 0.0;
+    for (int v = 0; v < nvel; ++v) {
+      const int ax = axes[v];
+      const double inv = ax == 0 ? inv_dx : (ax == 1 ? inv_dy : inv_dz[iz]);
+      f += fabs(grid[(size_t)v * npts + q]) * inv;
+    }
+    m = fmax(m, f);
+  }
+  // warp, then block maximum, one atomic per block
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double wm[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) wm[w] = m;
+  __syncthreads();
+  if (w == 0) {
+    m = l < (int)(blockDim.x >> 5) ? wm[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (l == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+cudaError_t launch_cfl_max(cudaStream_t s, const double* grid, int nvel, const int* axes, int Ngx, int Ngy, int Ngz,
+                           double inv_dx, double inv_dy, const double* inv_dz, unsigned long long* out) {
+  const size_t npts = (size_t)Ngx * Ngy * Ngz;
+  const int threads = 256;
+  const int blocks = (int)std::min<size_t>((npts + threads - 1) / threads, (size_t)152 * 8);
+  k_cfl_max<<<blocks, threads, 0, s>>>(grid, nvel, axes, Ngx, Ngy, Ngz, inv_dx, inv_dy, inv_dz, out);
+  return cudaGetLastError();
+}
+
 }  // namespace spectau

@@ -150,6 +150,18 @@ class TauSolver:
         L.check(h, L.lib().sp_get_band(h, self.pid, ctypes.byref(n), ctypes.byref(kl), ctypes.byref(ku)))
         return n.value, kl.value, ku.value
 
+    def cfl_frequency(self, velocities):
+        """Largest sum_v |v| / dx_axis over the dealiased grid of the current
+        state; velocities = ((variable, axis), ...), axis in 'x', 'y', 'z'."""
+        axis = {"x": 0, "y": 1, "z": 2}
+        n = len(velocities)
+        vs = (ctypes.c_int * n)(*[self.var[v] for v, _ in velocities])
+        ax = (ctypes.c_int * n)(*[axis[a] for _, a in velocities])
+        f = ctypes.c_double()
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_cfl_frequency(h, self.pid, n, vs, ax, ctypes.byref(f)))
+        return f.value
+
     def solve_work(self):
         """(multiply-adds per row and real right-hand side, factor bytes per
         pencil) of the substitution as the solve kernel performs it."""
@@ -229,6 +241,42 @@ class TauSolver:
         h = self.ctx.handle
         L.check(h, L.lib().sp_last_solve_time(h, self.pid, ctypes.byref(ms), ctypes.byref(cnt)))
         return ms.value, cnt.value
+
+
+class CFL:
+    """CFL timestep control (Sec. "Timestep determination") around a solver:
+    the frequency of the current state from the library (sp_cfl_frequency),
+    the step from the library's bounded, thresholded rule (sp_cfl_dt).
+    ``step(n)`` advances n steps, choosing dt before each and factoring only
+    when dt changes (the stored factorization is reused otherwise)."""
+
+    def __init__(self, solver, velocities, initial_dt, safety=0.5, min_dt=0.0, max_dt=np.inf,
+                 min_change=0.5, max_change=2.0, threshold=0.0):
+        if not solver.scheme.startswith("RK"):
+            raise ValueError("a changing step needs a Runge-Kutta scheme (SBDF here is constant-step)")
+        self.solver, self.velocities = solver, tuple(velocities)
+        self.dt = float(initial_dt)
+        self.params = (float(safety), float(min_dt), float(max_dt), float(min_change), float(max_change),
+                       float(threshold))
+        self.history, self.factorizations = [], 0
+
+    def compute_dt(self):
+        freq = self.solver.cfl_frequency(self.velocities)
+        out = ctypes.c_double()
+        st = L.lib().sp_cfl_dt(freq, self.dt, *self.params, ctypes.byref(out))
+        if st != 0:
+            raise ValueError("inconsistent CFL bounds")
+        self.dt = out.value
+        return self.dt
+
+    def step(self, nsteps=1):
+        for _ in range(nsteps):
+            dt = self.compute_dt()
+            if self.solver.dt != dt:
+                self.solver.factor(dt)
+                self.factorizations += 1
+            self.solver.step(1)
+            self.history.append(dt)
 
 
 class RBSolver(TauSolver):
