@@ -320,6 +320,66 @@ def run_batch(args):
     return res
 
 
+def run_cfl(args):
+    """The 512x256 RK222 step under CFL control (Sec. "Timestep
+    determination"): before every step the frequency of the state on the
+    dealiased grid (sp_cfl_frequency, read back to the host), the bounded and
+    thresholded step (sp_cfl_dt), and a factorization only when the step
+    changes.  The timed region holds all of it."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1905_10388_gb300.solver import CFL, Context, RBSolver
+    w = si.WORKLOADS["rb2d_512x256_sbdf2"]
+    ctx = Context(0, torch.cuda.current_stream(0).cuda_stream)
+    s = RBSolver(ctx, w.n_x, w.n_z, w.Ra, w.Pr, w.L_x, scheme="RK222", precision=args.precision)
+    dt0 = 1e-4
+    s.factor(dt0)
+    s.set_initial_state(si.rb_noise(w.seed, w.n_z, w.n_x))
+    s.step(args.warmup)
+    s.sync()
+    prm = dict(safety=0.5, min_dt=1e-6, max_dt=1e-3, min_change=0.5, max_change=1.5, threshold=0.1)
+    ctl = CFL(s, (("u", "x"), ("w", "z")), initial_dt=dt0, **prm)
+    t_cfl = []
+    for _ in range(3):                        # warm the frequency path (scratch, plans)
+        t0 = time.perf_counter()
+        s.cfl_frequency(ctl.velocities)
+        t_cfl.append(time.perf_counter() - t0)
+    stream = torch.cuda.current_stream(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctl.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    st, pen = ctx.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} at pencil {pen}")
+    ms = e0.elapsed_time(e1)
+    t0 = time.perf_counter()
+    for _ in range(10):
+        s.cfl_frequency(ctl.velocities)
+    freq_ms = (time.perf_counter() - t0) / 10 * 1e3
+    res = {"metric": METRIC, "value": w.dof * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "data": "synthetic (seeded Rayleigh-Benard initial state)",
+           "config": {"workload": "rb2d_512x256_rk222_cfl", "n_x": w.n_x, "n_z": w.n_z, "Ra": w.Ra,
+                      "scheme": "RK222", "precision": args.precision, "cfl": prm, "initial_dt": dt0,
+                      "l2": "working set > L2 (factor read every solve)"},
+           "cfl": {"factorizations": ctl.factorizations, "dt_first": ctl.history[0], "dt_last": ctl.history[-1],
+                   "distinct_dt": len(set(ctl.history)), "frequency_ms": freq_ms},
+           "roofline": None,
+           # per step: frequency (z backward, x rows, maximum) + two RK222 stages
+           # of four launches; one k_band_factor per change of step
+           "gpu_launches": args.steps * (3 + 2 * 4) + ctl.factorizations, "clocks": clk}
+    ctx.close()
+    return res
+
+
 def run_adjoint(args):
     """Gradient of the final-buoyancy misfit through K RK222 steps (discrete
     adjoint with checkpoints every 50 steps): forward sweep, adjoint sweep,
@@ -510,6 +570,8 @@ def main():
         res = run_batch(args)
     elif args.workload.endswith("_adjoint"):
         res = run_adjoint(args)
+    elif args.workload == "rb2d_512x256_rk222_cfl":
+        res = run_cfl(args)
     else:
         res = run_ours(args)
         if res is not None and not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:
