@@ -588,6 +588,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS, 2) k_pencil_solve(SolveArgs a) 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   pencil_solve_body<RU, PPC, -1, SOLVE_THREADS>(a, blockIdx.x, smem_raw);
 }
+// 128 threads, three CTAs per SM: for more pencils than two CTAs per SM
+// hold, more concurrent chains outweigh the narrower assembly and epilogue
+template <int RU>
+__global__ void __launch_bounds__(128, 3) k_pencil_solve_narrow(SolveArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  pencil_solve_body<RU, 1, -1, 128>(a, blockIdx.x, smem_raw);
+}
 
 // right-hand-side assembly only (MODE 1) or epilogue only (MODE 2), around
 // k_pencil_lanes: shared memory for B~ alone, several CTAs per SM
@@ -640,6 +647,24 @@ cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& args) {
   const size_t smem = PPC * solve_smem_bytes(a.npad, a.lpad, a.upad);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   const int grid = (a.P + PPC - 1) / PPC;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  }
+  // three CTAs of 128 threads per SM (228 KB of shared memory, 1 KB of it
+  // reserved per CTA) when the pencils fill more than one wave of two
+  if (a.P > 2 * sms && 3 * (smem + 1024) <= 228 * 1024) {
+    if (a.kuu <= 31) {
+      cudaFuncSetAttribute(k_pencil_solve_narrow<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_pencil_solve_narrow<1><<<grid, 128, smem, s>>>(a);
+    } else {
+      cudaFuncSetAttribute(k_pencil_solve_narrow<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_pencil_solve_narrow<2><<<grid, 128, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
   if (a.kuu <= 31) {
     cudaFuncSetAttribute(k_pencil_solve<1, PPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_pencil_solve<1, PPC><<<grid, SOLVE_THREADS, smem, s>>>(a);
