@@ -7,8 +7,12 @@ Multistep IMEX (Sec. "Multistep IMEX integrators"):
 with the first iterations taken at lower order.  The coefficients are the
 semi-implicit BDF schemes of Wang & Ruuth (2008), cited by the paper but not
 printed there; for a constant step:
-    SBDF1: a = (1, -1)/dt,           b = (1, 0),     c = (-, 1)
-    SBDF2: a = (3/2, -2, 1/2)/dt,    b = (1, 0, 0),  c = (-, 2, -1)
+    SBDF1: a = (1, -1)/dt,                   b = (1, 0, ...),  c = (-, 1)
+    SBDF2: a = (3/2, -2, 1/2)/dt,            c = (-, 2, -1)
+    SBDF3: a = (11/6, -3, 3/2, -1/3)/dt,     c = (-, 3, -3, 1)
+    SBDF4: a = (25/12, -4, 3, -4/3, 1/4)/dt, c = (-, 4, -6, 4, -1)
+(the backward-difference weights of the implicit part and the polynomial
+extrapolation weights of the explicit part).
 
 Runge-Kutta IMEX (Sec. "Runge-Kutta IMEX integrators"):
     (M + dt H_ii L) X^i = M X^0 + dt sum_{j<i} A_ij F^j - dt sum_{j<i} H_ij L X^j
@@ -147,7 +151,8 @@ class RungeKuttaIMEX:
 
 
 class SBDF:
-    """SBDF1 / SBDF2 multistep IMEX with the paper's general coefficient form."""
+    """SBDF1 .. SBDF4 multistep IMEX with the paper's general coefficient form;
+    the first steps at the orders the history allows."""
 
     def __init__(self, system, order=2):
         self.sys = system
@@ -163,6 +168,12 @@ class SBDF:
         if order == 2:
             return (np.array([1.5, -2.0, 0.5]) / dt, np.array([1.0, 0.0, 0.0]),
                     np.array([0.0, 2.0, -1.0]))
+        if order == 3:
+            return (np.array([11 / 6, -3.0, 3 / 2, -1 / 3]) / dt, np.array([1.0, 0.0, 0.0, 0.0]),
+                    np.array([0.0, 3.0, -3.0, 1.0]))
+        if order == 4:
+            return (np.array([25 / 12, -4.0, 3.0, -4 / 3, 1 / 4]) / dt, np.array([1.0, 0.0, 0.0, 0.0, 0.0]),
+                    np.array([0.0, 4.0, -6.0, 4.0, -1.0]))
         raise ValueError("order")
 
     def step(self, X, dt):

@@ -200,3 +200,47 @@ def test_imex_order_on_stiff_linear_quadratic_scalar(name, order):
         errs.append(abs(X[0] - exact))
     r = np.array(errs[:-1]) / np.array(errs[1:])
     assert np.all(np.abs(np.log2(r) - order) < 0.3), r
+
+
+# ---------------------------------------------------------------------------
+# SBDF3 / SBDF4
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
+def test_sbdf_coefficients_are_consistent(order):
+    """sum a_j = 0 and sum_j j a_j = -1 (exact for constants and lines,
+    with a in units of 1/dt), sum c_j = 1 (extrapolation of constants)."""
+    a, b, c = ts.SBDF.coefficients(order, 1.0)
+    j = np.arange(order + 1)
+    assert abs(a.sum()) < 1e-14 and abs((j * a).sum() + 1.0) < 1e-14
+    assert abs(c.sum() - 1.0) < 1e-14 and b[0] == 1.0 and np.all(b[1:] == 0)
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_sbdf_order_from_exact_history(order):
+    """x' = -lam x - x^2 with the exact solution as the start-up history:
+    the global error falls at the scheme's order (a lower-order start would
+    mask it)."""
+    lam, x0, T = 2.0, 1.0, 1.0
+
+    def exact(t):
+        return lam * x0 * np.exp(-lam * t) / (lam + x0 * (1 - np.exp(-lam * t)))
+
+    errs = []
+    for nsteps in (80, 160, 320):
+        dt = T / nsteps
+        sysm = _Scalar(lam)
+        st = ts.SBDF(sysm, order)
+        M, L = sysm.matrices()[0]
+        for k in range(order - 1, 0, -1):          # oldest first: the list is newest-first
+            xk = np.array([exact(-k * dt)])
+            st.hist_MX.insert(0, [M @ xk])
+            st.hist_LX.insert(0, [L @ xk])
+            st.hist_F.insert(0, sysm.rhs_vectors(xk))
+        st.iteration = order - 1
+        X = np.array([x0])
+        for _ in range(nsteps):
+            X = st.step(X, dt)
+        errs.append(abs(X[0] - exact(T)))
+    r = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(np.abs(np.log2(r) - order) < 0.35), r
