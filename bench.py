@@ -50,7 +50,7 @@ def measured_peaks():
 FP64_PEAK_TFLOPS = 1.25
 
 # implicit stage solves per step of each scheme
-STAGES = {"RK222": 2, "RK443": 4, "RK111": 1, "SBDF1": 1, "SBDF2": 1}
+STAGES = {"RK222": 2, "RK443": 4, "RK111": 1, "SBDF1": 1, "SBDF2": 1, "SBDF3": 1, "SBDF4": 1}
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one

@@ -70,9 +70,13 @@ typedef struct {
 /* IMEX schemes (Sec. "Timesteppers"): RK222 = ARS(2,2,2), RK111 and
  * RK443 = ARS(4,4,3) (third order, four stages, implicit diagonal 1/2: one
  * factorization serves every stage) of Ascher, Ruuth & Spiteri (1997);
- * SBDF1/SBDF2 of Wang & Ruuth (2008).  SBDF2 takes its first step as SBDF1
- * (lower-order start).  The adjoint entry points support RK222 and RK111. */
-typedef enum { SP_RK222 = 0, SP_SBDF1 = 1, SP_SBDF2 = 2, SP_RK111 = 3, SP_RK443 = 4 } sp_scheme;
+ * SBDF1 .. SBDF4 of Wang & Ruuth (2008), constant step.  SBDFq takes its
+ * first q - 1 steps at the orders the history allows (SBDF1, SBDF2, ...)
+ * and keeps one factorization per order.  The adjoint entry points support
+ * RK222 and RK111; batched stepping all but SBDF3 and SBDF4. */
+typedef enum {
+  SP_RK222 = 0, SP_SBDF1 = 1, SP_SBDF2 = 2, SP_RK111 = 3, SP_RK443 = 4, SP_SBDF3 = 5, SP_SBDF4 = 6
+} sp_scheme;
 
 /* FP64: every stage in FP64.  MIXED: transforms and grid products in FP32,
  * pencil factorization, right-hand-side assembly and solves in FP64. */

@@ -17,10 +17,11 @@ STATUS_NAMES = {0: "SP_OK", -1: "SP_ERR_ARG", -2: "SP_ERR_CUDA", -3: "SP_ERR_OOM
                 -4: "SP_ERR_SINGULAR", -5: "SP_ERR_NOT_FACTORED", -6: "SP_ERR_NONFINITE",
                 -7: "SP_ERR_TIMEOUT", -8: "SP_ERR_STATE"}
 SP_FOURIER, SP_CHEBYSHEV = 0, 1
-SP_RK222, SP_SBDF1, SP_SBDF2, SP_RK111, SP_RK443 = 0, 1, 2, 3, 4
-SCHEMES = {"RK222": SP_RK222, "SBDF1": SP_SBDF1, "SBDF2": SP_SBDF2, "RK111": SP_RK111, "RK443": SP_RK443}
+SP_RK222, SP_SBDF1, SP_SBDF2, SP_RK111, SP_RK443, SP_SBDF3, SP_SBDF4 = 0, 1, 2, 3, 4, 5, 6
+SCHEMES = {"RK222": SP_RK222, "SBDF1": SP_SBDF1, "SBDF2": SP_SBDF2, "RK111": SP_RK111, "RK443": SP_RK443,
+           "SBDF3": SP_SBDF3, "SBDF4": SP_SBDF4}
 # implicit solves per step
-STAGES = {"RK222": 2, "SBDF1": 1, "SBDF2": 1, "RK111": 1, "RK443": 4}
+STAGES = {"RK222": 2, "SBDF1": 1, "SBDF2": 1, "RK111": 1, "RK443": 4, "SBDF3": 1, "SBDF4": 1}
 SP_PREC_FP64, SP_PREC_MIXED = 0, 1
 SP_OP_ID, SP_OP_DX, SP_OP_DY = 0, 1, 2
 SP_SOLVE_AUTO, SP_SOLVE_WINDOW, SP_SOLVE_LANES = 0, 1, 2

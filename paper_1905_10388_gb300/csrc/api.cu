@@ -59,6 +59,33 @@ Tableau make_tableau(int scheme) {
 
 bool is_rk(int scheme) { return scheme == SP_RK222 || scheme == SP_RK111 || scheme == SP_RK443; }
 
+// SBDF order of a multistep scheme (0 for the Runge-Kutta schemes)
+int sbdf_order(int scheme) {
+  switch (scheme) {
+    case SP_SBDF1: return 1;
+    case SP_SBDF2: return 2;
+    case SP_SBDF3: return 3;
+    case SP_SBDF4: return 4;
+    default: return 0;
+  }
+}
+// history slots of a multistep scheme (two at least: SBDF1 alternates too)
+int sbdf_depth(int scheme) { return std::max(2, sbdf_order(scheme)); }
+
+// Constant-step SBDF of order q (Wang & Ruuth 2008) multiplied through by dt:
+//   (a_0 M + dt L) X^{n+1} = - sum_{j=1..q} a_j M X^{n+1-j} + dt sum_{j=1..q} c_j F^{n+1-j}
+// (BDF weights a, extrapolation weights c; both rows of c sum to one).
+const double SBDF_A[5][5] = {{0, 0, 0, 0, 0},
+                             {1.0, -1.0, 0, 0, 0},
+                             {1.5, -2.0, 0.5, 0, 0},
+                             {11.0 / 6.0, -3.0, 1.5, -1.0 / 3.0, 0},
+                             {25.0 / 12.0, -4.0, 3.0, -4.0 / 3.0, 0.25}};
+const double SBDF_C[5][5] = {{0, 0, 0, 0, 0},
+                             {0, 1.0, 0, 0, 0},
+                             {0, 2.0, -1.0, 0, 0},
+                             {0, 3.0, -3.0, 1.0, 0},
+                             {0, 4.0, -6.0, 4.0, -1.0}};
+
 bool is_smooth_length(int N) {  // 2^k or 3 * 2^k
   if (N <= 0) return false;
   if (N % 3 == 0) N /= 3;
@@ -126,13 +153,13 @@ struct Problem {
   int32_t* d_cfl_args = nullptr;             // vars[3], axes[3]
   unsigned long long* d_cfl_out = nullptr;
   int cfl_cap = 0;                           // fields the scratch holds
-  double2* d_MX[2] = {nullptr, nullptr};
+  double2* d_MX[4] = {nullptr, nullptr, nullptr, nullptr};   // M~X~ history (multistep: a ring)
   double2* d_LX[4] = {nullptr, nullptr, nullptr, nullptr};   // L~X~^j, j = 1 .. s - 1
   double2* d_Fc[4] = {nullptr, nullptr, nullptr, nullptr};   // F~ slots (RK: F^j, j < s)
   void* d_gz = nullptr;
   void* d_gy = nullptr;            // 3D: y-transformed fields [f][zg][yg][i_x]
   void* d_h = nullptr;
-  BandFactor fac[2];
+  BandFactor fac[4];                       // SBDFq: one per start-up order 1 .. q
   int nfac = 0;
   double fac_dt = 0;
   bool factored = false;
@@ -343,9 +370,10 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
     CK(upload(&pr->d_tcoef32, tc32, s));
   }
   CK(cudaMemsetAsync(pr->d_Xc, 0, nvec * sizeof(double2), s));
-  for (auto& b : pr->d_MX) CK(dalloc(&b, nvec));
+  for (int j = 0; j < sbdf_depth(pr->scheme); ++j) CK(dalloc(&pr->d_MX[j], nvec));
   // RK443 keeps three L~X~^j and four F~^j; the other schemes two and three
-  const int nlx = pr->scheme == SP_RK443 ? 4 : 3, nfc = pr->scheme == SP_RK443 ? 4 : 3;
+  const int nlx = pr->scheme == SP_RK443 ? 4 : 3;
+  const int nfc = (pr->scheme == SP_RK443 || pr->scheme == SP_SBDF4) ? 4 : 3;
   for (int j = 0; j < nlx; ++j) CK(dalloc(&pr->d_LX[j], nvec));
   const int nl = std::max<int>(1, (int)pr->nl_eqs.size());
   for (int j = 0; j < nfc; ++j) CK(dalloc(&pr->d_Fc[j], (size_t)nl * pr->P * pr->Nz));
@@ -365,9 +393,8 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
   pr->npad = (pr->n + SOLVE_CHUNK - 1) / SOLVE_CHUNK * SOLVE_CHUNK;
   pr->lpad = std::max(2, (pr->kl + 1) / 2 * 2);
   pr->upad = kuu <= 31 ? 32 : 64;
-  // SBDF2 keeps two factors (its SBDF1 start and the SBDF2 matrix); the
-  // other schemes one
-  const int nfactors = pr->scheme == SP_SBDF2 ? 2 : 1;
+  // SBDFq keeps q factors (its start-up orders); the Runge-Kutta schemes one
+  const int nfactors = std::max(1, sbdf_order(pr->scheme));
   // thousands of pencils fill the GPU with one lane per right-hand side
   pr->lanes = pr->solve_kind == SP_SOLVE_LANES ||
               (pr->solve_kind == SP_SOLVE_AUTO && pr->P >= LANE_MIN_PENCILS && lanes_supported(pr->kl, kuu));
@@ -587,31 +614,28 @@ std::vector<StagePlan> plan_step(sp_ctx* ctx, Problem* pr, double dt) {
       plan.push_back(StagePlan{pr->d_Fc[i - 1], a});               // F(X^{i-1}) before stage i
     }
   } else {
-    // SBDF1 / SBDF2 (Wang & Ruuth 2008), constant step, multiplied through by dt:
-    //   SBDF1: (M + dt L) X^n = M X^{n-1} + dt F^{n-1}
-    //   SBDF2: (3/2 M + dt L) X^n = 2 M X^{n-1} - 1/2 M X^{n-2} + dt (2 F^{n-1} - F^{n-2})
-    const int it = pr->iteration;
-    const int cur = it & 1, prv = cur ^ 1;
-    const bool first = (pr->scheme == SP_SBDF1) || it == 0;
-    SolveArgs a = base_args(pr, ctx, first ? 0 : 1);
-    if (!pr->mx_valid) {
-      a.mv_x = pr->d_Xt; a.mv_store = pr->d_MX[cur];
-      set_mv_M(pr, a);
-      a.mv_coef = first ? 1.0 : 2.0;
-    } else {
-      a.vec[a.nvec] = pr->d_MX[cur]; a.vec_coef[a.nvec++] = first ? 1.0 : 2.0;
-    }
-    if (first) {
-      a.fc[a.nfc] = pr->d_Fc[cur]; a.fc_coef[a.nfc++] = dt;
-    } else {
-      a.vec[a.nvec] = pr->d_MX[prv]; a.vec_coef[a.nvec++] = -0.5;
-      a.fc[a.nfc] = pr->d_Fc[cur]; a.fc_coef[a.nfc++] = 2.0 * dt;
-      a.fc[a.nfc] = pr->d_Fc[prv]; a.fc_coef[a.nfc++] = -dt;
+    // SBDF1 .. SBDF4 (Wang & Ruuth 2008), constant step, the first steps at
+    // the orders the history allows (SBDF1, SBDF2, ...), with SBDF_A / SBDF_C.
+    // Slot (it mod D) of the M~X~ and F~ rings holds step it's values.
+    const int it = pr->iteration, D = sbdf_depth(pr->scheme);
+    const int o = std::min(sbdf_order(pr->scheme), it + 1);
+    const int cur = it % D;
+    SolveArgs a = base_args(pr, ctx, o - 1);
+    for (int j = 1; j <= o; ++j) {
+      const int slot = ((it + 1 - j) % D + D) % D;
+      const double cm = -SBDF_A[o][j];
+      if (j == 1 && !pr->mx_valid) {
+        a.mv_x = pr->d_Xt; a.mv_store = pr->d_MX[cur]; a.mv_coef = cm;
+        set_mv_M(pr, a);
+      } else {
+        a.vec[a.nvec] = pr->d_MX[slot]; a.vec_coef[a.nvec++] = cm;
+      }
+      a.fc[a.nfc] = pr->d_Fc[slot]; a.fc_coef[a.nfc++] = dt * SBDF_C[o][j];
     }
     a.bc_coef = dt;
     a.xt_out = pr->d_Xt;
     a.xc_out = pr->d_Xc;
-    set_ep_M(pr, a); a.ep_mv_store = pr->d_MX[prv];               // M~ X~^n for the next step
+    set_ep_M(pr, a); a.ep_mv_store = pr->d_MX[(it + 1) % D];     // M~ X~^{n+1} for the next step
     plan.push_back(StagePlan{pr->d_Fc[cur], a});
   }
   return plan;
@@ -620,7 +644,7 @@ std::vector<StagePlan> plan_step(sp_ctx* ctx, Problem* pr, double dt) {
 // state after a planned step has been queued
 void commit_step(Problem* pr) {
   pr->mx_valid = true;
-  if (pr->scheme == SP_SBDF1 || pr->scheme == SP_SBDF2) pr->iteration += 1;
+  if (sbdf_order(pr->scheme) > 0) pr->iteration += 1;
 }
 
 sp_status ensure_solve_vars(sp_ctx* ctx, Problem* pr, cudaStream_t s) {
@@ -882,7 +906,7 @@ sp_status sp_add_problem(sp_ctx* ctx, int ndim, const sp_basis* bases, int nvars
   if (bx.kind != SP_FOURIER || bz.kind != SP_CHEBYSHEV || (ndim == 3 && bases[1].kind != SP_FOURIER))
     return fail(ctx, SP_ERR_ARG, "bases must be Fourier axes followed by one Chebyshev axis (last)");
   if (nvars < 1 || nvars > 16) return fail(ctx, SP_ERR_ARG, "nvars must be in [1, 16]");
-  if (scheme < SP_RK222 || scheme > SP_RK443) return fail(ctx, SP_ERR_ARG, "unknown scheme %d", scheme);
+  if (scheme < SP_RK222 || scheme > SP_SBDF4) return fail(ctx, SP_ERR_ARG, "unknown scheme %d", scheme);
   if (precision != SP_PREC_FP64 && precision != SP_PREC_MIXED)
     return fail(ctx, SP_ERR_ARG, "unknown precision %d", precision);
   auto pr = std::make_unique<Problem>();
@@ -1077,17 +1101,15 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
   CK(cudaSetDevice(ctx->device));
   sp_status st = upload_problem(ctx, pr);
   if (st != SP_OK) return st;
-  double ab[2][2];
+  double ab[4][2];
   int nf = 1;
   if (is_rk(pr->scheme)) {
     const Tableau tb = make_tableau(pr->scheme);
     ab[0][0] = 1.0; ab[0][1] = dt * tb.H[1][1];   // every stage: H_ii = H_11
-  } else if (pr->scheme == SP_SBDF1) {
-    ab[0][0] = 1.0; ab[0][1] = dt;
   } else {
-    ab[0][0] = 1.0; ab[0][1] = dt;
-    ab[1][0] = 1.5; ab[1][1] = dt;
-    nf = 2;
+    // SBDFq: the matrices a_0 M + dt L of the start-up orders 1 .. q
+    nf = sbdf_order(pr->scheme);
+    for (int f = 0; f < nf; ++f) { ab[f][0] = SBDF_A[f + 1][0]; ab[f][1] = dt; }
   }
   const int ldab = 2 * pr->kl + pr->ku + 1;
   double* work = nullptr;
@@ -1270,7 +1292,7 @@ sp_status sp_step_graph(sp_ctx* ctx, int problem, double dt, int nsteps) {
   int left = nsteps;
   // warm-up steps that change the buffer schedule run eagerly
   while (left > 0 && (!pr->xt_valid || !pr->mx_valid ||
-                      (pr->scheme == SP_SBDF2 && pr->iteration == 0))) {
+                      (sbdf_order(pr->scheme) > 1 && pr->iteration < sbdf_order(pr->scheme) - 1))) {
     sp_status st = one_step(ctx, pr, ctx->stream, dt);
     if (st != SP_OK) return st;
     --left;
@@ -1279,7 +1301,7 @@ sp_status sp_step_graph(sp_ctx* ctx, int problem, double dt, int nsteps) {
   pr->timing = false;  // event nodes are not recorded inside graphs
   while (left > 0) {
     const int block = std::min(left, 16);
-    const int parity = (pr->scheme == SP_SBDF2 || pr->scheme == SP_SBDF1) ? (pr->iteration & 1) : 0;
+    const int parity = sbdf_order(pr->scheme) > 0 ? pr->iteration % sbdf_depth(pr->scheme) : 0;
     auto key = std::make_tuple(block, parity, pr->scheme, dt);
     cudaGraphExec_t exec = nullptr;
     auto it = pr->graphs.find(key);
@@ -1327,6 +1349,8 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
   for (Problem* pr : ps)
     if (pr->scheme != ps[0]->scheme || pr->prec != ps[0]->prec)
       return fail(ctx, SP_ERR_ARG, "all problems of a batch need the same scheme and precision");
+  if (sbdf_order(ps[0]->scheme) > 2)
+    return fail(ctx, SP_ERR_ARG, "batched stepping supports SBDF1/SBDF2 and the Runge-Kutta schemes");
   CK(cudaSetDevice(ctx->device));
   sp_status st;
   // eager steps until every problem is in its steady schedule

@@ -46,7 +46,7 @@ def _oracle_run(sysr, X, scheme, dt, nsteps):
     elif scheme in ("RK111", "RK443"):
         st = ots.RungeKuttaIMEX(sysr, getattr(ots, scheme))
     else:
-        st = ots.SBDF(sysr, 2 if scheme == "SBDF2" else 1)
+        st = ots.SBDF(sysr, int(scheme[-1]))
     for _ in range(nsteps):
         X = st.step(X, dt)
     return X
@@ -151,7 +151,7 @@ def test_rb_64x32_rk222_100_steps(ctx, prec):
     _check(s.get_state(), ref, floor, TOL[prec])
 
 
-@pytest.mark.parametrize("scheme", ["SBDF2", "SBDF1", "RK111", "RK443"])
+@pytest.mark.parametrize("scheme", ["SBDF2", "SBDF1", "RK111", "RK443", "SBDF3", "SBDF4"])
 def test_rb_small_other_schemes(ctx, scheme):
     Nx, Nz, Ra, dt = 32, 32, 1e5, 2e-3
     xi = si.rb_noise(9, Nz, Nx)
@@ -216,12 +216,15 @@ def test_ragged_pencil_tiles(ctx):
     _check(s.get_state(), ref, floor, 1e-12)
 
 
-def test_graph_replay_matches_eager(ctx):
+@pytest.mark.parametrize("scheme", ["SBDF2", "SBDF4"])
+def test_graph_replay_matches_eager(ctx, scheme):
+    """Graph replay (blocks of up to 16 steps, keyed by the step's slot in
+    the multistep history ring) gives the eager steps bit for bit."""
     w = si.WORKLOADS["rb2d_64x32_rk222"]
     xi = si.rb_noise(1, w.n_z, w.n_x)
     outs = []
     for graph in (False, True):
-        s = RBSolver(ctx, w.n_x, w.n_z, w.Ra, scheme="SBDF2")
+        s = RBSolver(ctx, w.n_x, w.n_z, w.Ra, scheme=scheme)
         s.factor(w.dt)
         s.set_initial_state(xi)
         s.step(21, graph=graph)
