@@ -265,6 +265,21 @@ sp_status sp_eval_rhs(sp_ctx* ctx, int problem, void* out_host, int* n_eq);
  * superdiagonals after pivoting). */
 sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku);
 
+/* Eigenmode nearest a target in every pencil at once (Sec. "Eigenvalue
+ * solver", sparse solver): for sigma M~ X~ + L~ X~ = 0, the shift-and-invert
+ * operator A~ = (L~ + sigma_t M~)^{-1} M~ (its eigenvalue mu belongs to
+ * sigma = sigma_t - 1/mu) is applied by the banded pencil solve and iterated
+ * `iters` times from x0 -- a power iteration on A~, one mode per pencil
+ * (the paper hands A~ to an Arnoldi method for several modes).  mu is the
+ * Rayleigh quotient x^H A~ x / x^H x of the last normalized iterate.
+ * sigma_t is real (the factorization is real).  The factorization of
+ * L~ + sigma_t M~ replaces the step's: call sp_factor before stepping again.
+ * x0: host [P][n] complex FP64 start vectors in solve-variable order (NULL:
+ * all ones); sigma_re, sigma_im: host [P].  Device errors (a singular
+ * shifted pencil) are latched in the status word (sp_sync_status). */
+sp_status sp_eig_target(sp_ctx* ctx, int problem, double sigma_t, int iters, const void* x0_host, double* sigma_re,
+                        double* sigma_im);
+
 /* CFL frequency of the current state (Sec. "Timestep determination"): the
  * largest over the points of the dealiased grid of
  *     sum_v |v(x)| / dx_{axes[v]}(x),   v = vars[0 .. nvel),

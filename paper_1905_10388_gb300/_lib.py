@@ -34,7 +34,7 @@ EXPORTS = (
     "sp_get_band", "sp_set_timing", "sp_last_solve_time", "sp_transform_backward_static",
     "sp_step_batched", "sp_batch_tile", "sp_adjoint_init", "sp_step_adjoint", "sp_transform_adjoint",
     "sp_dz_adjoint", "sp_step_record", "sp_set_solve_kernel", "sp_get_solve_work",
-    "sp_cfl_frequency", "sp_cfl_dt",
+    "sp_cfl_frequency", "sp_cfl_dt", "sp_eig_target",
 )
 
 
@@ -79,6 +79,7 @@ _SIGS = {
     "sp_get_solve_work": [P, I, ctypes.POINTER(D), ctypes.POINTER(D)],
     "sp_cfl_frequency": [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)],
     "sp_cfl_dt": [D, D, D, D, D, D, D, D, ctypes.POINTER(D)],
+    "sp_eig_target": [P, I, D, I, P, P, P],
     "sp_set_timing": [P, I, I],
     "sp_last_solve_time": [P, I, ctypes.POINTER(D), ctypes.POINTER(I)],
     "sp_transform_backward_static": [P, P, I, I, I, I, I, P, ctypes.c_char_p, I],

@@ -1813,6 +1813,70 @@ sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku) {
   return SP_OK;
 }
 
+sp_status sp_eig_target(sp_ctx* ctx, int problem, double sigma_t, int iters, const void* x0_host, double* sigma_re,
+                        double* sigma_im) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (iters < 1 || !sigma_re || !sigma_im || !std::isfinite(sigma_t)) return fail(ctx, SP_ERR_ARG, "bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  sp_status st = upload_problem(ctx, pr);
+  if (st != SP_OK) return st;
+  cudaStream_t s = ctx->stream;
+  // L~ + sigma_T M~ into the first factor slot: the step's factorization is gone
+  pr->factored = false;
+  for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
+  pr->graphs.clear();
+  const int ldab = 2 * pr->kl + pr->ku + 1;
+  double* work = nullptr;
+  CK(dalloc(&work, (size_t)pr->P * pr->n * ldab));
+  cudaError_t e = launch_band_factor(s, pr->P, pr->n, (int)pr->nnz, pr->kl, pr->ku, pr->d_indptr, pr->d_indices,
+                                     pr->d_Mv, pr->d_Lv, sigma_t, 1.0, work, pr->fac[0], pr->npad, pr->lpad,
+                                     pr->upad, ctx->d_status);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(work);
+  CK(e);
+  const size_t nv = (size_t)pr->P * pr->n;
+  double2 *x = nullptr, *y = nullptr, *mu = nullptr;
+  auto release = [&]() { cudaFree(x); cudaFree(y); cudaFree(mu); };
+  if ((e = cudaMalloc(&x, nv * sizeof(double2))) == cudaSuccess && (e = cudaMalloc(&y, nv * sizeof(double2))) ==
+      cudaSuccess)
+    e = cudaMalloc(&mu, (size_t)pr->P * sizeof(double2));
+  if (e != cudaSuccess) { release(); CK(e); }
+  if (x0_host) {
+    e = cudaMemcpyAsync(x, x0_host, nv * sizeof(double2), cudaMemcpyHostToDevice, s);
+  } else {
+    std::vector<double2> ones(nv, make_double2(1.0, 0.0));
+    e = cudaMemcpyAsync(x, ones.data(), nv * sizeof(double2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  // y = (L~ + sigma_T M~)^{-1} M~ x: the solve kernel with the M~ matvec as
+  // its whole right-hand side (no stored vectors, F~ or boundary values)
+  SolveArgs a = base_args(pr, ctx, 0);
+  a.mode = 0;
+  a.nvec = 0; a.nfc = 0; a.n_nl = 0; a.nbc = 0; a.bc_coef = 0.0;
+  a.mv_x = x; a.mv_coef = 1.0; a.mv_store = nullptr;
+  set_mv_M(pr, a);
+  a.xt_out = y; a.xc_out = nullptr; a.xc32_out = nullptr; a.ep_mv_vals = nullptr;
+  a.Lg = nullptr; a.Ug = nullptr; a.pg = nullptr; a.umask = nullptr;
+  for (int k = 0; e == cudaSuccess && k < iters; ++k) {
+    e = launch_pencil_solve(s, a);
+    if (e == cudaSuccess) e = launch_eig_update(s, pr->P, pr->n, x, y, mu);
+  }
+  std::vector<double2> hm(pr->P);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), mu, hm.size() * sizeof(double2), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  CK(e);
+  for (int p = 0; p < pr->P; ++p) {
+    // sigma = sigma_T - 1 / mu
+    const double m2 = hm[p].x * hm[p].x + hm[p].y * hm[p].y;
+    sigma_re[p] = m2 > 0 ? sigma_t - hm[p].x / m2 : NAN;
+    sigma_im[p] = m2 > 0 ? hm[p].y / m2 : NAN;
+  }
+  return SP_OK;
+}
+
 sp_status sp_cfl_frequency(sp_ctx* ctx, int problem, int nvel, const int* vars, const int* axes, double* freq_out) {
   Problem* pr = get(ctx, problem);
   if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");

@@ -1186,4 +1186,55 @@ cudaError_t launch_dz_adjoint(cudaStream_t s, int P, int Nz, double scale, const
   k_dz_adjoint<<<(P + 127) / 128, 128, 0, s>>>(P, Nz, scale, dst_bar, src_bar);
   return cudaGetLastError();
 }
+// ---------------------------------------------------------------------------
+// Inverse iteration for the pencil eigenproblem (L~ + lambda M~) x = 0 with
+// shift sigma (Sec. "Eigenvalue solver"): after y = (L~ + sigma M~)^{-1} M~ x
+// (the solve kernel), per pencil mu = x^H y / x^H x, and x <- y / |y|;
+// lambda = sigma - 1 / mu is the eigenvalue nearest sigma.  One CTA per pencil.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_eig_update(int P, int n, double2* __restrict__ x,
+                                                    const double2* __restrict__ y, double2* __restrict__ mu) {
+  const int p = blockIdx.x;
+  if (p >= P) return;
+  double2* xp = x + (size_t)p * n;
+  const double2* yp = y + (size_t)p * n;
+  double xr = 0, xi = 0, xx = 0, yy = 0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const double2 a = xp[r], b = yp[r];
+    xr += a.x * b.x + a.y * b.y;            // conj(a) b
+    xi += a.x * b.y - a.y * b.x;
+    xx += a.x * a.x + a.y * a.y;
+    yy += b.x * b.x + b.y * b.y;
+  }
+  __shared__ double red[4][8];
+  for (int o = 16; o > 0; o >>= 1) {
+    xr += __shfl_xor_sync(0xffffffffu, xr, o);
+    xi += __shfl_xor_sync(0xffffffffu, xi, o);
+    xx += __shfl_xor_sync(0xffffffffu, xx, o);
+    yy += __shfl_xor_sync(0xffffffffu, yy, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { red[0][w] = xr; red[1][w] = xi; red[2][w] = xx; red[3][w] = yy; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    xr = xi = xx = yy = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      xr += red[0][k]; xi += red[1][k]; xx += red[2][k]; yy += red[3][k];
+    }
+    mu[p] = make_double2(xx > 0 ? xr / xx : 0.0, xx > 0 ? xi / xx : 0.0);
+    red[0][0] = yy > 0 ? 1.0 / sqrt(yy) : 0.0;
+  }
+  __syncthreads();
+  const double sc = red[0][0];
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const double2 b = yp[r];
+    xp[r] = make_double2(b.x * sc, b.y * sc);
+  }
+}
+
+cudaError_t launch_eig_update(cudaStream_t s, int P, int n, double2* x, const double2* y, double2* mu) {
+  k_eig_update<<<P, 256, 0, s>>>(P, n, x, y, mu);
+  return cudaGetLastError();
+}
+
 }  // namespace spectau

@@ -165,6 +165,7 @@ cudaError_t launch_band_factor(cudaStream_t s, int P, int n, int nnz, int kl, in
                                double* work, const BandFactor& f, int npad, int lpad, int upad,
                                DevStatus* st);
 cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a);
+cudaError_t launch_eig_update(cudaStream_t s, int P, int n, double2* x, const double2* y, double2* mu);
 size_t pencil_solve_smem(int npad, int lpad, int upad);
 cudaError_t launch_pencil_solve_batched(cudaStream_t s, const SolveArgs* args, const int4* work, int nwork,
                                         int max_kuu, size_t smem);

@@ -80,6 +80,15 @@ def rb_pencil_problem(Ra, Pr=1.0, variables=SLOT_ORDER, row_order=ROW_ORDER):
                          var_phase={"u": 1, "uz": 1}, row_order=row_order)
 
 
+def rb_onset_pencil_problem(Ra, Pr=1.0, variables=SLOT_ORDER, row_order=ROW_ORDER):
+    """The linearization about the conductive state b = 1 - z (u = w = 0):
+    the advection w dz(b0) = -w of the background moves to the b equation's
+    left side as -w (eigenproblems: sigma M X + L X = 0)."""
+    pr = rb_pencil_problem(Ra, Pr, variables, row_order)
+    pr.eq_by_name["b"].L.append(Term("w", "I", -1.0))
+    return pr
+
+
 # --- three dimensions: Fourier x, Fourier y, Chebyshev z ----------------------
 
 VARIABLES_3D = ("b", "p", "u", "v", "w", "bz", "uz", "vz", "wz")

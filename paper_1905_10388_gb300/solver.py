@@ -162,6 +162,22 @@ class TauSolver:
         L.check(h, L.lib().sp_cfl_frequency(h, self.pid, n, vs, ax, ctypes.byref(f)))
         return f.value
 
+    def eig_target(self, sigma_t, iters=60, x0=None):
+        """Eigenvalue sigma of sigma M~ X~ + L~ X~ = 0 nearest the real target
+        sigma_t in every pencil (shift-and-invert power iteration in the
+        library); x0: complex [P][n] start vectors in solve-variable order.
+        Replaces the step's factorization (factor again before stepping)."""
+        re, im = np.zeros(self.P), np.zeros(self.P)
+        h = self.ctx.handle
+        xp = None
+        if x0 is not None:
+            x0 = np.ascontiguousarray(x0, dtype=np.complex128)
+            xp = x0.ctypes.data_as(ctypes.c_void_p)
+        L.check(h, L.lib().sp_eig_target(h, self.pid, float(sigma_t), int(iters), xp,
+                                         re.ctypes.data_as(ctypes.c_void_p), im.ctypes.data_as(ctypes.c_void_p)))
+        self.dt = None
+        return re + 1j * im
+
     def solve_work(self):
         """(multiply-adds per row and real right-hand side, factor bytes per
         pencil) of the substitution as the solve kernel performs it."""
@@ -319,6 +335,21 @@ class FisherKPPSolver(TauSolver):
         device), uz = dz u (device recurrence)."""
         self.set_field("u", np.asarray(u_grid, np.float64), layout="g")
         self.dz("u", "uz")
+
+
+class RBOnsetEVP(TauSolver):
+    """The linearization of 2D Rayleigh-Benard convection about the
+    conductive state (b = 1 - z: the advection of the background adds -w to
+    the b equation's L) as a pencil eigenproblem sigma M X + L X = 0; a
+    perturbation grows as exp(sigma t), so sigma is the growth rate."""
+
+    def __init__(self, ctx, n_x, n_z, Ra, Pr=1.0, L_x=4.0):
+        super().__init__(ctx, rbmod.rb_onset_pencil_problem(Ra, Pr), n_x, n_z, L_x)
+        self.state_order = rbmod.VARIABLES
+
+    def growth_rates(self, target=0.0, iters=60, x0=None):
+        """Growth rate sigma of the mode nearest `target` in every pencil."""
+        return self.eig_target(target, iters, x0)
 
 
 class RB3DSolver(TauSolver):

@@ -1,0 +1,91 @@
+"""GPU parity of the pencil eigenvalue solver (Sec. "Eigenvalue solver",
+sparse solver: shift and invert) on the Rayleigh-Benard onset problem.
+
+* every pencil's eigenvalue nearest the target equals the one the oracle's
+  dense generalized eigensolver finds nearest it (scipy.linalg.eig on the
+  oracle's own, non-interleaved pencil), to 1e-9;
+* at the textbook critical wavenumber the growth rate changes sign between
+  0.99 and 1.01 times the textbook Ra_c (tests/golden/rb_onset.txt);
+* stepping after an eigensolve needs a new factorization.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import rb as orb
+from paper_1905_10388_gb300 import _lib as L
+from paper_1905_10388_gb300.solver import Context, RBOnsetEVP
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "rb_onset.txt")
+
+
+def _golden():
+    vals = {}
+    for line in open(GOLDEN):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split("=")
+            vals[k.strip()] = float(v)
+    return vals
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def _nearest_dense(Nz, Ra, k, target):
+    """Nearest eigenvalue and the convergence ratio |t - s1| / |t - s2| of
+    the power iteration on the shift-and-invert operator."""
+    M, Lm = orb.rb_onset_pencil(Nz, Ra, 1.0, k)
+    w = sla.eig(-Lm.toarray(), M.toarray(), right=False)
+    w = w[np.isfinite(w)]
+    d = np.sort(np.abs(w - target))
+    return w[np.argmin(np.abs(w - target))], d[0] / d[1]
+
+
+@pytest.mark.parametrize("Ra,target", [(2000.0, 0.0), (1e5, 0.5)])
+def test_nearest_eigenvalue_matches_dense_oracle(ctx, Ra, target):
+    """Pencils whose two nearest eigenvalues are too close to separate in
+    `iters` power steps (ratio^iters > 1e-10) are left out."""
+    Nx, Nz, Lx, iters = 32, 32, 4.0, 300
+    e = RBOnsetEVP(ctx, Nx, Nz, Ra, L_x=Lx)
+    got = e.growth_rates(target, iters=iters)
+    kx = 2 * np.pi * np.arange(Nx // 2) / Lx
+    checked = 0
+    for p in range(Nx // 2):
+        ref, ratio = _nearest_dense(Nz, Ra, kx[p], target)
+        if ratio ** iters > 1e-10:
+            continue
+        checked += 1
+        assert abs(got[p] - ref) < 1e-9 * max(1.0, abs(ref)), (p, got[p], ref, ratio)
+    assert checked >= Nx // 4
+
+
+def test_onset_sign_change_at_textbook_critical_point(ctx):
+    g = _golden()
+    Ra_c, k_c = g["Ra_c"], g["k_c"]
+    Lx = 2 * np.pi / k_c                       # pencil 1 sits at k_c
+    rates = []
+    for f in (0.99, 1.01):
+        e = RBOnsetEVP(ctx, 16, 32, f * Ra_c, L_x=Lx)
+        rates.append(e.growth_rates(0.0, iters=300)[1])
+    assert rates[0].real < 0 < rates[1].real
+    assert abs(rates[0].imag) < 1e-12 and abs(rates[1].imag) < 1e-12
+
+
+def test_step_after_eigensolve_needs_factor(ctx):
+    e = RBOnsetEVP(ctx, 16, 16, 2000.0)
+    e.factor(1e-3)
+    e.growth_rates(0.0, iters=5)
+    with pytest.raises(L.SpectauError):
+        e.step(1, dt=1e-3)
