@@ -55,10 +55,11 @@ STAGES = {"RK222": 2, "RK443": 4, "RK111": 1, "SBDF1": 1, "SBDF2": 1, "SBDF3": 1
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
 # k_pencil_solve launch of the 512x256 SBDF2 mixed-precision step, from one
-# ncu capture of `bench.py --steps 3 --warmup 3 --no-cpu-baseline`.  It is
+# ncu capture of `bench.py --steps 3 --warmup 3 --no-cpu-baseline`
+# (metrics dram__bytes_read.sum, dram__bytes_write.sum, one launch).  It is
 # reported only while the kernel's sources hash to the captured ones.
-SOLVE_TRAFFIC = {"workload": "rb2d_512x256_sbdf2", "precision": "mixed", "bytes": 180.167424e6,
-                 "sources_sha256": "6e1faf7afac97e168c6b898896ba0d11584f537a2c2b681e09e6b6babf466739"}
+SOLVE_TRAFFIC = {"workload": "rb2d_512x256_sbdf2", "precision": "mixed", "bytes": 179.688704e6,
+                 "sources_sha256": "122f04f36a85c3048d2d61e501482163f9f8b4371ef3dcdfde4362e20e578a96"}
 SOLVE_SOURCES = ("paper_1905_10388_gb300/csrc/band.cu", "paper_1905_10388_gb300/csrc/internal.h",
                  "paper_1905_10388_gb300/csrc/common.cuh")
 
@@ -380,6 +381,60 @@ def run_cfl(args):
     return res
 
 
+def run_evp(args):
+    """Growth rate of the mode nearest zero in every pencil of the
+    linearized 512x256 Rayleigh-Benard problem at Ra = 1e4 (Sec. "Eigenvalue
+    solver", shift and invert): one factorization of L~ + sigma_T M~, then
+    `steps` power iterations (a banded solve and a normalization each)."""
+    import torch
+    torch.cuda.set_device(0)
+    import scipy.linalg as sla
+    from oracle import rb as orb
+    from paper_1905_10388_gb300.solver import Context, RBOnsetEVP
+    Nx, Nz, Ra, Lx = 512, 256, 1e4, 4.0
+    ctx = Context(0, torch.cuda.current_stream(0).cuda_stream)
+    e = RBOnsetEVP(ctx, Nx, Nz, Ra, L_x=Lx)
+    e.growth_rates(0.0, iters=args.warmup)
+    stream = torch.cuda.current_stream(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rates = e.growth_rates(0.0, iters=args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    dof = 7 * Nx * Nz
+    # oracle: the dense generalized eigensolver on two sampled pencils
+    kx = 2 * np.pi * np.arange(Nx // 2) / Lx
+    t0 = time.perf_counter()
+    worst = 0.0
+    for p in (1, 3):
+        M, Lm = orb.rb_onset_pencil(Nz, Ra, 1.0, kx[p])
+        w = sla.eig(-Lm.toarray(), M.toarray(), right=False)
+        w = w[np.isfinite(w)]
+        ref = w[np.argmin(np.abs(w))]
+        worst = max(worst, abs(rates[p] - ref) / max(1.0, abs(ref)))
+    t_pencil = (time.perf_counter() - t0) / 2
+    res = {"metric": "pencil eigenmodes/s (mode nearest the target, every pencil)",
+           "value": (Nx // 2) / (ms * 1e-3), "unit": "pencils/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (the linearized Rayleigh-Benard pencils; start vectors all ones)",
+           "config": {"workload": "rb2d_512x256_onset_evp", "n_x": Nx, "n_z": Nz, "Ra": Ra, "target": 0.0,
+                      "iterations": args.steps, "dof": dof, "l2": "working set > L2 (factor read every iteration)"},
+           "evp": {"ms_total": ms, "max_rate": float(np.max(rates.real)), "sampled_rel_err_vs_dense": worst},
+           "cpu_baseline": {"value": 1.0 / t_pencil, "unit": "pencils/s", "cores": os.cpu_count(),
+                            "kind": "oracle", "sample": f"dense scipy.linalg.eig of 2 pencils (n = {7 * Nz}), "
+                                                         f"{t_pencil:.1f} s each"},
+           "roofline": None, "gpu_launches": 1 + 2 * args.steps, "clocks": clk}
+    ctx.close()
+    return res
+
+
 def run_adjoint(args):
     """Gradient of the final-buoyancy misfit through K RK222 steps (discrete
     adjoint with checkpoints every 50 steps): forward sweep, adjoint sweep,
@@ -572,6 +627,8 @@ def main():
         res = run_adjoint(args)
     elif args.workload == "rb2d_512x256_rk222_cfl":
         res = run_cfl(args)
+    elif args.workload == "rb2d_512x256_onset_evp":
+        res = run_evp(args)
     else:
         res = run_ours(args)
         if res is not None and not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:
