@@ -695,12 +695,18 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// doubles of shared memory per warp: two forward buffers (multipliers and
-// pivots) or two backward buffers (listed U entries), whichever is larger
+// Rows staged ahead in the lane substitution: LANE_BUFS buffers, the copy
+// of row j + LANE_BUFS - 1 in flight while row j is used
+constexpr int LANE_BUFS = 3;
+
+// doubles of shared memory per warp: LANE_BUFS forward buffers (multipliers
+// and pivots) or LANE_BUFS backward buffers (listed U entries), whichever is
+// larger
 __host__ __device__ inline int lane_stride(int kl, int cmax) {
-  const int fw = 2 * (kl * LANE_GROUP + 2), bw = 2 * cmax * LANE_GROUP;
+  const int fw = LANE_BUFS * (kl * LANE_GROUP + 2), bw = LANE_BUFS * cmax * LANE_GROUP;
   return fw > bw ? fw : bw;
 }
 
@@ -726,11 +732,11 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, co
   double* st = lane_stage + (size_t)(threadIdx.x >> 5) * lane_stride(KL, cmax);
   // forward: row interchanges and unit-lower multipliers; win[t] = row j + t.
   // Each row's multipliers and pivot offsets for the warp's 16 pencils are
-  // copied into shared memory one row ahead (cp.async, two buffers).
+  // copied into shared memory two rows ahead (cp.async, three buffers).
   constexpr int FW = KL * LANE_GROUP + 2;        // doubles per forward buffer (+16 bytes of pivots)
   auto fstage = [&](int jr) {
     const double* src = Lg + (gn + jr) * KL * LANE_GROUP;
-    double* dst = st + (jr & 1) * FW;
+    double* dst = st + (jr % LANE_BUFS) * FW;
     for (int c = lane; c < KL * (LANE_GROUP / 2); c += 32) cp_async16(dst + 2 * c, src + 2 * c);
     if (lane == 31) cp_async16(dst + KL * LANE_GROUP, pg + (gn + jr) * LANE_GROUP);
     cp_async_commit();
@@ -740,12 +746,14 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, co
 #pragma unroll
     for (int t = 0; t <= KL; ++t) win[t] = (act && t < n) ? bp[2 * t] : 0.0;
     fstage(0);
+    if (n > 1) fstage(1);
+    else cp_async_commit();
     for (int j = 0; j < n; ++j) {
-      if (j + 1 < n) fstage(j + 1);
-      else cp_async_commit();
-      cp_async_wait1();
+      if (j + 2 < n) fstage(j + 2);
+      else cp_async_commit();                    // one group per row keeps wait_group 2 exact
+      cp_async_wait2();
       __syncwarp();
-      const double* Ls = st + (j & 1) * FW;
+      const double* Ls = st + (j % LANE_BUFS) * FW;
       const int off = reinterpret_cast<const uint8_t*>(Ls + KL * LANE_GROUP)[i];
       const double* Lrow = Ls + i;
       double piv_val = win[0];
@@ -760,7 +768,7 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, co
 #pragma unroll
       for (int t = 0; t < KL; ++t) win[t] = win[t + 1];
       win[KL] = (act && j + KL + 1 < n) ? bp[2 * (j + KL + 1)] : 0.0;
-      __syncwarp();                              // buffer j & 1 is refilled for row j + 2 next
+      __syncwarp();                              // buffer j % 3 is refilled for row j + 3 next
     }
     cp_async_wait0();
     __syncwarp();
@@ -768,7 +776,7 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, co
   // back substitution with the scaled columns U_{j-t,j} / U_jj.  Only entries
   // nonzero in some pencil are stored: the k-th set bit t of umask[j] holds
   // U_{j-t,j} / U_jj at Uc[g][j][k] (k = 0: 1/U_jj).  Each row's entries
-  // are copied into shared memory one row ahead (cp.async, two buffers per
+  // are copied into shared memory two rows ahead (cp.async, three buffers per
   // warp), and only the listed entries issue an FMA: the mask is the same for
   // the whole warp, so the loop branches (a predicated-off FP64 instruction
   // would still hold the FP64 pipe) and jumps to the FMA of its window
@@ -776,7 +784,7 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, co
   auto stage = [&](int jr) {
     const int cnt = __popcll(umask[jr]);
     const double* src = Uc + (gn + jr) * (size_t)cmax * LANE_GROUP;
-    double* dst = st + (jr & 1) * cmax * LANE_GROUP;
+    double* dst = st + (jr % LANE_BUFS) * cmax * LANE_GROUP;
     for (int c = lane; c < cnt * (LANE_GROUP / 2); c += 32) cp_async16(dst + 2 * c, src + 2 * c);
     cp_async_commit();
   };
@@ -785,12 +793,14 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, co
   for (int t = 0; t <= KUU; ++t) w[t] = (act && n - 1 - t >= 0) ? yp[(size_t)2 * (n - 1 - t) * LANE_GROUP] : 0.0;
   double* xp = reinterpret_cast<double*>(x + (size_t)(act ? pen : 0) * n) + comp;
   stage(n - 1);
+  if (n > 1) stage(n - 2);
+  else cp_async_commit();
   for (int j = n - 1; j >= 0; --j) {
-    if (j >= 1) stage(j - 1);
-    else cp_async_commit();                      // one group per row keeps wait_group 1 exact
-    cp_async_wait1();
+    if (j >= 2) stage(j - 2);
+    else cp_async_commit();                      // one group per row keeps wait_group 2 exact
+    cp_async_wait2();
     __syncwarp();
-    const double* vals = st + (j & 1) * cmax * LANE_GROUP + i;
+    const double* vals = st + (j % LANE_BUFS) * cmax * LANE_GROUP + i;
     const unsigned long long m = umask[j];
     const double bj = w[0];
     if (act) xp[2 * j] = bj * vals[0];
@@ -877,7 +887,7 @@ __global__ void __launch_bounds__(128) k_pencil_lanes(int P, int n, int cmax, co
     for (int t = 0; t < KUU; ++t) w[t] = w[t + 1];
     const int row = j - KUU - 1;
     w[KUU] = (act && row >= 0) ? yp[(size_t)2 * row * LANE_GROUP] : 0.0;
-    __syncwarp();                                // buffer j & 1 is refilled for row j - 2 next
+    __syncwarp();                                // buffer j % 3 is refilled for row j - 3 next
   }
   cp_async_wait0();
 }
