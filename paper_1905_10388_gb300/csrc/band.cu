@@ -419,6 +419,10 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     // forward: row interchanges and unit-lower multipliers
     double v = Bd[2 * lane];          // window element b[j + ((lane - j) & 31)]
     double nv = Bd[2 * (lane + 32)];  // the element this lane takes next
+    // shuffle source: v before the owner lane swaps in its next element --
+    // the shuffles of a step read the pivot lane and lane jj, never the
+    // previous step's owner, so the swap stays off the dependency chain
+    double vs = v;
     for (int c = 0; c < nchunks; ++c) {
       const int s = c % SOLVE_RING;
       if (!chunk_sync(&sm.barL[s], c, doneL)) { ok = false; break; }
@@ -435,11 +439,12 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
         const int pl = (jj + off) & 31;
         const int d = (lane - jj) & 31;
         const double l = (d >= 1 && d <= a.kl) ? Lc[jj * a.lpad + d - 1] : 0.0;
-        const double bj = __shfl_sync(0xffffffffu, v, pl);   // pivot row value = y_j
-        const double vo = __shfl_sync(0xffffffffu, v, jj);   // old b_j moves to the pivot row
+        const double bj = __shfl_sync(0xffffffffu, vs, pl);  // pivot row value = y_j
+        const double vo = __shfl_sync(0xffffffffu, vs, jj);  // old b_j moves to the pivot row
         const double nxt = Bd[2 * (j0 + jj + 64)];   // same address in every lane
         v = (lane == pl) ? vo : v;
         v = fma(-l, bj, v);
+        vs = v;
         const bool own = (lane == jj);
         if (own) Bd[2 * (j0 + jj)] = bj;
         v = own ? nv : v;
@@ -462,6 +467,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
       w[r] = (ok && i >= 0) ? Bd[2 * i] : 0.0;
       nw[r] = (ok && i - W >= 0) ? Bd[2 * (i - W)] : 0.0;
     }
+    double ws = w[0];   // RU = 1: shuffle source before the owner's swap (as vs above)
     for (int k = 0; ok && k < nchunks; ++k) {
       const int s = k % SOLVE_RING;
       if (!chunk_sync(&sm.barU[s], k, doneU)) { ok = false; break; }
@@ -478,7 +484,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
         const int j = j0 + jj;
         const double* Ucol = Uc + jj * a.upad;
         const int oreg = (RU == 1) ? 0 : ((j & (W - 1)) >> 5);
-        double src = w[0];
+        double src = (RU == 1) ? ws : w[0];
 #pragma unroll
         for (int r = 1; r < RU; ++r) src = (oreg == r) ? w[r] : src;
         const double bj = __shfl_sync(0xffffffffu, src, jj);
@@ -488,6 +494,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
           const double u = (t >= 1) ? Ucol[t] : 0.0;
           w[r] = fma(-u, bj, w[r]);
         }
+        if (RU == 1) ws = w[0];
         const double nxt = (j - 2 * W >= 0) ? Bd[2 * (j - 2 * W)] : 0.0;   // same address in every lane
         const bool own = (lane == jj);
         xo = own ? bj : xo;
