@@ -135,7 +135,6 @@ struct Problem {
   double* d_MvC = nullptr;
   int32_t *d_col_map = nullptr, *d_row_map = nullptr, *d_var_rec = nullptr, *d_var_ph = nullptr;
   int32_t *d_eq_diff = nullptr, *d_eq_ph = nullptr, *d_bc_rows = nullptr, *d_nl_eq = nullptr;
-  int32_t *d_row_f = nullptr, *d_row_bc = nullptr;   // inverse row maps of the right-hand side
   double2* d_bc_values = nullptr;
   double* d_kx = nullptr;
   int32_t *d_gvar = nullptr, *d_gop = nullptr, *d_tslot = nullptr, *d_tfa = nullptr, *d_tfb = nullptr;
@@ -345,17 +344,6 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
   CK(upload(&pr->d_tfb, pr->t_fb, s));
   CK(upload(&pr->d_tcoef, pr->t_coef, s));
   CK(upload(&pr->d_nl_eq, pr->nl_eqs, s));
-  {
-    std::vector<int32_t> row_f(pr->n, -1), row_bc(pr->n, -1);
-    for (size_t sl = 0; sl < pr->nl_eqs.size(); ++sl)
-      for (int m = 0; m < pr->Nz; ++m) {
-        const int r = pr->row_map[(size_t)pr->nl_eqs[sl] * pr->Nz + m];
-        if (r >= 0) row_f[r] = (int32_t)(sl * pr->Nz + m);
-      }
-    for (int q = 0; q < pr->nbc; ++q) row_bc[pr->bc_rows[q]] = q;
-    CK(upload(&pr->d_row_f, row_f, s));
-    CK(upload(&pr->d_row_bc, row_bc, s));
-  }
   std::vector<int32_t> ident(64), zero(64, 0);
   for (int i = 0; i < 64; ++i) ident[i] = i;
   CK(upload(&pr->d_ident, ident, s));
@@ -425,7 +413,7 @@ void free_problem(Problem* pr) {
   auto F = [](void* p) { if (p) cudaFree(p); };
   F(pr->d_indptr); F(pr->d_indices); F(pr->d_Mv); F(pr->d_Lv); F(pr->d_indptrM); F(pr->d_indicesM); F(pr->d_mrows); F(pr->d_MvC); F(pr->d_col_map); F(pr->d_row_map);
   F(pr->d_var_rec); F(pr->d_var_ph); F(pr->d_eq_diff); F(pr->d_eq_ph); F(pr->d_bc_rows); F(pr->d_nl_eq);
-  F(pr->d_row_f); F(pr->d_row_bc);
+
   F(pr->d_cfl_grid); F(pr->d_cfl_mid1); F(pr->d_cfl_mid2); F(pr->d_inv_dz); F(pr->d_cfl_args); F(pr->d_cfl_out);
   F(pr->d_bc_values); F(pr->d_kx); F(pr->d_gvar); F(pr->d_gop); F(pr->d_tslot); F(pr->d_tfa); F(pr->d_tfb);
   F(pr->d_tcoef); F(pr->d_ident); F(pr->d_zero); F(pr->d_Xt); F(pr->d_Xc); F(pr->d_Xc32); F(pr->d_kx32);
@@ -522,7 +510,6 @@ SolveArgs base_args(Problem* pr, sp_ctx* ctx, int fac) {
   a.eq_differential = pr->d_eq_diff; a.eq_phase = pr->d_eq_ph;
   a.nl_eq = pr->d_nl_eq; a.n_nl = (int)pr->nl_eqs.size();
   a.bc_rows = pr->d_bc_rows; a.bc_values = pr->d_bc_values;
-  a.row_f = pr->d_row_f; a.row_bc = pr->d_row_bc;
   a.status = ctx->d_status;
   a.xc32_out = pr->d_Xc32;   // null unless mixed precision
   a.Lg = pr->fac[fac].Lg; a.Ug = pr->fac[fac].Ug; a.pg = pr->fac[fac].pg;   // null unless lane mode

@@ -100,9 +100,6 @@ struct SolveArgs {
   // epilogue (mode 2): store (B~ - ep_alpha M~X~) ep_from_b, i.e. L~X~ from the
   // stage's own right-hand side, when ep_from_b != 0
   double ep_from_b, ep_alpha;
-  // inverse row maps: row_f[r] = slot * N_z + m of the F~ entry placed in row r
-  // (or -1), row_bc[r] = boundary row index q (or -1)
-  const int32_t* row_f; const int32_t* row_bc;
   // factor in the lane-interleaved layout (null: not available)
   const double* Lg; const double* Ug; const uint8_t* pg; const unsigned long long* umask; int cmax;
 };
