@@ -27,8 +27,12 @@
 namespace spectau {
 
 // ---------------------------------------------------------------------------
-// factorization: one warp per pencil, working in a global band array
-// AB[p][j][t], t = i - j + kuu, holding a*M~ + b*L~
+// factorization: one warp per pencil.  The band a*M~ + b*L~ is assembled in a
+// global array AB[p][j][t] (t = i - j + kuu), then eliminated column by
+// column (LAPACK gbtrf order: partial pivoting within the kl rows below the
+// diagonal) in a shared-memory ring of the kuu + 1 columns a step touches;
+// each column leaves the ring, in the solve layout, as soon as it is final,
+// and the next column of AB enters.
 // ---------------------------------------------------------------------------
 __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32_t* __restrict__ indptr,
                               const int32_t* __restrict__ indices, const double* __restrict__ Mv,
@@ -36,12 +40,17 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
                               double* __restrict__ work, double* __restrict__ Lf, uint8_t* __restrict__ piv,
                               double* __restrict__ Uf, double* __restrict__ Rd, int npad, int lpad, int upad,
                               DevStatus* st) {
+  extern __shared__ __align__(16) double fring[];
   const int warps = blockDim.x / 32;
-  const int p = blockIdx.x * warps + threadIdx.x / 32;
+  const int wi = threadIdx.x / 32;
+  const int p = blockIdx.x * warps + wi;
   const int lane = threadIdx.x & 31;
   if (p >= P) return;
   const int kuu = kl + ku;
   const int ldab = kl + kuu + 1;
+  const int R = kuu + 1;                          // ring columns: j .. j + kuu
+  double* ring = fring + (size_t)wi * R * ldab;
+  auto slot = [&](int c) { return ring + (size_t)(c % R) * ldab; };
   double* AB = work + (size_t)p * n * ldab;
   for (size_t e = lane; e < (size_t)n * ldab; e += 32) AB[e] = 0.0;
   __syncwarp();
@@ -54,11 +63,26 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
     }
   }
   __syncwarp();
+  for (int c = 0; c < min(R, n); ++c)
+    for (int t = lane; t < ldab; t += 32) slot(c)[t] = AB[(size_t)c * ldab + t];
+  __syncwarp();
   uint8_t* pv = piv + (size_t)p * npad;
+  double* Lp = Lf + (size_t)p * npad * lpad;
+  double* Up = Uf + (size_t)p * npad * upad;
+  double* Rp = Rd + (size_t)p * npad;
+  // the column that enters the ring next, fetched into registers one step
+  // ahead of its store (ldab <= 64: two entries per lane)
+  double pre0 = 0.0, pre1 = 0.0;
+  auto fetch = [&](int c) {
+    pre0 = (c < n && lane < ldab) ? AB[(size_t)c * ldab + lane] : 0.0;
+    pre1 = (c < n && lane + 32 < ldab) ? AB[(size_t)c * ldab + lane + 32] : 0.0;
+  };
+  fetch(R);
   bool singular = false;
   for (int j = 0; j < n; ++j) {
     const int m = min(kl, n - 1 - j);
-    double* colj = AB + (size_t)j * ldab;
+    const int clast = min(n - 1, j + kuu);
+    double* colj = slot(j);
     // pivot search: first maximum of |a| over rows j .. j+m
     double a = (lane <= m) ? fabs(colj[kuu + lane]) : -1.0;
     int ia = lane;
@@ -72,8 +96,8 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
     if (!(a > 0.0)) { singular = true; break; }
     // interchange rows j and j+t over columns j .. j+kuu
     if (t != 0) {
-      for (int c = j + lane; c <= min(n - 1, j + kuu); c += 32) {
-        double* col = AB + (size_t)c * ldab;
+      for (int c = j + lane; c <= clast; c += 32) {
+        double* col = slot(c);
         const int r0 = j - c + kuu, r1 = j + t - c + kuu;
         const double x0 = col[r0];
         col[r0] = col[r1];
@@ -82,15 +106,11 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
     }
     __syncwarp();
     const double pivot = colj[kuu];
-    double lt = 0.0;
-    if (lane >= 1 && lane <= m) {
-      lt = colj[kuu + lane] / pivot;
-      colj[kuu + lane] = lt;
-    }
+    if (lane >= 1 && lane <= m) colj[kuu + lane] = colj[kuu + lane] / pivot;
     __syncwarp();
     // rank-1 update of rows j+1..j+m, columns j+1..j+kuu
-    for (int c = j + 1 + lane; c <= min(n - 1, j + kuu); c += 32) {
-      double* col = AB + (size_t)c * ldab;
+    for (int c = j + 1 + lane; c <= clast; c += 32) {
+      double* col = slot(c);
       const double u = col[j - c + kuu];
       for (int tt = 1; tt <= m; ++tt) {
         const double l = colj[kuu + tt];
@@ -98,31 +118,31 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
       }
     }
     __syncwarp();
+    // column j is final: L multipliers, 1/U_jj and the scaled U column
+    const double rd = 1.0 / colj[kuu];
+    for (int q = lane; q < lpad; q += 32)
+      Lp[(size_t)j * lpad + q] = (q < kl && j + 1 + q < n) ? colj[kuu + 1 + q] : 0.0;
+    for (int q = lane; q < upad; q += 32)
+      Up[(size_t)j * upad + q] = q == 0 ? rd : ((q <= kuu && j - q >= 0) ? colj[kuu - q] * rd : 0.0);
+    if (lane == 0) Rp[j] = rd;
+    __syncwarp();
+    // its slot takes column j + kuu + 1 (fetched during this step)
+    if (j + R < n) {
+      if (lane < ldab) colj[lane] = pre0;
+      if (lane + 32 < ldab) colj[lane + 32] = pre1;
+    }
+    fetch(j + R + 1);
+    __syncwarp();
   }
   if (singular) {
     if (lane == 0) raise_status(st, SP_ERR_SINGULAR, p);
     return;
   }
-  // write the solve layout: L multipliers, scaled U columns
-  double* Lp = Lf + (size_t)p * npad * lpad;
-  double* Up = Uf + (size_t)p * npad * upad;
-  double* Rp = Rd + (size_t)p * npad;
-  for (int j = lane; j < npad; j += 32) {
-    if (j >= n) {
-      for (int t = 0; t < lpad; ++t) Lp[(size_t)j * lpad + t] = 0.0;
-      for (int t = 0; t < upad; ++t) Up[(size_t)j * upad + t] = 0.0;
-      pv[j] = 0;
-      Rp[j] = 0.0;
-      continue;
-    }
-    const double* col = AB + (size_t)j * ldab;
-    for (int t = 0; t < lpad; ++t)
-      Lp[(size_t)j * lpad + t] = (t < kl && j + 1 + t < n) ? col[kuu + 1 + t] : 0.0;
-    const double rd = 1.0 / col[kuu];
-    Up[(size_t)j * upad] = rd;
-    Rp[j] = rd;
-    for (int t = 1; t < upad; ++t)
-      Up[(size_t)j * upad + t] = (t <= kuu && j - t >= 0) ? col[kuu - t] * rd : 0.0;
+  for (int j = n + lane; j < npad; j += 32) {   // padding columns
+    for (int q = 0; q < lpad; ++q) Lp[(size_t)j * lpad + q] = 0.0;
+    for (int q = 0; q < upad; ++q) Up[(size_t)j * upad + q] = 0.0;
+    pv[j] = 0;
+    Rp[j] = 0.0;
   }
 }
 
@@ -131,9 +151,13 @@ cudaError_t launch_band_factor(cudaStream_t s, int P, int n, int nnz, int kl, in
                                const double* Lv, double alpha, double beta, double* work,
                                const BandFactor& f, int npad, int lpad, int upad, DevStatus* st) {
   const int wpb = 4;
-  k_band_factor<<<(P + wpb - 1) / wpb, 32 * wpb, 0, s>>>(P, n, nnz, kl, ku, indptr, indices, Mv, Lv,
-                                                        alpha, beta, work, f.L, f.piv, f.U, f.rd, npad,
-                                                        lpad, upad, st);
+  const size_t smem = (size_t)wpb * (kl + ku + 1) * (2 * kl + ku + 1) * sizeof(double);
+  if (smem > 227 * 1024 || 2 * kl + ku + 1 > 64) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_band_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_band_factor<<<(P + wpb - 1) / wpb, 32 * wpb, smem, s>>>(P, n, nnz, kl, ku, indptr, indices, Mv, Lv,
+                                                           alpha, beta, work, f.L, f.piv, f.U, f.rd, npad,
+                                                           lpad, upad, st);
   return cudaGetLastError();
 }
 
