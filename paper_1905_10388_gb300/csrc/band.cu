@@ -105,21 +105,34 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
       }
     }
     __syncwarp();
-    const double pivot = colj[kuu];
-    if (lane >= 1 && lane <= m) colj[kuu + lane] = colj[kuu + lane] / pivot;
+    // multipliers by the reciprocal of the pivot (as LAPACK's gbtf2 scales)
+    const double rd = 1.0 / colj[kuu];
+    if (lane >= 1 && lane <= m) colj[kuu + lane] *= rd;
     __syncwarp();
-    // rank-1 update of rows j+1..j+m, columns j+1..j+kuu
+    // rank-1 update of rows j+1..j+m, columns j+1..j+kuu: each lane loads
+    // its column's m entries and the m multipliers, then updates them all
+    // (independent FMAs in flight instead of one load-FMA-store at a time)
+    constexpr int MREG = 16;
     for (int c = j + 1 + lane; c <= clast; c += 32) {
       double* col = slot(c);
       const double u = col[j - c + kuu];
-      for (int tt = 1; tt <= m; ++tt) {
-        const double l = colj[kuu + tt];
-        col[j + tt - c + kuu] = fma(-l, u, col[j + tt - c + kuu]);
+      double* dst = col + (j - c + kuu);          // dst[tt]: row j + tt
+      if (m <= MREG) {
+        double lv[MREG], av[MREG];
+#pragma unroll
+        for (int tt = 0; tt < MREG; ++tt) {
+          lv[tt] = tt < m ? colj[kuu + 1 + tt] : 0.0;
+          av[tt] = tt < m ? dst[1 + tt] : 0.0;
+        }
+#pragma unroll
+        for (int tt = 0; tt < MREG; ++tt)
+          if (tt < m) dst[1 + tt] = fma(-lv[tt], u, av[tt]);
+      } else {
+        for (int tt = 1; tt <= m; ++tt) dst[tt] = fma(-colj[kuu + tt], u, dst[tt]);
       }
     }
     __syncwarp();
     // column j is final: L multipliers, 1/U_jj and the scaled U column
-    const double rd = 1.0 / colj[kuu];
     for (int q = lane; q < lpad; q += 32)
       Lp[(size_t)j * lpad + q] = (q < kl && j + 1 + q < n) ? colj[kuu + 1 + q] : 0.0;
     for (int q = lane; q < upad; q += 32)
