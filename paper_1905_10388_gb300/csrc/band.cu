@@ -83,17 +83,21 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
     const int m = min(kl, n - 1 - j);
     const int clast = min(n - 1, j + kuu);
     double* colj = slot(j);
-    // pivot search: first maximum of |a| over rows j .. j+m
-    double a = (lane <= m) ? fabs(colj[kuu + lane]) : -1.0;
+    // pivot search: first maximum of |a| over rows j .. j+m, compared on the
+    // bit patterns of |a| (their integer order is the numeric order of
+    // non-negative doubles; no FP64 compare on the chain)
+    unsigned long long a =
+        (lane <= m) ? ((unsigned long long)__double_as_longlong(colj[kuu + lane]) & 0x7fffffffffffffffull) : 0ull;
     int ia = lane;
     for (int o = 16; o > 0; o >>= 1) {
-      const double b = __shfl_xor_sync(0xffffffffu, a, o);
+      const unsigned long long b = __shfl_xor_sync(0xffffffffu, a, o);
       const int ib = __shfl_xor_sync(0xffffffffu, ia, o);
       if (b > a || (b == a && ib < ia)) { a = b; ia = ib; }
     }
     const int t = ia;
     if (lane == 0) pv[j] = (uint8_t)t;
-    if (!(a > 0.0)) { singular = true; break; }
+    // a zero pivot, or an infinite or NaN one
+    if (a == 0ull || a >= 0x7ff0000000000000ull) { singular = true; break; }
     // interchange rows j and j+t over columns j .. j+kuu
     if (t != 0) {
       for (int c = j + lane; c <= clast; c += 32) {
