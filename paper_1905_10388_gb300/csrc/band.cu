@@ -50,7 +50,8 @@ __global__ void k_band_factor(int P, int n, int nnz, int kl, int ku, const int32
   const int ldab = kl + kuu + 1;
   const int R = kuu + 1;                          // ring columns: j .. j + kuu
   double* ring = fring + (size_t)wi * R * ldab;
-  auto slot = [&](int c) { return ring + (size_t)(c % R) * ldab; };
+  const float invR = 1.0f / (float)R;
+  auto slot = [&](int c) { return ring + (size_t)(c - R * div_idx(c, invR)) * ldab; };   // c mod R
   double* AB = work + (size_t)p * n * ldab;
   for (size_t e = lane; e < (size_t)n * ldab; e += 32) AB[e] = 0.0;
   __syncwarp();
