@@ -33,7 +33,7 @@ def _make(ctx, scheme, prec, seed0=1000):
 
 
 @pytest.mark.parametrize("scheme,prec,graph", [("RK222", "fp64", False), ("RK222", "mixed", True),
-                                               ("SBDF2", "fp64", True)])
+                                               ("SBDF2", "fp64", True), ("RK443", "mixed", True)])
 def test_batch_equals_individual_steps(scheme, prec, graph):
     ctx = Context(0)
     solo = _make(ctx, scheme, prec)
@@ -45,6 +45,17 @@ def test_batch_equals_individual_steps(scheme, prec, graph):
     assert batch_tile(batch) in (4, 8, 16)
     for a, b in zip(solo, batch):
         assert np.array_equal(a.get_state(), b.get_state())
+    ctx.close()
+
+
+def test_batch_rejects_sbdf3():
+    """Batched stepping keeps two history slots per problem: SBDF3 and SBDF4
+    are refused with SP_ERR_ARG rather than stepped wrongly."""
+    from paper_1905_10388_gb300 import _lib as L
+    ctx = Context(0)
+    solvers = _make(ctx, "SBDF3", "fp64")[:2]
+    with pytest.raises(L.SpectauError):
+        step_batched(solvers, 3, graph=False)
     ctx.close()
 
 
