@@ -1,7 +1,7 @@
 """Rayleigh-Benard convection in first-order tau form (oracle; test infrastructure).
 
 The paper does not write these equations; this is the reading used on both
-sides (stated once, here and in the design notes).  Free-fall units with
+sides.  Free-fall units with
 kappa = (Ra Pr)^(-1/2), nu = (Ra/Pr)^(-1/2); z in [0, 1] (Chebyshev),
 x in [0, L_x) (Fourier), buoyancy b, gravity along -z.  In the paper's IVP
 form  M dt(X) + L X = F(X)  (Sec. "Initial value solver", Eq. ivp) with
@@ -24,8 +24,11 @@ transforms & dealiasing"): backward transforms (z then x) of u, w, dx b, bz,
 dx u, uz, dx w, wz, pointwise products, forward transforms (x then z).
 
 Pins: ``tests/test_oracle_rb.py`` (conductive steady state, linear onset at the
-textbook Ra_c = 1707.76, k_c = 3.117, mean/BC invariants).  Long nonlinear
-trajectories: parity unpinned beyond these invariants.
+textbook Ra_c = 1707.76, k_c = 3.117, mean/BC invariants) and
+``tests/test_oracle_advection.py`` (the advective terms of ``nonlinear``
+against their closed form on a manufactured band-limited state, evaluated
+pointwise by explicit sums).  Long nonlinear trajectories have no closed form:
+they are pinned only through these pieces.
 """
 import numpy as np
 

@@ -23,7 +23,9 @@ x backward and x, y, z forward, on the 3/2 grid.
 
 Pins: ``tests/test_oracle_rb3d.py`` (y-transform modes and round trip, the
 reduction to the 2D system for y-independent states, rotation invariance of
-the linear growth rates, the conductive steady state).
+the linear growth rates, the conductive steady state) and
+``tests/test_oracle_advection.py`` (the advective terms against their closed
+form on a manufactured band-limited state).
 """
 import numpy as np
 
