@@ -355,10 +355,13 @@ sp_status sp_last_solve_time(sp_ctx* ctx, int problem, double* ms_per_launch, in
  * Its intermediate data and twiddle tables live in fixed static device
  * arrays that every GPU loading the library keeps until exit: at most
  * nfields * N_gz * (n_x/2) <= 524288 complex values (8 MiB), N_gx <= 4096,
- * N_gz <= 1536, nfields <= 16; larger requests return SP_ERR_ARG with the
- * reason in errbuf.  The first call on a device (with that device current)
- * looks up the device addresses of those arrays; make it before any stream
- * capture.  All calls share the arrays: calls that may overlap on the GPU
+ * N_gz <= 1536, nfields <= 16, and jointly one grid row of every field in a
+ * block's shared memory: (2 ceil(nfields/2) + 1) * N_gx * 16 + nfields * N_gx
+ * * 8 <= 227 KiB (N_gx <= 3632 for 2 fields, <= 580 for 16); larger requests
+ * return SP_ERR_ARG with the reason in errbuf, before anything is queued.
+ * The first call on a device (with that device current) looks up the device
+ * addresses of those arrays, once per device even under concurrent first
+ * calls from several host threads; make it before any stream capture.  All calls share the arrays: calls that may overlap on the GPU
  * (other streams or threads without ordering) race and must be serialized.
  * Each call rewrites everything it reads, so nothing carries over between
  * calls.  Asynchronous: the result is ready when the stream reaches it. */

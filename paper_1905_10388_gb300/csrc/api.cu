@@ -830,6 +830,23 @@ sp_status build_batch(sp_ctx* ctx, const std::vector<Problem*>& ps, const std::v
   return SP_OK;
 }
 
+// A batch bakes each problem's factor pointers and step coefficients (dt H,
+// dt A, the SBDF weights, the boundary-row coefficient) into its device
+// argument tables and captured graphs; once a problem is re-factored, every
+// cached batch that holds it is stale and is dropped.
+void drop_batches(sp_ctx* ctx, int problem) {
+  for (auto it = ctx->batches.begin(); it != ctx->batches.end();) {
+    const std::vector<int>& ids = it->first.first;
+    if (std::find(ids.begin(), ids.end(), problem) != ids.end()) {
+      free_batch(it->second);
+      delete it->second;
+      it = ctx->batches.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 sp_status batch_step(sp_ctx* ctx, Batch* b, cudaStream_t s) {
   for (const BatchStage& st : b->stages) {
     CK(launch_cheb_backward_batched(s, b->prec, b->tile, st.d_zb, b->d_wzb, b->nzb, b->max_ngz));
@@ -1149,6 +1166,7 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
   pr->factored = true;
   for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
   pr->graphs.clear();
+  drop_batches(ctx, problem);
   return SP_OK;
 }
 
@@ -1814,6 +1832,7 @@ sp_status sp_eig_target(sp_ctx* ctx, int problem, double sigma_t, int iters, con
   pr->factored = false;
   for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
   pr->graphs.clear();
+  drop_batches(ctx, problem);
   const int ldab = 2 * pr->kl + pr->ku + 1;
   double* work = nullptr;
   CK(dalloc(&work, (size_t)pr->P * pr->n * ldab));

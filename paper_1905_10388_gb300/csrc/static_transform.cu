@@ -15,7 +15,8 @@
 // device addresses of those arrays with cudaGetSymbolAddress; a host-side
 // name of a __device__ array is not a device address.  Make that first call
 // before any stream capture.  Later calls on the same device reuse the
-// addresses.
+// addresses; the set-up runs exactly once per device even when several host
+// threads make their first calls at the same time (std::call_once).
 //
 // Sharing: every call uses the same arrays.  Calls that overlap on the GPU
 // (different streams, or different threads, without ordering between them)
@@ -25,6 +26,7 @@
 // from the previous call.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 
@@ -46,7 +48,8 @@ static __device__ __align__(256) int32_t s_field_index[STATIC_MAX_FIELDS] = {0, 
 static __device__ __align__(256) int32_t s_field_op[STATIC_MAX_FIELDS] = {0};
 
 struct StaticAddrs {
-  bool ready = false;
+  std::once_flag once;            // set-up runs once per device, whichever host thread gets there first
+  cudaError_t setup = cudaSuccess;
   double2* scratch = nullptr;
   double2* tw_x = nullptr;
   double2* tw_z = nullptr;
@@ -114,23 +117,34 @@ extern "C" sp_status sp_transform_backward_static(const double* coef_dev, double
                   need, STATIC_SCRATCH_COMPLEX);
     return report(errbuf, errlen, SP_ERR_ARG, msg);
   }
+  // the x-row kernel keeps a whole grid row of every field in shared memory
+  // (227 KiB per CTA), which bounds N_gx jointly with nfields
+  const size_t xsm = x_smem_bytes(0, ngx, 1, nfields, 0);
+  const size_t zsm = z_smem_bytes(0, ngz, 4);
+  if (xsm > 227 * 1024 || zsm > 227 * 1024) {
+    std::snprintf(msg, sizeof msg,
+                  "%d fields at N_gx = %d, N_gz = %d need %zu B (x rows) / %zu B (z columns) of shared memory "
+                  "per block; the limit is %d B",
+                  nfields, ngx, ngz, xsm, zsm, 227 * 1024);
+    return report(errbuf, errlen, SP_ERR_ARG, msg);
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= STATIC_MAX_DEVICES)
     return report(errbuf, errlen, SP_ERR_CUDA, "no current CUDA device");
   StaticAddrs& A = g_static[dev];
-  if (!A.ready) {
-    // one-time set-up on this device: device addresses of the static arrays
+  // one-time set-up on this device: device addresses of the static arrays
+  std::call_once(A.once, [&A]() {
     cudaError_t e = cudaGetSymbolAddress((void**)&A.scratch, s_scratch);
     if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&A.tw_x, s_tw_x);
     if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&A.tw_z, s_tw_z);
     if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&A.dct_z, s_dct_z);
     if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&A.field_index, s_field_index);
     if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&A.field_op, s_field_op);
-    if (e != cudaSuccess) {
-      std::snprintf(msg, sizeof msg, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return report(errbuf, errlen, SP_ERR_CUDA, msg);
-    }
-    A.ready = true;
+    A.setup = e;
+  });
+  if (A.setup != cudaSuccess) {
+    std::snprintf(msg, sizeof msg, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(A.setup));
+    return report(errbuf, errlen, SP_ERR_CUDA, msg);
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   TransformPlan pz, px;

@@ -79,3 +79,25 @@ def test_batch_sample_against_oracle():
                                   lambda sysr: sysr.initial_state(si.rb_noise(1000 + i, nz, nx)), stepper, 4)
         check_fields(batch[i].get_state(), ref, floor, 1e-12)
     ctx.close()
+
+
+@pytest.mark.parametrize("scheme", ["RK222", "SBDF2"])
+def test_batch_after_refactor_equals_individual_steps(scheme):
+    """A batch caches each problem's factor and step coefficients in its
+    argument tables and graphs; re-factoring at a new dt must drop that cache,
+    so batch steps after the re-factor equal individual steps bit for bit."""
+    ctx = Context(0)
+    solo = _make(ctx, scheme, "fp64")
+    batch = _make(ctx, scheme, "fp64")
+    for s in solo:
+        s.step(4)
+    step_batched(batch, 4, graph=True)
+    for s in solo + batch:
+        s.factor(0.5e-3 * 32.0 / s.Nz)
+    for s in solo:
+        s.step(5)
+    step_batched(batch, 5, graph=True)
+    ctx.sync_status()
+    for a, b in zip(solo, batch):
+        assert np.array_equal(a.get_state(), b.get_state())
+    ctx.close()

@@ -6,9 +6,11 @@ into a CUDA graph, where cudaMalloc is not allowed, or when all device memory
 belongs to another allocator): its intermediate buffer and twiddle tables are
 fixed-size static device arrays.  This test calls it through the C ABI on
 device buffers, twice in a row with different fields and sizes, and checks
-each result against ``sp_transform`` (which allocates its own scratch) to the
-FP64 transform tolerance used elsewhere (1e-13 relative).  It lives in a file
-of its own that pytest collects last.
+each result against the FP64 oracle's backward transform (Chebyshev z, then
+Fourier x, Sec. "Scaled transforms & dealiasing") and against
+``sp_transform`` (which allocates its own scratch), to the FP64 transform
+tolerance used elsewhere (1e-13 relative).  It lives in a file of its own
+that pytest collects last.
 """
 import ctypes
 
@@ -19,6 +21,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
+from oracle import rb as orb
 from paper_1905_10388_gb300 import _lib
 from paper_1905_10388_gb300.solver import Context, RBSolver
 from gpu_util import rel_err
@@ -47,9 +50,13 @@ def test_static_backward_two_calls_in_a_row():
         rng = np.random.default_rng(seed)
         c = rng.standard_normal((nf, n_x // 2, n_z)) + 1j * rng.standard_normal((nf, n_x // 2, n_z))
         c[:, 0, :] = c[:, 0, :].real
+        ngx, ngz = n_x * scale[0] // scale[1], n_z * scale[0] // scale[1]
+        sysr = orb.RB2D(n_x, n_z, 1e6)
+        oracle_grid = np.stack([sysr.to_grid(c[f], ngx, ngz) for f in range(nf)])
         s = RBSolver(ctx, n_x, n_z, 1e6, dealias=scale)
         ref = s.transform(c, -1, scale)
         got = _static_backward(c, n_x, n_z, scale)
+        assert rel_err(got, oracle_grid) < 1e-13
         assert rel_err(got, ref) < 1e-13
     ctx.close()
 
@@ -60,3 +67,9 @@ def test_static_backward_rejects_oversize():
         ctypes.c_void_p(16), ctypes.c_void_p(16), 16, 1024, 512, 3, 2, None, err, len(err))
     assert st == _lib.SP_ERR_ARG
     assert b"static buffer" in err.value
+    # fits the intermediate buffer, but one grid row of both fields (N_gx =
+    # 4096: 256 KiB) exceeds a block's shared memory: refused before any launch
+    st = _lib.lib().sp_transform_backward_static(
+        ctypes.c_void_p(16), ctypes.c_void_p(16), 2, 2048, 64, 2, 1, None, err, len(err))
+    assert st == _lib.SP_ERR_ARG
+    assert b"shared memory" in err.value
