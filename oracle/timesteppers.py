@@ -12,7 +12,13 @@ printed there; for a constant step:
     SBDF3: a = (11/6, -3, 3/2, -1/3)/dt,     c = (-, 3, -3, 1)
     SBDF4: a = (25/12, -4, 3, -4/3, 1/4)/dt, c = (-, 4, -6, 4, -1)
 (the backward-difference weights of the implicit part and the polynomial
-extrapolation weights of the explicit part).
+extrapolation weights of the explicit part).  The Crank-Nicolson
+Adams-Bashforth schemes of the same family (also cited, not printed):
+    CNAB1: a = (1, -1)/dt,     b = (1/2, 1/2),     c = (-, 1)
+    CNAB2: a = (1, -1, 0)/dt,  b = (1/2, 1/2, 0),  c = (-, 3/2, -1/2)
+(the trapezoidal rule on the implicit part, Adams-Bashforth extrapolation
+of the explicit part; CNAB2 starts with one CNAB1 step, and both orders
+factor the same matrix M/dt + L/2).
 
 Runge-Kutta IMEX (Sec. "Runge-Kutta IMEX integrators"):
     (M + dt H_ii L) X^i = M X^0 + dt sum_{j<i} A_ij F^j - dt sum_{j<i} H_ij L X^j
@@ -30,7 +36,8 @@ there: implicit diagonal 1/2 throughout, c = [0, 1/2, 2/3, 1/2, 1],
 
 Pins: ``tests/test_oracle_timesteppers.py`` (amplification factors of the
 linear test equation, exact decay of polynomial diffusion modes, second-order
-convergence, SBDF two-term recurrence; for RK443 the third-order conditions
+convergence, SBDF two-term recurrence, the Crank-Nicolson factor of CNAB on a
+polynomial mode and CNAB2's second order; for RK443 the third-order conditions
 of both tableaux and of their coupling, third-order convergence of a
 diffusion mode and of a stiff-linear / quadratic-explicit scalar problem with
 a closed-form solution).
@@ -199,3 +206,18 @@ class SBDF:
         del self.hist_MX[keep:], self.hist_LX[keep:], self.hist_F[keep:]
         self.iteration += 1
         return sys.from_pencils(x_new)
+
+
+class CNAB(SBDF):
+    """CNAB1 / CNAB2 (Crank-Nicolson Adams-Bashforth, Wang & Ruuth 2008),
+    constant step, through the multistep form of ``SBDF.step``: the first
+    step at first order."""
+
+    @staticmethod
+    def coefficients(order, dt):
+        if order == 1:
+            return np.array([1.0, -1.0]) / dt, np.array([0.5, 0.5]), np.array([0.0, 1.0])
+        if order == 2:
+            return (np.array([1.0, -1.0, 0.0]) / dt, np.array([0.5, 0.5, 0.0]),
+                    np.array([0.0, 1.5, -0.5]))
+        raise ValueError("order")

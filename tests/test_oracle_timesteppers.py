@@ -244,3 +244,67 @@ def test_sbdf_order_from_exact_history(order):
         errs.append(abs(X[0] - exact(T)))
     r = np.array(errs[:-1]) / np.array(errs[1:])
     assert np.all(np.abs(np.log2(r) - order) < 0.35), r
+
+
+# ---------------------------------------------------------------------------
+# CNAB1 / CNAB2
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_cnab_coefficients_are_consistent(order):
+    """Trapezoidal implicit part (b = (1/2, 1/2)), first-difference a, and
+    Adams-Bashforth weights: sum c_j = 1, and for CNAB2 sum_j c_j (1 - j) =
+    1/2 (the extrapolation to the midpoint t^{n-1/2} is exact for lines)."""
+    a, b, c = ts.CNAB.coefficients(order, 1.0)
+    assert abs(a.sum()) < 1e-15 and a[0] == 1.0
+    assert b[0] == 0.5 and b[1] == 0.5 and abs(b.sum() - 1.0) < 1e-15
+    assert abs(c.sum() - 1.0) < 1e-15
+    if order == 2:
+        j = np.arange(order + 1)
+        assert abs((c * (1 - j)).sum() - 0.5) < 1e-15
+
+
+def test_cnab_neumann_mode_crank_nicolson_factor():
+    """F = 0: both orders reduce to the trapezoidal rule, x_{n+1} =
+    x_n (1 - h/2) / (1 + h/2) for the z-independent diffusion mode."""
+    N = 12
+    kx = 2 * np.pi * np.arange(3) / L_X
+    sysm = LinearPencilSystem(diffusion(N), kx)
+    X = _mode_state(sysm, N, 2, np.ones_like, np.zeros_like)
+    stepper = ts.CNAB(sysm, order=2)
+    dt = 0.2
+    h = KAPPA * kx[2] ** 2 * dt
+    amp0 = X[0, 2, 0]
+    for n in range(1, 8):
+        X = stepper.step(X, dt)
+        assert abs(X[0, 2, 0] - amp0 * ((1 - h / 2) / (1 + h / 2)) ** n) < 1e-14
+        assert np.abs(X[0, 2, 1:]).max() < 1e-14
+
+
+def test_cnab2_second_order():
+    """x' = -lam x - x^2 (closed form): second order from the CNAB1 start and
+    from an exact start-up history."""
+    lam, x0, T = 2.0, 1.0, 1.0
+
+    def exact(t):
+        return lam * x0 * np.exp(-lam * t) / (lam + x0 * (1 - np.exp(-lam * t)))
+
+    for warm in (False, True):
+        errs = []
+        for nsteps in (80, 160, 320):
+            dt = T / nsteps
+            sysm = _Scalar(lam)
+            st = ts.CNAB(sysm, 2)
+            if warm:
+                M, L = sysm.matrices()[0]
+                xk = np.array([exact(-dt)])
+                st.hist_MX.insert(0, [M @ xk])
+                st.hist_LX.insert(0, [L @ xk])
+                st.hist_F.insert(0, sysm.rhs_vectors(xk))
+                st.iteration = 1
+            X = np.array([x0])
+            for _ in range(nsteps):
+                X = st.step(X, dt)
+            errs.append(abs(X[0] - exact(T)))
+        r = np.array(errs[:-1]) / np.array(errs[1:])
+        assert np.all(np.abs(np.log2(r) - 2) < 0.3), (warm, r)
