@@ -6,6 +6,13 @@ dt = 1e-4, seeded synthetic initial state.  One "step" is one full IMEX
 step: dealiased transforms and products of the advective RHS, right-hand
 side assembly and one banded FP64 tau solve per Fourier pencil.
 
+The headline line is the FP64 form (the paper's arithmetic throughout); the
+mixed form (FP32 transforms and products, FP64 pencils) is timed in the same
+run and reported beside it under "mixed".  Each form's per-field error
+against the FP64 oracle (same seeded initial state, a bounded number of
+steps, computed outside the timed regions) is in "error".  The ALU roofline
+divides by this GPU's FP64 FMA throughput, measured at start-up.
+
 Timing: W untimed warm-up steps and an untimed rehearsal of the K steps
 (which captures their CUDA graphs), then K steps replayed from the graphs,
 bracketed by a barrier and torch.cuda.synchronize() and timed with CUDA
@@ -45,10 +52,6 @@ def measured_peaks():
     except Exception:
         return {}
 
-
-# FP64 peak of GB300: 1.25 TFLOP/s nominal; equivalently 152 SMs x 4
-# sub-partitions x one 32-lane DFMA per 64 cycles x 2 flops x 2.07 GHz.
-FP64_PEAK_TFLOPS = 1.25
 
 # implicit stage solves per step of each scheme
 STAGES = {"RK222": 2, "RK443": 4, "RK111": 1, "SBDF1": 1, "SBDF2": 1, "SBDF3": 1, "SBDF4": 1}
@@ -167,44 +170,32 @@ def solve_flops_bytes(s):
     return flops, factor_bytes + vec_bytes
 
 
-def run_ours(args):
-    import torch
-    distributed = int(os.environ.get("WORLD_SIZE", "1")) > 1
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    if distributed:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    from paper_1905_10388_gb300 import build as _b  # noqa: F401
-    from paper_1905_10388_gb300.solver import Context, FisherKPPSolver, RB3DSolver, RBSolver
-    w = si.WORKLOADS[args.workload]
-    ctx = Context(local, torch.cuda.current_stream(local).cuda_stream)
-    fisher = isinstance(w, si.FisherWorkload)
-    if fisher:
-        s = FisherKPPSolver(ctx, w.n_x, w.n_z, w.D, w.R, w.L_x, scheme=w.scheme, precision=args.precision)
+def _make_solver(ctx, w, precision, rank):
+    from paper_1905_10388_gb300.solver import FisherKPPSolver, RB3DSolver, RBSolver
+    if isinstance(w, si.FisherWorkload):
+        s = FisherKPPSolver(ctx, w.n_x, w.n_z, w.D, w.R, w.L_x, scheme=w.scheme, precision=precision)
         xi = si.fisher_noise(w.seed + rank, w.n_z, w.n_x)
     elif w.n_y > 1:
-        s = RB3DSolver(ctx, w.n_x, w.n_y, w.n_z, w.Ra, w.Pr, w.L_x, w.L_y, scheme=w.scheme,
-                       precision=args.precision)
+        s = RB3DSolver(ctx, w.n_x, w.n_y, w.n_z, w.Ra, w.Pr, w.L_x, w.L_y, scheme=w.scheme, precision=precision)
         xi = si.rb_noise3(w.seed + rank, w.n_z, w.n_y, w.n_x)
     else:
-        s = RBSolver(ctx, w.n_x, w.n_z, w.Ra, w.Pr, w.L_x, scheme=w.scheme, precision=args.precision)
+        s = RBSolver(ctx, w.n_x, w.n_z, w.Ra, w.Pr, w.L_x, scheme=w.scheme, precision=precision)
         xi = si.rb_noise(w.seed + rank, w.n_z, w.n_x)
     s.factor(w.dt)
     s.set_initial_state(xi)
+    return s, xi
+
+
+def _time_form(s, args, stages, stream, distributed):
+    """Warm-up, graph rehearsal, the K timed steps replayed from graphs, then
+    the same K steps launched one by one with events around every solve."""
+    import torch
     s.step(args.warmup)
     # a rehearsal of the timed steps captures the CUDA graphs they replay
     # (blocks of up to 16 steps) outside the timed region
     s.step(args.steps, graph=True)
     s.sync()
-    stages = STAGES.get(w.scheme, 1)
-    stream = torch.cuda.current_stream(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.2)
     if distributed:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -215,18 +206,95 @@ def run_ours(args):
     if distributed:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
-    # the same steps launched one by one with an event pair around every
-    # solve: the solve kernel's launch durations for the roofline
     s.set_timing(args.steps * stages)
     torch.cuda.synchronize()
     e0.record(stream)
     s.step(args.steps, graph=False)
     e1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
     eager_ms = e0.elapsed_time(e1)
     s.sync()
     solve_ms, solve_launches = s.solve_time()
+    s.set_timing(0)
+    return ms, eager_ms, solve_ms, solve_launches
+
+
+# Steps of the per-field error check (from the seeded initial state, GPU
+# against the FP64 oracle): about 10 s of oracle work per workload size.
+def error_steps(w):
+    return 50 if w.dof <= 1_000_000 else 5
+
+
+def oracle_states(w, xi, nsteps):
+    """The FP64 oracle's state after `nsteps` steps from the seeded initial state."""
+    from oracle import timesteppers as ots
+    if isinstance(w, si.FisherWorkload):
+        from oracle import fisher as ofk
+        sysr = ofk.FisherKPP(w.n_x, w.n_z, w.D, w.R, w.L_x)
+    else:
+        from oracle import rb as orb
+        sysr = orb.RB2D(w.n_x, w.n_z, w.Ra, w.Pr, w.L_x)
+    X = sysr.initial_state(xi)
+    if w.scheme.startswith("RK"):
+        st = ots.RungeKuttaIMEX(sysr, getattr(ots, w.scheme))
+    else:
+        st = ots.SBDF(sysr, int(w.scheme[-1]))
+    for _ in range(nsteps):
+        X = st.step(X, w.dt)
+    return X
+
+
+def field_errors(s, X_ref, xi, nsteps):
+    """Per-field ||x_gpu - x_ref|| / ||x_ref|| (absolute below a reference norm
+    of 1e-30) over the coefficients after `nsteps` steps from `xi`."""
+    s.set_initial_state(xi)
+    s.step(nsteps, graph=True)
+    s.sync()
+    got = s.get_state()
+    out = {}
+    for i, name in enumerate(s.state_order):
+        nr = float(np.linalg.norm(X_ref[i]))
+        d = float(np.linalg.norm(got[i] - X_ref[i]))
+        out[name] = d if nr < 1e-30 else d / nr
+    return out
+
+
+def run_ours(args):
+    import torch
+    distributed = int(os.environ.get("WORLD_SIZE", "1")) > 1
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if distributed:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1905_10388_gb300 import _lib
+    from paper_1905_10388_gb300.solver import Context
+    w = si.WORKLOADS[args.workload]
+    fisher = isinstance(w, si.FisherWorkload)
+    # measured FMA throughput of this GPU: the ALU roofline's denominators
+    fp64_peak = _lib.measure_fma_peak(local, "fp64")
+    fp32_peak = _lib.measure_fma_peak(local, "fp32")
+    ctx = Context(local, torch.cuda.current_stream(local).cuda_stream)
+    stages = STAGES.get(w.scheme, 1)
+    stream = torch.cuda.current_stream(local)
+    # the headline form (FP64 throughout, the paper's arithmetic, unless
+    # --precision picks one) and, by default, the mixed form beside it
+    forms = [args.precision] if args.precision != "both" else ["fp64", "mixed"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    timed = {}
+    solvers = {}
+    for prec in forms:
+        s, xi = _make_solver(ctx, w, prec, rank)
+        timed[prec] = _time_form(s, args, stages, stream, distributed)
+        solvers[prec] = s
+    clk = clocks.stop()
+    head = forms[0]
+    s = solvers[head]
+    ms, eager_ms, solve_ms, solve_launches = timed[head]
     value, secs = job_rate(w.dof * args.steps, ms * 1e-3, world, device="cuda")
     ms = secs * 1e3
 
@@ -247,44 +315,82 @@ def run_ours(args):
     e2e = {"value": e2e_rate, "unit": UNIT,
            "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": s.P * s.Nz * 16}
 
+    # per-field error against the FP64 oracle (outside every timed region)
+    errors = {}
+    err_steps = None
+    if rank == 0 and w.n_y == 1 and not args.no_error:
+        err_steps = error_steps(w)
+        X_ref = oracle_states(w, xi, err_steps)
+        for prec in forms:
+            errors[prec] = field_errors(solvers[prec], X_ref, xi, err_steps)
+
     flops, nbytes = solve_flops_bytes(s)
     n_, kl_, ku_ = s.band()
     # the library's automatic choice of substitution kernel (sp_set_solve_kernel):
-    # assembly, lane substitution and epilogue are three launches
+    # lane substitution (assembly, lanes, epilogue: three launches), the
+    # partitioned substitution (assembly, two forward passes and their
+    # recurrence, two backward passes and theirs, epilogue: eight launches),
+    # or the single window kernel
     lanes = s.P >= 4096 and (kl_, kl_ + ku_) in ((9, 38), (7, 29))
+    nblk = s.spike_blocks()
     factor_mb = s.P * s.solve_work()[1] / 1e6
     achieved = flops / (solve_ms * 1e-3) / 1e12
     peaks = measured_peaks()
-    kernel = "k_pencil_stage<1> + k_pencil_lanes + k_pencil_stage<2>" if lanes else "k_pencil_solve"
-    roof = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": solve_traffic(args.workload, args.precision), "algorithmic_bytes": nbytes,
-            "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (152 SMs x 2 DFMA/cycle x 2.07 GHz)",
+    if lanes:
+        kernel, solve_launches_per = "k_pencil_stage<1> + k_pencil_lanes + k_pencil_stage<2>", 3
+    elif nblk > 0:
+        kernel = (f"partitioned substitution, {nblk} row blocks per pencil: k_pencil_stage_wide<1> + "
+                  "k_spike_fwd<1> + k_spike_fwd_rec + k_spike_fwd<2> + k_spike_bwd<1> + k_spike_bwd_rec + "
+                  "k_spike_bwd<2> + k_pencil_stage_wide<2>")
+        solve_launches_per = 8
+    else:
+        kernel, solve_launches_per = "k_pencil_solve", 1
+    roof = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+            "traffic": solve_traffic(args.workload, head), "algorithmic_bytes": nbytes,
+            "peak_source": "measured: FP64 FMA throughput of this GPU (sp_measure_fma_peak, independent "
+                           "chains on every SM, best of 3); of measured",
             "ms_per_launch": solve_ms, "launches": solve_launches,
             "hbm_achieved_gbs": nbytes / (solve_ms * 1e-3) / 1e9,
-            "hbm_peak_gbs": peaks.get("hbm_gbs")}
+            "hbm_peak_gbs": peaks.get("hbm_gbs"),
+            "hbm_frac": nbytes / (solve_ms * 1e-3) / 1e9 / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+            "measured_peaks_tflops": {"fp64_fma": fp64_peak, "fp32_fma": fp32_peak}}
+    launches = stages * ((5 if w.n_y > 1 else 3) + solve_launches_per) * args.steps
     result = None
     if rank == 0:
+        dtype = {"fp64": "f64", "mixed": "f32+f64"}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "dtype": dtype[head],
             "data": "synthetic (seeded %s initial state)" % ("Fisher-KPP" if fisher else "Rayleigh-Benard"),
             "config": dict({"workload": args.workload, "n_x": w.n_x, "n_y": w.n_y, "n_z": w.n_z},
                            **({"D": w.D, "R": w.R} if fisher else {"Ra": w.Ra, "Pr": w.Pr}),
-                           **{"scheme": w.scheme, "dt": w.dt, "dof": w.dof, "precision": args.precision,
+                           **{"scheme": w.scheme, "dt": w.dt, "dof": w.dof, "precision": head,
                               "parallelism": f"replicas{world}",
                               "l2": (f"working set > L2 (factor {factor_mb:.0f} MB read every solve)"
                                      if factor_mb > 129 else
                                      f"L2-resident (factor {factor_mb:.0f} MB < 129 MB L2; no flush)")}),
+            "error": ({"vs": "FP64 oracle, same seeded initial state", "steps": err_steps,
+                       "norm": "per field ||x_gpu - x_ref||_2 / ||x_ref||_2 over the coefficients",
+                       "fields": errors.get(head), "max": max(errors[head].values())}
+                      if head in errors else None),
             "roofline": roof, "e2e": e2e,
             "timing": {"value": "CUDA-graph replay of the steps (blocks of up to 16), inputs resident",
                        "roofline": "an eager pass of the same steps right after, CUDA events around every solve",
                        "eager_ms_per_step": eager_ms / args.steps},
-            "gpu_launches": stages * ((5 if w.n_y > 1 else 3) + (3 if lanes else 1)) * args.steps,
+            "gpu_launches": launches * len(forms),
             "clocks": clk,
         }
+        for prec in forms[1:]:
+            ms2, eager2, solve2, _ = timed[prec]
+            result[prec] = {
+                "value": w.dof * args.steps / (ms2 * 1e-3), "unit": UNIT, "ms_per_step": ms2 / args.steps,
+                "dtype": dtype[prec], "solve_ms_per_launch": solve2,
+                "over_fp64": (w.dof * args.steps / (ms2 * 1e-3)) / value,
+                "error": ({"steps": err_steps, "fields": errors[prec], "max": max(errors[prec].values())}
+                          if prec in errors else None)}
     ctx.close()
     if distributed:
         torch.distributed.destroy_process_group()
@@ -626,7 +732,9 @@ def main():
     ap.add_argument("--steps", type=int, default=None, help="default 200 (500 for the adjoint workload)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
+                    help="both (default): the FP64 form as the headline and the mixed form beside it")
+    ap.add_argument("--no-error", action="store_true", help="skip the per-field error check against the oracle")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -634,6 +742,12 @@ def main():
         args.steps = 500 if args.workload.endswith("_adjoint") else 200
     if args.warmup < 3:
         args.warmup = 3
+    if args.precision == "both" and args.workload in (
+            "rb2d_batch64_rk222", "rb2d_512x256_rk222_cfl", "rb2d_512x256_onset_evp") or (
+            args.precision == "both" and args.workload.endswith("_adjoint")):
+        # the batched and adjoint workloads are posed in the mixed form
+        # (FP32 transforms and products, FP64 pencils); CFL and EVP lines too
+        args.precision = "mixed"
     if args.impl == "reference":
         res = run_reference(args)
     elif args.workload == "rb2d_batch64_rk222":

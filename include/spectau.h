@@ -72,10 +72,15 @@ typedef struct {
  * factorization serves every stage) of Ascher, Ruuth & Spiteri (1997);
  * SBDF1 .. SBDF4 of Wang & Ruuth (2008), constant step.  SBDFq takes its
  * first q - 1 steps at the orders the history allows (SBDF1, SBDF2, ...)
- * and keeps one factorization per order.  The adjoint entry points support
- * RK222 and RK111; batched stepping all but SBDF3 and SBDF4. */
+ * and keeps one factorization per order.  CNAB1 and CNAB2 (Crank-Nicolson
+ * Adams-Bashforth, the same family and paper; Sec. "Multistep IMEX
+ * integrators"): (M~ + dt/2 L~) X^{n+1} = (M~ - dt/2 L~) X^n
+ * + dt (3/2 F^n - 1/2 F^{n-1}) (CNAB1: dt F^n, CNAB2's first step), one
+ * factorization for both orders.  The adjoint entry points support RK222
+ * and RK111; batched stepping every scheme. */
 typedef enum {
-  SP_RK222 = 0, SP_SBDF1 = 1, SP_SBDF2 = 2, SP_RK111 = 3, SP_RK443 = 4, SP_SBDF3 = 5, SP_SBDF4 = 6
+  SP_RK222 = 0, SP_SBDF1 = 1, SP_SBDF2 = 2, SP_RK111 = 3, SP_RK443 = 4, SP_SBDF3 = 5, SP_SBDF4 = 6,
+  SP_CNAB1 = 7, SP_CNAB2 = 8
 } sp_scheme;
 
 /* FP64: every stage in FP64.  MIXED: transforms and grid products in FP32,
@@ -332,12 +337,41 @@ sp_status sp_set_timing(sp_ctx* ctx, int problem, int max_launches);
  * SP_SOLVE_WINDOW.  WINDOW: one warp per pencil and real/imaginary part,
  * the band across the lanes (latency-bound few-pencil problems).  LANES:
  * one lane per pencil and real/imaginary part (throughput-bound
- * many-pencil problems; SP_ERR_ARG for other band widths).  Must precede
+ * many-pencil problems; SP_ERR_ARG for other band widths).  SPIKE: the
+ * partitioned substitution below (few long pencils; SP_ERR_ARG unless
+ * kl <= 7 and kl + ku <= 31).  Must precede
  * the first call that moves the problem to the device (sp_factor,
  * sp_set_field, sp_transform): SP_ERR_STATE afterwards. */
-typedef enum { SP_SOLVE_AUTO = 0, SP_SOLVE_WINDOW = 1, SP_SOLVE_LANES = 2 } sp_solve_kernel;
+typedef enum { SP_SOLVE_AUTO = 0, SP_SOLVE_WINDOW = 1, SP_SOLVE_LANES = 2, SP_SOLVE_SPIKE = 3 } sp_solve_kernel;
 sp_status sp_set_solve_kernel(sp_ctx* ctx, int problem, int kind);
+
+/* Partitioned substitution (SP_SOLVE_SPIKE; Sec. "Matrix solvers": the
+ * pencil solves are O(n) with the stored factor).  With fewer pencils than
+ * the GPU has dependent-chain slots, each pencil's rows are cut into nblk
+ * blocks of whole 32-row chunks, substituted in parallel: a zero-inflow pass
+ * per block, a recurrence over blocks with coupling matrices computed at
+ * sp_factor (kl x kl forward, (kl+ku) x (kl+ku) backward per block), then a
+ * pass with the true inflows.  Results equal the whole-row-order
+ * substitution to rounding.  SP_SOLVE_AUTO picks it for 2D problems with
+ * fewer than 608 pencils of at least 512 rows when kl <= 7 and kl + ku <= 31.
+ * sp_set_spike_blocks sets nblk (0: automatic, blocks of about 256 rows);
+ * SP_ERR_ARG if the padded rows do not split into nblk whole 32-row chunks,
+ * SP_ERR_STATE once the problem is on the device (like sp_set_solve_kernel).
+ * sp_get_spike_blocks returns the block count in use (0: not partitioned,
+ * or the problem not yet on the device). */
+sp_status sp_set_spike_blocks(sp_ctx* ctx, int problem, int nblk);
+sp_status sp_get_spike_blocks(sp_ctx* ctx, int problem, int* nblk);
 sp_status sp_last_solve_time(sp_ctx* ctx, int problem, double* ms_per_launch, int* launches);
+
+/* Measured fused multiply-add throughput of a device (no paper counterpart;
+ * a measurement utility for the ALU rooflines of the FP64 pencil solves and
+ * the FP32 transforms).  precision 0: FP64, 1: FP32.  Runs a kernel of
+ * independent FMA chains on every SM (about 10 ms, on its own stream, after
+ * one warm-up launch) and writes the best of three launches to *tflops
+ * (2 flops per FMA).  Synchronous; allocates a small sink buffer; changes no
+ * device setting.  SP_ERR_ARG for a bad precision or null output,
+ * SP_ERR_CUDA for a device error. */
+sp_status sp_measure_fma_peak(int device, int precision, double* tflops);
 
 /* Backward transform without any device allocation.  The paper has no
  * counterpart; this entry point is for callers that cannot call cudaMalloc

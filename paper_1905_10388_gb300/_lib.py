@@ -17,15 +17,15 @@ STATUS_NAMES = {0: "SP_OK", -1: "SP_ERR_ARG", -2: "SP_ERR_CUDA", -3: "SP_ERR_OOM
                 -4: "SP_ERR_SINGULAR", -5: "SP_ERR_NOT_FACTORED", -6: "SP_ERR_NONFINITE",
                 -7: "SP_ERR_TIMEOUT", -8: "SP_ERR_STATE"}
 SP_FOURIER, SP_CHEBYSHEV = 0, 1
-SP_RK222, SP_SBDF1, SP_SBDF2, SP_RK111, SP_RK443, SP_SBDF3, SP_SBDF4 = 0, 1, 2, 3, 4, 5, 6
+SP_RK222, SP_SBDF1, SP_SBDF2, SP_RK111, SP_RK443, SP_SBDF3, SP_SBDF4, SP_CNAB1, SP_CNAB2 = range(9)
 SCHEMES = {"RK222": SP_RK222, "SBDF1": SP_SBDF1, "SBDF2": SP_SBDF2, "RK111": SP_RK111, "RK443": SP_RK443,
-           "SBDF3": SP_SBDF3, "SBDF4": SP_SBDF4}
+           "SBDF3": SP_SBDF3, "SBDF4": SP_SBDF4, "CNAB1": SP_CNAB1, "CNAB2": SP_CNAB2}
 # implicit solves per step
 STAGES = {"RK222": 2, "SBDF1": 1, "SBDF2": 1, "RK111": 1, "RK443": 4, "SBDF3": 1, "SBDF4": 1}
 SP_PREC_FP64, SP_PREC_MIXED = 0, 1
 SP_OP_ID, SP_OP_DX, SP_OP_DY = 0, 1, 2
-SP_SOLVE_AUTO, SP_SOLVE_WINDOW, SP_SOLVE_LANES = 0, 1, 2
-SOLVE_KERNELS = {"auto": SP_SOLVE_AUTO, "window": SP_SOLVE_WINDOW, "lanes": SP_SOLVE_LANES}
+SP_SOLVE_AUTO, SP_SOLVE_WINDOW, SP_SOLVE_LANES, SP_SOLVE_SPIKE = 0, 1, 2, 3
+SOLVE_KERNELS = {"auto": SP_SOLVE_AUTO, "window": SP_SOLVE_WINDOW, "lanes": SP_SOLVE_LANES, "spike": SP_SOLVE_SPIKE}
 
 EXPORTS = (
     "sp_create", "sp_destroy", "sp_last_error", "sp_add_problem", "sp_set_layout",
@@ -34,7 +34,8 @@ EXPORTS = (
     "sp_get_band", "sp_set_timing", "sp_last_solve_time", "sp_transform_backward_static",
     "sp_step_batched", "sp_batch_tile", "sp_adjoint_init", "sp_step_adjoint", "sp_transform_adjoint",
     "sp_dz_adjoint", "sp_step_record", "sp_set_solve_kernel", "sp_get_solve_work",
-    "sp_cfl_frequency", "sp_cfl_dt", "sp_eig_target",
+    "sp_cfl_frequency", "sp_cfl_dt", "sp_eig_target", "sp_measure_fma_peak",
+    "sp_set_spike_blocks", "sp_get_spike_blocks",
 )
 
 
@@ -91,7 +92,19 @@ _SIGS = {
     "sp_set_solve_kernel": [P, I, I],
     "sp_transform_adjoint": [P, I, P, P, I, I, I, I, I],
     "sp_dz_adjoint": [P, I, P, P],
+    "sp_measure_fma_peak": [I, I, ctypes.POINTER(D)],
+    "sp_set_spike_blocks": [P, I, I],
+    "sp_get_spike_blocks": [P, I, ctypes.POINTER(I)],
 }
+
+
+def measure_fma_peak(device, precision):
+    """Measured FMA throughput of the device in TFLOP/s (precision 'fp64' or 'fp32')."""
+    out = D()
+    st = lib().sp_measure_fma_peak(int(device), 0 if precision == "fp64" else 1, ctypes.byref(out))
+    if st != SP_OK:
+        raise SpectauError(st, "sp_measure_fma_peak failed")
+    return out.value
 
 
 def lib():

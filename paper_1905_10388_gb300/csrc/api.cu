@@ -4,6 +4,7 @@
 // on the host; every stage is one of the kernels in band.cu / transforms.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -59,16 +60,19 @@ Tableau make_tableau(int scheme) {
 
 bool is_rk(int scheme) { return scheme == SP_RK222 || scheme == SP_RK111 || scheme == SP_RK443; }
 
-// SBDF order of a multistep scheme (0 for the Runge-Kutta schemes)
+// order of a multistep scheme, SBDF or CNAB (0 for the Runge-Kutta schemes)
 int sbdf_order(int scheme) {
   switch (scheme) {
     case SP_SBDF1: return 1;
     case SP_SBDF2: return 2;
     case SP_SBDF3: return 3;
     case SP_SBDF4: return 4;
+    case SP_CNAB1: return 1;
+    case SP_CNAB2: return 2;
     default: return 0;
   }
 }
+bool is_cnab(int scheme) { return scheme == SP_CNAB1 || scheme == SP_CNAB2; }
 // history slots of a multistep scheme (two at least: SBDF1 alternates too)
 int sbdf_depth(int scheme) { return std::max(2, sbdf_order(scheme)); }
 
@@ -85,6 +89,10 @@ const double SBDF_C[5][5] = {{0, 0, 0, 0, 0},
                              {0, 2.0, -1.0, 0, 0},
                              {0, 3.0, -3.0, 1.0, 0},
                              {0, 4.0, -6.0, 4.0, -1.0}};
+// Constant-step CNAB1 / CNAB2 (Wang & Ruuth 2008) multiplied through by dt:
+//   (M + dt/2 L) X^{n+1} = (M - dt/2 L) X^n + dt sum_{j=1..q} c_j F^{n+1-j}
+// (trapezoidal implicit part, Adams-Bashforth weights c)
+const double CNAB_C[3][3] = {{0, 0, 0}, {0, 1.0, 0}, {0, 1.5, -0.5}};
 
 bool is_smooth_length(int N) {  // 2^k or 3 * 2^k
   if (N <= 0) return false;
@@ -167,6 +175,12 @@ struct Problem {
   bool lanes = false;
   int solve_kind = SP_SOLVE_AUTO;
   double2 *d_bg = nullptr, *d_xg = nullptr, *d_yg = nullptr;
+  // partitioned substitution (few pencils): blocks per pencil and the
+  // inflow/outflow vectors of the blocks
+  bool spike = false;
+  int spike_blocks = 0;                      // requested (0: automatic)
+  int nblk = 0, nblk_f = 0;
+  double *d_sp_s0 = nullptr, *d_sp_s = nullptr, *d_sp_o0 = nullptr, *d_sp_u = nullptr;
   std::map<std::pair<int, int>, TransformPlan> plans;
   // stepping state
   int iteration = 0;
@@ -197,7 +211,7 @@ struct sp_ctx {
   std::string err;
   std::vector<std::unique_ptr<Problem>> probs;
   DevStatus* d_status = nullptr;
-  // batches keyed by (problem ids, schedule parity); tile chosen per ids
+  // batches keyed by (problem ids, schedule phase); tile chosen per ids
   std::map<std::pair<std::vector<int>, int>, Batch*> batches;
   std::map<std::vector<int>, int> batch_tile;
 };
@@ -277,6 +291,20 @@ sp_status make_plan(sp_ctx* ctx, Problem* pr, int Nc, int Ng, TransformPlan** ou
   pr->plans[key] = pl;
   *out = &pr->plans[key];
   return SP_OK;
+}
+
+// Blocks per pencil of the partitioned back substitution: about 1024 / P
+// (two to four chains per GPU sub-partition with its two parts; measured at
+// 256 pencils of 1792 rows: 4 blocks 0.224 ms per solve, 7 blocks 0.254, 14
+// blocks 0.253, 28 blocks 0.274, whole pencils 0.289), each a whole number of
+// 32-row chunks and at least 64 rows.
+int default_spike_blocks(int npad, int P) {
+  const int nch = npad / SOLVE_CHUNK;
+  const int target = std::max(2, (1024 + std::max(P, 1) - 1) / std::max(P, 1));
+  int best = 1;
+  for (int nb = 2; nb <= nch / 2; ++nb)
+    if (nch % nb == 0 && std::abs(nb - target) < std::abs(best - target)) best = nb;
+  return best;
 }
 
 sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
@@ -382,7 +410,7 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
   pr->lpad = std::max(2, (pr->kl + 1) / 2 * 2);
   pr->upad = kuu <= 31 ? 32 : 64;
   // SBDFq keeps q factors (its start-up orders); the Runge-Kutta schemes one
-  const int nfactors = std::max(1, sbdf_order(pr->scheme));
+  const int nfactors = is_cnab(pr->scheme) ? 1 : std::max(1, sbdf_order(pr->scheme));
   // thousands of pencils fill the GPU with one lane per right-hand side
   pr->lanes = pr->solve_kind == SP_SOLVE_LANES ||
               (pr->solve_kind == SP_SOLVE_AUTO && pr->P >= LANE_MIN_PENCILS && lanes_supported(pr->kl, kuu));
@@ -391,6 +419,23 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
     CK(dalloc(&pr->d_bg, (size_t)pr->P * pr->n));
     CK(dalloc(&pr->d_xg, (size_t)pr->P * pr->n));
     CK(dalloc(&pr->d_yg, ngroups * LANE_GROUP * pr->n));
+  }
+  // a few hundred pencils are too few chains for the GPU: cut each pencil's
+  // rows into blocks substituted in parallel (spike.cu)
+  pr->nblk = pr->spike_blocks > 0 ? pr->spike_blocks : default_spike_blocks(pr->npad, pr->P);
+  pr->spike = !pr->lanes && spike_supported(pr->kl, kuu, pr->npad, pr->nblk) &&
+              (pr->solve_kind == SP_SOLVE_SPIKE ||
+               (pr->solve_kind == SP_SOLVE_AUTO && pr->P < SPIKE_MAX_PENCILS && pr->npad >= SPIKE_MIN_ROWS));
+  if (pr->spike) {
+    CK(dalloc(&pr->d_bg, (size_t)pr->P * pr->n));
+    CK(dalloc(&pr->d_xg, (size_t)pr->P * pr->n));
+    CK(dalloc(&pr->d_yg, (size_t)pr->P * pr->n));
+    pr->nblk_f = spike_forward_blocks(pr->npad);
+    const size_t nv = (size_t)pr->P * pr->nblk * 2, nvf = (size_t)pr->P * pr->nblk_f * 2;
+    CK(dalloc(&pr->d_sp_s0, nvf * 8));
+    CK(dalloc(&pr->d_sp_s, nvf * 8));
+    CK(dalloc(&pr->d_sp_o0, nv * 32));
+    CK(dalloc(&pr->d_sp_u, nv * 32));
   }
   for (int fi = 0; fi < nfactors; ++fi) {
     BandFactor& f = pr->fac[fi];
@@ -403,6 +448,10 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
     CK(dalloc(&f.piv, (size_t)pr->P * pr->npad));
     CK(dalloc(&f.U, (size_t)pr->P * pr->npad * pr->upad));
     CK(dalloc(&f.rd, (size_t)pr->P * pr->npad));
+    if (pr->spike) {
+      CK(dalloc(&f.spD, (size_t)pr->P * pr->nblk_f * 7 * 8));
+      CK(dalloc(&f.spE, (size_t)pr->P * pr->nblk * kuu * 32));
+    }
   }
   CK(cudaStreamSynchronize(s));
   pr->uploaded = true;
@@ -422,8 +471,9 @@ void free_problem(Problem* pr) {
   for (auto b : pr->d_LX) F(b);
   for (auto b : pr->d_Fc) F(b);
   F(pr->d_gz); F(pr->d_gy); F(pr->d_h);
-  for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); F(f.rd); F(f.Lg); F(f.Ug); F(f.pg); F(f.umask); }
+  for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); F(f.rd); F(f.Lg); F(f.Ug); F(f.pg); F(f.umask); F(f.spD); F(f.spE); }
   F(pr->d_bg); F(pr->d_xg); F(pr->d_yg);
+  F(pr->d_sp_s0); F(pr->d_sp_s); F(pr->d_sp_o0); F(pr->d_sp_u);
   F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd);
   F(pr->d_indptrT); F(pr->d_indicesT); F(pr->d_MvT); F(pr->d_LvT);
   F(pr->d_mu[0]); F(pr->d_mu[1]); F(pr->d_LTmu); F(pr->d_MTmu); F(pr->d_JF); F(pr->d_lamx);
@@ -515,6 +565,8 @@ SolveArgs base_args(Problem* pr, sp_ctx* ctx, int fac) {
   a.Lg = pr->fac[fac].Lg; a.Ug = pr->fac[fac].Ug; a.pg = pr->fac[fac].pg;   // null unless lane mode
   a.cmax = pr->fac[fac].cmax;
   a.umask = pr->fac[fac].umask;
+  a.spD = pr->spike ? pr->fac[fac].spD : nullptr;   // null unless partitioned substitution
+  a.spE = pr->spike ? pr->fac[fac].spE : nullptr;
   return a;
 }
 
@@ -533,19 +585,34 @@ void set_ep_L(Problem* pr, SolveArgs& a) {
 sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
   const bool t = pr->timing && pr->ev_used + 2 <= pr->ev.size();
   if (t) CK(cudaEventRecord(pr->ev[pr->ev_used], s));
-  if (a.Lg && pr->lanes) {
-    // assembly -> lane-per-pencil substitution -> epilogue
+  if ((a.Lg && pr->lanes) || (a.spD && pr->spike)) {
+    // assembly -> lane-per-pencil or partitioned substitution -> epilogue
     SolveArgs a1 = a;
     a1.mode = 1; a1.bg = pr->d_bg;
     CK(launch_pencil_solve(s, a1));
-    CK(launch_pencil_lanes(s, pr->P, pr->n, a.kl, a.kuu, a.Lg, a.Ug, a.cmax, a.pg, a.umask, pr->d_bg, pr->d_yg,
-                           pr->d_xg));
+    if (pr->lanes) {
+      CK(launch_pencil_lanes(s, pr->P, pr->n, a.kl, a.kuu, a.Lg, a.Ug, a.cmax, a.pg, a.umask, pr->d_bg,
+                             pr->d_yg, pr->d_xg));
+    } else {
+      SpikeArgs sa{};
+      sa.P = pr->P; sa.n = pr->n; sa.npad = pr->npad; sa.kl = a.kl; sa.kuu = a.kuu; sa.lpad = a.lpad;
+      sa.upad = a.upad; sa.nblk = pr->nblk; sa.m = pr->npad / pr->nblk;
+      sa.nblk_f = pr->nblk_f; sa.m_f = pr->npad / pr->nblk_f;
+      sa.L = a.Lf; sa.piv = a.piv; sa.U = a.Uf; sa.rd = a.rd; sa.D = a.spD; sa.E = a.spE;
+      sa.bg = pr->d_bg; sa.yg = pr->d_yg; sa.xg = pr->d_xg;
+      sa.s0 = pr->d_sp_s0; sa.sst = pr->d_sp_s; sa.o0 = pr->d_sp_o0; sa.uin = pr->d_sp_u;
+      sa.status = ctx->d_status;
+      CK(launch_spike_solve(s, sa));
+    }
     SolveArgs a2 = a;
     a2.mode = 2; a2.xg = pr->d_xg; a2.bg = pr->d_bg;
     if (a2.ep_mv_vals == pr->d_Lv) {
       // L~ X~ of a stage from its own right-hand side: (B~ - alpha M~ X~) / beta
       // with the factored alpha M~ + beta L~ (compact M~ pattern instead of L~'s)
-      const BandFactor& f = (a.Lg == pr->fac[1].Lg && pr->fac[1].Lg) ? pr->fac[1] : pr->fac[0];
+      int fi = 0;
+      for (int q = 1; q < 4; ++q)
+        if (a.Lf == pr->fac[q].L && pr->fac[q].L) fi = q;
+      const BandFactor& f = pr->fac[fi];
       set_ep_M(pr, a2);
       a2.ep_alpha = f.alpha;
       a2.ep_from_b = 1.0 / f.beta;
@@ -600,6 +667,26 @@ std::vector<StagePlan> plan_step(sp_ctx* ctx, Problem* pr, double dt) {
       }
       plan.push_back(StagePlan{pr->d_Fc[i - 1], a});               // F(X^{i-1}) before stage i
     }
+  } else if (is_cnab(pr->scheme)) {
+    // CNAB1 / CNAB2: M~ X~^n and L~ X~^n evaluated in the prologue (two
+    // matvecs on X~^n: B~ = M~X~^n - dt/2 L~X~^n + dt sum_j c_j F~), the F~
+    // ring as in SBDF (slot it mod 2 holds step it's F~), one factor
+    const int it = pr->iteration, D = sbdf_depth(pr->scheme);
+    const int o = std::min(sbdf_order(pr->scheme), it + 1);
+    const int cur = it % D;
+    SolveArgs a = base_args(pr, ctx, 0);
+    a.mv_x = pr->d_Xt; a.mv_coef = 1.0; a.mv_store = nullptr;
+    set_mv_M(pr, a);
+    a.mv2_vals = pr->d_Lv; a.mv2_coef = -0.5 * dt;
+    a.mv2_indptr = pr->d_indptr; a.mv2_indices = pr->d_indices; a.mv2_nnz = (int)pr->nnz;
+    for (int j = 1; j <= o; ++j) {
+      const int slot = ((it + 1 - j) % D + D) % D;
+      a.fc[a.nfc] = pr->d_Fc[slot]; a.fc_coef[a.nfc++] = dt * CNAB_C[o][j];
+    }
+    a.bc_coef = dt;
+    a.xt_out = pr->d_Xt;
+    a.xc_out = pr->d_Xc;
+    plan.push_back(StagePlan{pr->d_Fc[cur], a});
   } else {
     // SBDF1 .. SBDF4 (Wang & Ruuth 2008), constant step, the first steps at
     // the orders the history allows (SBDF1, SBDF2, ...), with SBDF_A / SBDF_C.
@@ -696,6 +783,7 @@ SolveArgs transposed_args(Problem* pr, sp_ctx* ctx) {
   a.n_nl = 0; a.nbc = 0; a.bc_coef = 0.0;
   a.xc32_out = nullptr;
   a.Lg = nullptr; a.Ug = nullptr; a.pg = nullptr; a.umask = nullptr;
+  a.spD = nullptr; a.spE = nullptr;      // no coupling matrices for the transposed factor
   a.ep_rows = nullptr; a.ep_nrows = 0;   // the transposed patterns carry no row list
   return a;
 }
@@ -800,11 +888,12 @@ sp_status build_batch(sp_ctx* ctx, const std::vector<Problem*>& ps, const std::v
   CK(upload_vec(&b->d_wzf, wzf));
   CK(upload_vec(&b->d_ws, ws));
   // per-stage descriptor tables from the single-problem plans, planned at
-  // the requested schedule parity (multistep schemes alternate buffers)
+  // the requested schedule phase (multistep schemes rotate their buffers)
   std::vector<std::vector<StagePlan>> plans;
   for (Problem* pr : ps) {
     const int saved = pr->iteration;
-    if ((b->scheme == SP_SBDF2 || b->scheme == SP_SBDF1) && (pr->iteration & 1) != parity) pr->iteration += 1;
+    // a steady-state iteration of the requested phase (past the start-up orders)
+    if (sbdf_order(b->scheme) > 0) pr->iteration = sbdf_depth(b->scheme) + parity;
     plans.push_back(plan_step(ctx, pr, pr->fac_dt));
     pr->iteration = saved;
   }
@@ -910,7 +999,7 @@ sp_status sp_add_problem(sp_ctx* ctx, int ndim, const sp_basis* bases, int nvars
   if (bx.kind != SP_FOURIER || bz.kind != SP_CHEBYSHEV || (ndim == 3 && bases[1].kind != SP_FOURIER))
     return fail(ctx, SP_ERR_ARG, "bases must be Fourier axes followed by one Chebyshev axis (last)");
   if (nvars < 1 || nvars > 16) return fail(ctx, SP_ERR_ARG, "nvars must be in [1, 16]");
-  if (scheme < SP_RK222 || scheme > SP_SBDF4) return fail(ctx, SP_ERR_ARG, "unknown scheme %d", scheme);
+  if (scheme < SP_RK222 || scheme > SP_CNAB2) return fail(ctx, SP_ERR_ARG, "unknown scheme %d", scheme);
   if (precision != SP_PREC_FP64 && precision != SP_PREC_MIXED)
     return fail(ctx, SP_ERR_ARG, "unknown precision %d", precision);
   auto pr = std::make_unique<Problem>();
@@ -1110,6 +1199,8 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
   if (is_rk(pr->scheme)) {
     const Tableau tb = make_tableau(pr->scheme);
     ab[0][0] = 1.0; ab[0][1] = dt * tb.H[1][1];   // every stage: H_ii = H_11
+  } else if (is_cnab(pr->scheme)) {
+    ab[0][0] = 1.0; ab[0][1] = 0.5 * dt;         // both orders: M + dt/2 L
   } else {
     // SBDFq: the matrices a_0 M + dt L of the start-up orders 1 .. q
     nf = sbdf_order(pr->scheme);
@@ -1125,6 +1216,11 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
                                        pr->d_indices, pr->d_Mv, pr->d_Lv, ab[f][0], ab[f][1], work, pr->fac[f],
                                        pr->npad, pr->lpad, pr->upad, ctx->d_status);
     if (e != cudaSuccess) { cudaFree(work); CK(e); }
+    if (pr->spike) {
+      e = launch_spike_coupling(ctx->stream, pr->P, pr->npad, pr->nblk_f, pr->nblk, pr->kl, pr->kl + pr->ku,
+                                pr->lpad, pr->upad, pr->fac[f]);
+      if (e != cudaSuccess) { cudaFree(work); CK(e); }
+    }
     if (pr->lanes) {
       // lane layout: the union pattern of U over pencils, then the copy with
       // only the listed entries
@@ -1354,13 +1450,13 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
   for (Problem* pr : ps)
     if (pr->scheme != ps[0]->scheme || pr->prec != ps[0]->prec)
       return fail(ctx, SP_ERR_ARG, "all problems of a batch need the same scheme and precision");
-  if (sbdf_order(ps[0]->scheme) > 2)
-    return fail(ctx, SP_ERR_ARG, "batched stepping supports SBDF1/SBDF2 and the Runge-Kutta schemes");
   CK(cudaSetDevice(ctx->device));
   sp_status st;
-  // eager steps until every problem is in its steady schedule
+  // eager steps until every problem is in its steady schedule (multistep
+  // schemes: past their lower-order start-up steps)
+  const int order = sbdf_order(ps[0]->scheme);
   auto steady = [&](Problem* pr) {
-    return pr->xt_valid && pr->mx_valid && !(pr->scheme == SP_SBDF2 && pr->iteration == 0);
+    return pr->xt_valid && pr->mx_valid && (order == 0 || pr->iteration >= order - 1);
   };
   while (nsteps > 0 && !std::all_of(ps.begin(), ps.end(), steady)) {
     for (Problem* pr : ps)
@@ -1368,10 +1464,13 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
     --nsteps;
   }
   if (nsteps == 0) return SP_OK;
-  const bool multistep = (ps[0]->scheme == SP_SBDF1 || ps[0]->scheme == SP_SBDF2);
+  // multistep schemes rotate their history rings: the buffers a step uses
+  // depend on its phase, iteration mod the ring depth D (one batch per phase)
+  const bool multistep = order > 0;
+  const int D = multistep ? sbdf_depth(ps[0]->scheme) : 1;
   for (Problem* pr : ps)
-    if (multistep && (pr->iteration & 1) != (ps[0]->iteration & 1))
-      return fail(ctx, SP_ERR_STATE, "problems of a batch must be at the same step parity");
+    if (multistep && pr->iteration % D != ps[0]->iteration % D)
+      return fail(ctx, SP_ERR_STATE, "problems of a batch must be at the same step phase (iteration mod %d)", D);
   // tile autotuning of the z-transform kernels (first call for these ids)
   auto get_batch = [&](int parity, int tile) -> Batch* {
     auto key = std::make_pair(ids, parity);
@@ -1390,7 +1489,7 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
     int best = 8;
     float best_ms = 1e30f;
     for (int tile : {4, 8, 16}) {
-      Batch* b = get_batch(multistep ? (ps[0]->iteration & 1) : 0, tile);
+      Batch* b = get_batch(multistep ? ps[0]->iteration % D : 0, tile);
       if (!b) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
       // the transform kernels write only scratch buffers that the next step overwrites
       const BatchStage& sg = b->stages[0];
@@ -1413,7 +1512,7 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
   }
   const int tile = ctx->batch_tile[ids];
   while (nsteps > 0) {
-    const int parity = multistep ? (ps[0]->iteration & 1) : 0;
+    const int parity = multistep ? ps[0]->iteration % D : 0;
     Batch* b = get_batch(parity, tile);
     if (!b) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
     if (!use_graph) {
@@ -1422,17 +1521,20 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
       --nsteps;
       continue;
     }
-    // a graph of `block` steps starting at this parity (parities alternate)
+    // a graph of `block` steps starting at this phase (phases cycle mod D)
     const int block = std::min(nsteps, 16);
     auto git = b->graphs.find(block);
     cudaGraphExec_t exec = nullptr;
     if (git == b->graphs.end()) {
-      Batch* other = multistep ? get_batch(parity ^ 1, tile) : b;
-      if (!other) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
+      std::vector<Batch*> phase_batch(D, nullptr);
+      for (int q = 0; q < D; ++q) {
+        phase_batch[q] = q == parity ? b : get_batch(q, tile);
+        if (!phase_batch[q]) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
+      }
       cudaGraph_t g;
       CK(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
       st = SP_OK;
-      for (int k = 0; k < block && st == SP_OK; ++k) st = batch_step(ctx, (k & 1) ? other : b, ctx->capture);
+      for (int k = 0; k < block && st == SP_OK; ++k) st = batch_step(ctx, phase_batch[(parity + k) % D], ctx->capture);
       cudaError_t e = cudaStreamEndCapture(ctx->capture, &g);
       if (st != SP_OK) return st;
       CK(e);
@@ -1988,13 +2090,44 @@ sp_status sp_set_solve_kernel(sp_ctx* ctx, int problem, int kind) {
   Problem* pr = get(ctx, problem);
   if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
   ctx->err.clear();
-  if (kind != SP_SOLVE_AUTO && kind != SP_SOLVE_WINDOW && kind != SP_SOLVE_LANES)
+  if (kind != SP_SOLVE_AUTO && kind != SP_SOLVE_WINDOW && kind != SP_SOLVE_LANES && kind != SP_SOLVE_SPIKE)
     return fail(ctx, SP_ERR_ARG, "unknown solve kernel %d", kind);
   if (pr->uploaded) return fail(ctx, SP_ERR_STATE, "the solve kernel is fixed once the problem is on the device");
   if (kind == SP_SOLVE_LANES && (pr->nnz < 0 || !lanes_supported(pr->kl, pr->kl + pr->ku)))
     return fail(ctx, SP_ERR_ARG, "no lane-per-pencil substitution for kl = %d, kl + ku = %d (set the pencils first)",
                 pr->kl, pr->kl + pr->ku);
+  if (kind == SP_SOLVE_SPIKE) {
+    const int npad = (pr->n + SOLVE_CHUNK - 1) / SOLVE_CHUNK * SOLVE_CHUNK;
+    const int nblk = pr->spike_blocks > 0 ? pr->spike_blocks : default_spike_blocks(npad, pr->P);
+    if (pr->nnz < 0 || !spike_supported(pr->kl, pr->kl + pr->ku, npad, nblk))
+      return fail(ctx, SP_ERR_ARG, "no partitioned substitution for kl = %d, kl + ku = %d, %d rows in %d blocks "
+                  "(needs kl <= 7, kl + ku <= 31, whole 32-row chunks per block; set the pencils first)",
+                  pr->kl, pr->kl + pr->ku, npad, nblk);
+  }
   pr->solve_kind = kind;
+  return SP_OK;
+}
+
+sp_status sp_set_spike_blocks(sp_ctx* ctx, int problem, int nblk) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (pr->uploaded) return fail(ctx, SP_ERR_STATE, "the block count is fixed once the problem is on the device");
+  if (nblk < 0) return fail(ctx, SP_ERR_ARG, "nblk must be >= 0");
+  if (nblk > 0 && pr->nnz >= 0) {
+    const int npad = (pr->n + SOLVE_CHUNK - 1) / SOLVE_CHUNK * SOLVE_CHUNK;
+    if (npad % (nblk * SOLVE_CHUNK))
+      return fail(ctx, SP_ERR_ARG, "%d rows do not split into %d blocks of whole 32-row chunks", npad, nblk);
+  }
+  pr->spike_blocks = nblk;
+  return SP_OK;
+}
+
+sp_status sp_get_spike_blocks(sp_ctx* ctx, int problem, int* nblk) {
+  Problem* pr = get(ctx, problem);
+  if (!pr || !nblk) return fail(ctx, SP_ERR_ARG, "bad context, problem id or output");
+  ctx->err.clear();
+  *nblk = (pr->uploaded && pr->spike) ? pr->nblk : 0;
   return SP_OK;
 }
 

@@ -23,6 +23,7 @@
 #include <cstdio>
 
 #include "internal.h"
+#include "tma.cuh"
 
 namespace spectau {
 
@@ -177,50 +178,6 @@ cudaError_t launch_band_factor(cudaStream_t s, int P, int n, int nnz, int kl, in
                                                            alpha, beta, work, f.L, f.piv, f.U, f.rd, npad,
                                                            lpad, upad, st);
   return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// TMA bulk copy + mbarrier helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// A bulk copy that has not landed after ~1 s of SM clock (2^31 cycles at
-// ~2 GHz) is declared lost.
-constexpr long long WAIT_CYCLES = 1ll << 31;
-
-__device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t phase) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, phase))
-    if (clock64() - t0 > WAIT_CYCLES) return false;
-  return true;
 }
 
 __device__ __forceinline__ double2 shfl2(double2 v, int src) {
@@ -398,6 +355,18 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
       if (a.mv_store != nullptr) a.mv_store[prow + r] = s;
       acc.x = fma(a.mv_coef, s.x, acc.x);
       acc.y = fma(a.mv_coef, s.y, acc.y);
+    }
+    if (a.mv2_vals != nullptr) {                 // a second matrix on the same vector (CNAB: L~ X~^n)
+      double2 s = make_double2(0.0, 0.0);
+      const double* vals = a.mv2_vals + (size_t)p * a.mv2_nnz;
+      for (int e = a.mv2_indptr[r]; e < a.mv2_indptr[r + 1]; ++e) {
+        const double m = vals[e];
+        const double2 x = a.mv_x[prow + a.mv2_indices[e]];
+        s.x = fma(m, x.x, s.x);
+        s.y = fma(m, x.y, s.y);
+      }
+      acc.x = fma(a.mv2_coef, s.x, acc.x);
+      acc.y = fma(a.mv2_coef, s.y, acc.y);
     }
     sm.B[r] = acc;
   }
@@ -653,6 +622,14 @@ __global__ void __launch_bounds__(128, 6) k_pencil_stage(SolveArgs a) {
   pencil_solve_body<1, 1, MODE>(a, blockIdx.x, smem_raw);
 }
 
+// the same with 512-thread CTAs, for problems with few pencils (one CTA
+// per pencil would leave most of the GPU idle at 128 threads)
+template <int MODE>
+__global__ void __launch_bounds__(512, 2) k_pencil_stage_wide(SolveArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  pencil_solve_body<1, 1, MODE, 512>(a, blockIdx.x, smem_raw);
+}
+
 // a batch of problems: work item (problem, pencil) per CTA
 template <int RU>
 __global__ void __launch_bounds__(128, 1) k_pencil_solve_batched(const SolveArgs* __restrict__ args,
@@ -683,6 +660,16 @@ cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& args) {
   if (a.mode == 1 || a.mode == 2) {
     const size_t smem = solve_smem_bytes(a.npad, 0, 0);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    if (a.P < 2 * 152) {
+      if (a.mode == 1) {
+        cudaFuncSetAttribute(k_pencil_stage_wide<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_pencil_stage_wide<1><<<a.P, 512, smem, s>>>(a);
+      } else {
+        cudaFuncSetAttribute(k_pencil_stage_wide<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_pencil_stage_wide<2><<<a.P, 512, smem, s>>>(a);
+      }
+      return cudaGetLastError();
+    }
     if (a.mode == 1) {
       cudaFuncSetAttribute(k_pencil_stage<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_pencil_stage<1><<<a.P, 128, smem, s>>>(a);

@@ -30,7 +30,40 @@ struct BandFactor {
   double u_listed = 0;          // mean listed entries per column, the diagonal excluded
   uint8_t* pg = nullptr;        // [G][n][16]
   unsigned long long* umask = nullptr;   // [n] bit t: U_{j-t,j} != 0 in some pencil (bit 0 set)
+  // partitioned substitution (spike.cu): coupling matrices of the row blocks
+  double* spD = nullptr;        // [P][nblk_f][7][8]   forward window after a block from the window before
+  double* spE = nullptr;        // [P][nblk][kuu][32]  back-substitution outflow from the inflow
 };
+
+// Partitioned substitution of problems with few pencils (spike.cu).
+struct SpikeArgs {
+  int P, n, npad, kl, kuu, lpad, upad;
+  int nblk, m;                  // back-substitution blocks per pencil and their rows
+  int nblk_f, m_f;              // forward-substitution blocks and rows (multiples of 8)
+  const double* L; const uint8_t* piv; const double* U; const double* rd;
+  const double* D; const double* E;
+  const double2* bg;            // B~ [p][n]
+  double2* yg;                  // y = L^-1 P B~ [p][n]
+  double2* xg;                  // x~ = y / U_jj [p][n] (the epilogue's input)
+  double* s0; double* sst;      // forward outflows / inflows [p][nblk_f][2][8]
+  double* o0; double* uin;      // backward outflows / inflows [p][nblk][2][32]
+  DevStatus* status;
+};
+// Problems with fewer pencils than this (and kl <= 7, kl + ku <= 31, at
+// least SPIKE_MIN_ROWS rows) use the partitioned substitution by default.
+constexpr int SPIKE_MAX_PENCILS = 608;
+constexpr int SPIKE_MIN_ROWS = 512;
+bool spike_supported(int kl, int kuu, int npad, int nblk);
+cudaError_t launch_spike_coupling(cudaStream_t s, int P, int npad, int nblk_f, int nblk, int kl, int kuu, int lpad,
+                                  int upad, const BandFactor& f);
+// forward blocks of the partitioned substitution: 128 rows, or 64 or 32 when
+// those divide the padded rows
+inline int spike_forward_blocks(int npad) {
+  for (int m = 128; m >= 32; m /= 2)
+    if (npad % m == 0) return npad / m;
+  return 1;
+}
+cudaError_t launch_spike_solve(cudaStream_t s, const SpikeArgs& a);
 
 // Pencils per warp in the lane-per-pencil substitution (two lanes each:
 // real and imaginary part).
@@ -74,6 +107,9 @@ struct SolveArgs {
   int nvec; const double2* vec[SP_MAX_TERMS]; double vec_coef[SP_MAX_TERMS];
   const double2* mv_x; const double* mv_vals; double mv_coef; double2* mv_store;
   const int32_t* mv_indptr; const int32_t* mv_indices; int mv_nnz;   // pattern of mv_vals
+  // + mv2_coef (Mat2 x) on the same x (null mv2_vals: none)
+  const double* mv2_vals; double mv2_coef;
+  const int32_t* mv2_indptr; const int32_t* mv2_indices; int mv2_nnz;
   int nfc; const double2* fc[SP_MAX_TERMS]; double fc_coef[SP_MAX_TERMS];
   // fc_coef / 2 and -fc_coef / 2 for the T-to-U rows, filled by the launcher
   double fc_half[SP_MAX_TERMS], fc_mhalf[SP_MAX_TERMS];
@@ -102,6 +138,8 @@ struct SolveArgs {
   double ep_from_b, ep_alpha;
   // factor in the lane-interleaved layout (null: not available)
   const double* Lg; const double* Ug; const uint8_t* pg; const unsigned long long* umask; int cmax;
+  // coupling matrices of the partitioned substitution (null: not available)
+  const double* spD; const double* spE;
 };
 
 // fc_half / fc_mhalf from fc_coef (exact scalings), before a launch

@@ -107,9 +107,21 @@ class TauSolver:
         self.dt = None
 
     def set_solve_kernel(self, kind):
-        """'auto', 'window' or 'lanes' (before the problem moves to the device)."""
+        """'auto', 'window', 'lanes' or 'spike' (before the problem moves to the device)."""
         h = self.ctx.handle
         L.check(h, L.lib().sp_set_solve_kernel(h, self.pid, L.SOLVE_KERNELS[kind]))
+
+    def set_spike_blocks(self, nblk):
+        """Row blocks per pencil of the partitioned substitution (0: automatic)."""
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_set_spike_blocks(h, self.pid, int(nblk)))
+
+    def spike_blocks(self):
+        """Row blocks per pencil in use (0: the substitution is not partitioned)."""
+        out = ctypes.c_int()
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_get_spike_blocks(h, self.pid, ctypes.byref(out)))
+        return out.value
 
     def set_bilinear(self, terms):
         ops = {"ID": L.SP_OP_ID, "DX": L.SP_OP_DX, "DY": L.SP_OP_DY}

@@ -1,4 +1,7 @@
 """Shared helpers for the GPU tests (no method arithmetic here)."""
+import json
+import os
+
 import numpy as np
 
 
@@ -39,9 +42,27 @@ def oracle_floor(make_system, X0_fn, step_fn, nsteps):
     return ref, floor
 
 
-def check_fields(got, ref, floor, bar):
-    errs = field_errors(got, ref, NAMES)
-    bad = {v: (errs[v], max(bar, 10 * floor[v])) for v in errs if errs[v] >= max(bar, 10 * floor[v])}
+def record(label, field, err, floor, bar):
+    """Print one parity figure and append it (JSON line) to the file named by
+    SPECTAU_PARITY_LOG when that is set: the measured error, the oracle
+    variants' floor, and the bar the test applied."""
+    line = {"test": label, "field": field, "err": float(err),
+            "floor": None if floor is None else float(floor), "bar": float(bar)}
+    print("parity", json.dumps(line))
+    out = os.environ.get("SPECTAU_PARITY_LOG")
+    if out:
+        with open(out, "a") as f:
+            f.write(json.dumps(line) + "\n")
+
+
+def check_fields(got, ref, floor, bar, label=None, names=None):
+    names = names or NAMES
+    errs = field_errors(got, ref, names)
+    tol = {v: max(bar, 10 * floor[v]) for v in errs}
+    if label:
+        for v in errs:
+            record(label, v, errs[v], floor[v], tol[v])
+    bad = {v: (errs[v], tol[v]) for v in errs if errs[v] >= tol[v]}
     assert not bad, {"errors": errs, "floor": floor, "failing (err, tol)": bad}
 
 

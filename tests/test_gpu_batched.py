@@ -48,14 +48,20 @@ def test_batch_equals_individual_steps(scheme, prec, graph):
     ctx.close()
 
 
-def test_batch_rejects_sbdf3():
-    """Batched stepping keeps two history slots per problem: SBDF3 and SBDF4
-    are refused with SP_ERR_ARG rather than stepped wrongly."""
-    from paper_1905_10388_gb300 import _lib as L
+@pytest.mark.parametrize("scheme", ["SBDF3", "SBDF4", "CNAB2"])
+def test_batch_multistep_phases_equal_individual_steps(scheme):
+    """Multistep schemes rotate history rings of depth D (SBDF3: 3, SBDF4: 4,
+    CNAB2: 2): the batch keeps one set of launch tables per phase and must
+    still equal the problems stepped alone, bit for bit."""
     ctx = Context(0)
-    solvers = _make(ctx, "SBDF3", "fp64")[:2]
-    with pytest.raises(L.SpectauError):
-        step_batched(solvers, 3, graph=False)
+    solo = _make(ctx, scheme, "fp64")
+    for s in solo:
+        s.step(11)
+    batch = _make(ctx, scheme, "fp64")
+    step_batched(batch, 11, graph=True)
+    ctx.sync_status()
+    for a, b in zip(solo, batch):
+        assert np.array_equal(a.get_state(), b.get_state())
     ctx.close()
 
 
@@ -77,7 +83,7 @@ def test_batch_sample_against_oracle():
             return st
         ref, floor = oracle_floor(lambda m, lu: orb.RB2D(nx, nz, ra, cheb_method=m, lu_method=lu),
                                   lambda sysr: sysr.initial_state(si.rb_noise(1000 + i, nz, nx)), stepper, 4)
-        check_fields(batch[i].get_state(), ref, floor, 1e-12)
+        check_fields(batch[i].get_state(), ref, floor, 1e-12, label=f"batch_sample_{nx}x{nz}_rk222_fp64_4steps")
     ctx.close()
 
 
