@@ -360,6 +360,21 @@ sp_status sp_set_solve_kernel(sp_ctx* ctx, int problem, int kind);
  * sp_get_spike_blocks returns the block count in use (0: not partitioned,
  * or the problem not yet on the device). */
 sp_status sp_set_spike_blocks(sp_ctx* ctx, int problem, int nblk);
+
+/* Chebyshev backward transform of the mixed form (Sec. "Chebyshev basis":
+ * g_i = sum_n c_n T_n(x_i)): SP_ZT_FFT, the DCT through a shared-memory FFT
+ * in FP32; SP_ZT_MMA, the dense product with the matrix T_n(x_i) on the
+ * tensor cores (tcgen05.mma kind::tf32, each operand split into a TF32 head
+ * and remainder, three products accumulated in FP32; operands staged by
+ * TMA), for N_z a multiple of 32 and N_gz a multiple of 16 up to 256;
+ * SP_ZT_AUTO: MMA on three-dimensional mixed problems where it fits, else
+ * FFT.  FP64 problems always use the FFT.  SP_ERR_ARG for MMA on sizes or a
+ * precision it does not take, SP_ERR_STATE once the problem is on the
+ * device.  sp_get_z_transform returns the requested kind before, and the
+ * kind in use after, the problem moves to the device. */
+typedef enum { SP_ZT_AUTO = 0, SP_ZT_FFT = 1, SP_ZT_MMA = 2 } sp_z_transform;
+sp_status sp_set_z_transform(sp_ctx* ctx, int problem, int kind);
+sp_status sp_get_z_transform(sp_ctx* ctx, int problem, int* kind);
 sp_status sp_get_spike_blocks(sp_ctx* ctx, int problem, int* nblk);
 sp_status sp_last_solve_time(sp_ctx* ctx, int problem, double* ms_per_launch, int* launches);
 

@@ -35,7 +35,7 @@ EXPORTS = (
     "sp_step_batched", "sp_batch_tile", "sp_adjoint_init", "sp_step_adjoint", "sp_transform_adjoint",
     "sp_dz_adjoint", "sp_step_record", "sp_set_solve_kernel", "sp_get_solve_work",
     "sp_cfl_frequency", "sp_cfl_dt", "sp_eig_target", "sp_measure_fma_peak",
-    "sp_set_spike_blocks", "sp_get_spike_blocks",
+    "sp_set_spike_blocks", "sp_get_spike_blocks", "sp_set_z_transform", "sp_get_z_transform",
 )
 
 
@@ -95,7 +95,10 @@ _SIGS = {
     "sp_measure_fma_peak": [I, I, ctypes.POINTER(D)],
     "sp_set_spike_blocks": [P, I, I],
     "sp_get_spike_blocks": [P, I, ctypes.POINTER(I)],
+    "sp_set_z_transform": [P, I, I],
+    "sp_get_z_transform": [P, I, ctypes.POINTER(I)],
 }
+Z_TRANSFORMS = {"auto": 0, "fft": 1, "mma": 2}
 
 
 def measure_fma_peak(device, precision):

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libspectau.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "band.cu", "spike.cu", "transforms.cu", "static_transform.cu", "peak.cu"]
+SOURCES = ["api.cu", "band.cu", "spike.cu", "chebmma.cu", "transforms.cu", "static_transform.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -153,6 +153,11 @@ struct Problem {
   float* d_kx32 = nullptr;
   float* d_tcoef32 = nullptr;
   bool xc32_valid = false;
+  // Chebyshev backward transform on the tensor cores (mixed precision)
+  int zkind = SP_ZT_AUTO;
+  bool zmma = false;
+  bool xs32_valid = false;
+  ChebMMA cm;
   // CFL frequency scratch (sp_cfl_frequency), allocated on first use
   double* d_cfl_grid = nullptr;
   void *d_cfl_mid1 = nullptr, *d_cfl_mid2 = nullptr;
@@ -420,6 +425,18 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
     CK(dalloc(&pr->d_xg, (size_t)pr->P * pr->n));
     CK(dalloc(&pr->d_yg, ngroups * LANE_GROUP * pr->n));
   }
+  // mixed precision: the Chebyshev backward transform on the tensor cores
+  // (SP_ZT_MMA, or SP_ZT_AUTO on three-dimensional problems), when its sizes fit
+  pr->zmma = pr->prec == SP_PREC_MIXED && cheb_mma_supported(pr->Nz, pr->Ngz) &&
+             (pr->zkind == SP_ZT_MMA || (pr->zkind == SP_ZT_AUTO && pr->ndim == 3));
+  if (pr->zmma) {
+    cudaError_t e = cheb_mma_setup(pr->cm, pr->P, pr->Nz, pr->Ngz, pr->S, s);
+    if (e != cudaSuccess) {
+      cheb_mma_free(pr->cm);
+      pr->zmma = false;
+      if (pr->zkind == SP_ZT_MMA) CK(e);
+    }
+  }
   // a few hundred pencils are too few chains for the GPU: cut each pencil's
   // rows into blocks substituted in parallel (spike.cu)
   pr->nblk = pr->spike_blocks > 0 ? pr->spike_blocks : default_spike_blocks(pr->npad, pr->P);
@@ -474,6 +491,7 @@ void free_problem(Problem* pr) {
   for (auto& f : pr->fac) { F(f.L); F(f.piv); F(f.U); F(f.rd); F(f.Lg); F(f.Ug); F(f.pg); F(f.umask); F(f.spD); F(f.spE); }
   F(pr->d_bg); F(pr->d_xg); F(pr->d_yg);
   F(pr->d_sp_s0); F(pr->d_sp_s); F(pr->d_sp_o0); F(pr->d_sp_u);
+  cheb_mma_free(pr->cm);
   F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd);
   F(pr->d_indptrT); F(pr->d_indicesT); F(pr->d_MvT); F(pr->d_LvT);
   F(pr->d_mu[0]); F(pr->d_mu[1]); F(pr->d_LTmu); F(pr->d_MTmu); F(pr->d_JF); F(pr->d_lamx);
@@ -530,8 +548,19 @@ sp_status eval_rhs(sp_ctx* ctx, Problem* pr, cudaStream_t s, double2* fc_out) {
     CK(launch_to_f32(s, pr->d_Xc, pr->d_Xc32, (size_t)pr->S * pr->P * pr->Nz));
     pr->xc32_valid = true;
   }
-  CK(launch_cheb_backward(s, pr->prec, pz, pr->P, nf, pr->d_gvar, pr->d_gop, pr->d_kx, pr->d_Xc,
-                          pr->P * pr->Nz, pr->d_gz, pr->d_kx32, pr->d_Xc32));
+  if (pr->zmma) {
+    // z backward on the tensor cores from the split FP32 copy
+    if (!pr->xs32_valid) {
+      CK(launch_to_f32_split(s, pr->d_Xc, pr->cm.xs32, (size_t)pr->S * pr->P, pr->Nz));
+      pr->xs32_valid = true;
+    }
+    std::vector<int> fv(nf), fo(nf);
+    for (int f = 0; f < nf; ++f) { fv[f] = pr->gfields[f].var; fo[f] = pr->gfields[f].op; }
+    CK(launch_cheb_backward_mma(s, pr->cm, nf, fv.data(), fo.data(), pr->d_kx32, pr->d_gz, ctx->d_status));
+  } else {
+    CK(launch_cheb_backward(s, pr->prec, pz, pr->P, nf, pr->d_gvar, pr->d_gop, pr->d_kx, pr->d_Xc,
+                            pr->P * pr->Nz, pr->d_gz, pr->d_kx32, pr->d_Xc32));
+  }
   if (pr->ndim == 3) {
     TransformPlan& py = pr->plans.at({pr->Ny, pr->Ngy});
     CK(launch_fourier_y(s, pr->prec, py, -1, nf, pr->Ngz, pr->K, pr->d_gz, pr->d_gy));
@@ -562,6 +591,7 @@ SolveArgs base_args(Problem* pr, sp_ctx* ctx, int fac) {
   a.bc_rows = pr->d_bc_rows; a.bc_values = pr->d_bc_values;
   a.status = ctx->d_status;
   a.xc32_out = pr->d_Xc32;   // null unless mixed precision
+  a.xs32_out = pr->zmma ? pr->cm.xs32 : nullptr;
   a.Lg = pr->fac[fac].Lg; a.Ug = pr->fac[fac].Ug; a.pg = pr->fac[fac].pg;   // null unless lane mode
   a.cmax = pr->fac[fac].cmax;
   a.umask = pr->fac[fac].umask;
@@ -782,6 +812,7 @@ SolveArgs transposed_args(Problem* pr, sp_ctx* ctx) {
   a.Lf = pr->facT.L; a.piv = pr->facT.piv; a.Uf = pr->facT.U; a.rd = pr->facT.rd;
   a.n_nl = 0; a.nbc = 0; a.bc_coef = 0.0;
   a.xc32_out = nullptr;
+  a.xs32_out = nullptr;
   a.Lg = nullptr; a.Ug = nullptr; a.pg = nullptr; a.umask = nullptr;
   a.spD = nullptr; a.spE = nullptr;      // no coupling matrices for the transposed factor
   a.ep_rows = nullptr; a.ep_nrows = 0;   // the transposed patterns carry no row list
@@ -801,6 +832,7 @@ sp_status adjoint_rhs(sp_ctx* ctx, Problem* pr, cudaStream_t s, const double2* x
   if (pr->prec) {
     CK(launch_to_f32(s, xc, pr->d_Xc32, (size_t)pr->S * pr->P * pr->Nz));
     pr->xc32_valid = (xc == pr->d_Xc);
+    pr->xs32_valid = false;
   }
   CK(launch_adj_gather(s, pr->P, pr->Nz, pr->Ngz, pr->n, ne, pr->d_nl_eq, pr->d_row_map, pr->d_eq_diff,
                        pr->d_eq_ph, nv, vecs, coefs, pr->d_Fbar, pr->prec ? pr->d_Fbar32 : nullptr));
@@ -1307,6 +1339,7 @@ sp_status sp_set_field(sp_ctx* ctx, int problem, int var, const void* data, int 
   pr->xt_valid = false;
   pr->mx_valid = false;
   pr->xc32_valid = false;
+  pr->xs32_valid = false;
   pr->iteration = 0;
   return SP_OK;
 }
@@ -1362,6 +1395,7 @@ sp_status sp_dz(sp_ctx* ctx, int problem, int src_var, int dst_var) {
   CK(launch_dz(ctx->stream, pr->P, pr->Nz, 2.0 / (pr->zb - pr->za), pr->d_Xc + src_var * f, pr->d_Xc + dst_var * f));
   pr->xt_valid = false;
   pr->xc32_valid = false;
+  pr->xs32_valid = false;
   pr->mx_valid = false;
   pr->iteration = 0;
   return SP_OK;
@@ -1656,6 +1690,7 @@ sp_status sp_step_adjoint(sp_ctx* ctx, int problem, double dt, const void* state
   // the problem's state buffers are scratch from here on
   pr->xt_valid = false;
   pr->xc32_valid = false;
+  pr->xs32_valid = false;
   pr->mx_valid = false;
   pr->iteration = 0;
   if (tb.s == 2 && nstates == 2) {
@@ -2105,6 +2140,31 @@ sp_status sp_set_solve_kernel(sp_ctx* ctx, int problem, int kind) {
                   pr->kl, pr->kl + pr->ku, npad, nblk);
   }
   pr->solve_kind = kind;
+  return SP_OK;
+}
+
+sp_status sp_set_z_transform(sp_ctx* ctx, int problem, int kind) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (kind != SP_ZT_AUTO && kind != SP_ZT_FFT && kind != SP_ZT_MMA)
+    return fail(ctx, SP_ERR_ARG, "unknown z transform %d", kind);
+  if (pr->uploaded) return fail(ctx, SP_ERR_STATE, "the z transform is fixed once the problem is on the device");
+  if (kind == SP_ZT_MMA) {
+    const int ngz = pr->bz.n_coeff * pr->bz.dealias_num / std::max(1, pr->bz.dealias_den);
+    if (pr->prec != SP_PREC_MIXED || !cheb_mma_supported(pr->bz.n_coeff, ngz))
+      return fail(ctx, SP_ERR_ARG, "the tensor-core z transform needs mixed precision, N_z a multiple of 32 and "
+                  "N_gz a multiple of 16 up to 256 (N_z = %d, N_gz = %d)", pr->bz.n_coeff, ngz);
+  }
+  pr->zkind = kind;
+  return SP_OK;
+}
+
+sp_status sp_get_z_transform(sp_ctx* ctx, int problem, int* kind) {
+  Problem* pr = get(ctx, problem);
+  if (!pr || !kind) return fail(ctx, SP_ERR_ARG, "bad context, problem id or output");
+  ctx->err.clear();
+  *kind = !pr->uploaded ? pr->zkind : (pr->zmma ? SP_ZT_MMA : SP_ZT_FFT);
   return SP_OK;
 }
 

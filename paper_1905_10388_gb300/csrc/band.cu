@@ -550,6 +550,10 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
       const double2 xv = cipow_d(x, a.var_phase[v]);
       a.xc_out[((size_t)v * a.P + p) * Nz + m] = xv;
       if (a.xc32_out) a.xc32_out[((size_t)v * a.P + p) * Nz + m] = make_float2((float)xv.x, (float)xv.y);
+      if (a.xs32_out) {
+        a.xs32_out[(((size_t)v * a.P + p) * 2) * Nz + m] = (float)xv.x;
+        a.xs32_out[(((size_t)v * a.P + p) * 2 + 1) * Nz + m] = (float)xv.y;
+      }
     }
   }
   if (a.ep_mv_vals) {

@@ -72,6 +72,28 @@ constexpr int LANE_GROUP = 16;
 // substitution (2 P lanes = P / 16 warps: several per SM).
 constexpr int LANE_MIN_PENCILS = 4096;
 
+// Chebyshev backward transform on the tensor cores (chebmma.cu): the split
+// FP32 copy of the coefficients it reads, the transform matrix halves, and
+// the TMA tensor maps (opaque CUtensorMap storage, 64-byte aligned).
+struct ChebMMA {
+  bool ready = false;
+  int P = 0, Nz = 0, Ng = 0, S = 0;
+  float* xs32 = nullptr;        // [S][2P][Nz]: real part (column 2p) and imaginary part (2p + 1)
+  float* Thi = nullptr;         // [Ng][Nz] T_m(x_zg) truncated to TF32
+  float* Tlo = nullptr;         // [Ng][Nz] the FP32 remainder
+  alignas(64) unsigned char tmA[128];
+  alignas(64) unsigned char tmThi[128];
+  alignas(64) unsigned char tmTlo[128];
+};
+bool cheb_mma_supported(int Nz, int Ng);
+cudaError_t cheb_mma_setup(ChebMMA& c, int P, int Nz, int Ng, int S, cudaStream_t s);
+void cheb_mma_free(ChebMMA& c);
+// grid fields f (variable f_var[f], operator f_op[f]; host arrays) of the
+// FP32 coefficients in c.xs32 to gz [f][Ng][P] complex FP32
+cudaError_t launch_cheb_backward_mma(cudaStream_t s, const ChebMMA& c, int nf, const int* f_var, const int* f_op,
+                                     const float* kx32, void* gz, DevStatus* st);
+cudaError_t launch_to_f32_split(cudaStream_t s, const double2* src, float* dst, size_t ncols, int Nz);
+
 // Up to four device vectors with coefficients, passed to kernels by value.
 struct VecList4 {
   const double2* p[4];
@@ -116,6 +138,7 @@ struct SolveArgs {
   double bc_coef;
   // epilogue
   double2* xt_out; double2* xc_out; float2* xc32_out;   // xc32_out: FP32 copy (mixed precision)
+  float* xs32_out;                             // split FP32 copy [var][2p + c][m] (tensor-core z transform)
   const double* ep_mv_vals; double2* ep_mv_store;
   const double2* ep_mv_addvec;                 // epilogue matvec acts on (X~ + addvec) if set
   const int32_t* ep_indptr; const int32_t* ep_indices; int ep_nnz;    // pattern of ep_mv_vals

@@ -111,6 +111,18 @@ class TauSolver:
         h = self.ctx.handle
         L.check(h, L.lib().sp_set_solve_kernel(h, self.pid, L.SOLVE_KERNELS[kind]))
 
+    def set_z_transform(self, kind):
+        """'auto', 'fft' or 'mma' (tensor cores; mixed precision; before the
+        problem moves to the device)."""
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_set_z_transform(h, self.pid, L.Z_TRANSFORMS[kind]))
+
+    def z_transform(self):
+        out = ctypes.c_int()
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_get_z_transform(h, self.pid, ctypes.byref(out)))
+        return {v: k for k, v in L.Z_TRANSFORMS.items()}[out.value]
+
     def set_spike_blocks(self, nblk):
         """Row blocks per pencil of the partitioned substitution (0: automatic)."""
         h = self.ctx.handle
