@@ -6,7 +6,11 @@ general sparse tau method" for one Fourier wavenumber k_x (one pencil):
 * every equation is a sum of terms  coef(k_x) * op(variable)  split into the
   M group (multiplying the time derivative) and the L group, with
   op in {I, dz} along the Chebyshev axis (k_x factors such as i k_x or
-  -k_x^2 are folded into coef);
+  -k_x^2 are folded into coef), or a non-constant coefficient g(z) given by
+  its Chebyshev coefficients (Sec. "Non-constant coefficients"): op = NCC(g)
+  for g u, NCC(g, "dz") for dz(g u); the multiplication matrix in the T basis
+  is (M_g)_{ij} = sum_n g_n (delta_{i,j+n} + delta_{i,|j-n|}) / 2 (Appendix,
+  Chebyshev multiplication matrices), truncated to the N modes;
 * an equation containing a z-derivative is "differential": each block is
   left-multiplied by the T-to-U conversion P^L (the dz blocks become the
   T-to-U derivative D^TU, times 2/(b-a) for the problem interval) and its last
@@ -33,6 +37,27 @@ import scipy.sparse as sps
 from . import bases
 
 
+class NCC:
+    """Multiplication by g(z) = sum_n g[n] T_n, optionally followed by dz."""
+
+    def __init__(self, g, after="I"):
+        self.g = np.asarray(g, dtype=np.float64)
+        self.after = after
+
+
+def ncc_matrix(g, N):
+    """(M_g)_{ij} = sum_n g_n (delta_{i,j+n} + delta_{i,|j-n|}) / 2, i, j < N."""
+    M = np.zeros((N, N))
+    for n, gn in enumerate(np.asarray(g, dtype=np.float64)):
+        if gn == 0.0:
+            continue
+        for j in range(N):
+            if j + n < N:
+                M[j + n, j] += 0.5 * gn
+            M[abs(j - n), j] += 0.5 * gn
+    return M
+
+
 class TauProblem:
     """A first-order system M dt(X) + L X = F on one Chebyshev axis per pencil."""
 
@@ -55,7 +80,7 @@ class TauProblem:
         """Terms are (variable, op, coef) with op 'I' or 'dz' and coef a
         number or a function of k_x."""
         terms = list(M_terms) + list(L_terms)
-        differential = any(op == "dz" for (_, op, _) in terms)
+        differential = any((op.after if isinstance(op, NCC) else op) == "dz" for (_, op, _) in terms)
         self.equations.append(dict(name=name, M=list(M_terms), L=list(L_terms),
                                    differential=differential))
 
@@ -74,7 +99,15 @@ class TauProblem:
         return self.N - 1 if eq["differential"] else self.N
 
     def _block(self, eq, op, coef):
-        if eq["differential"]:
+        if isinstance(op, NCC):
+            Mg = sps.csr_matrix(ncc_matrix(op.g, self.N))
+            if op.after == "dz":
+                if not eq["differential"]:
+                    raise ValueError("algebraic equation with a z-derivative")
+                base = self._DTU @ Mg
+            else:
+                base = (self._PL @ Mg) if eq["differential"] else Mg
+        elif eq["differential"]:
             base = self._PL if op == "I" else self._DTU
         else:
             if op != "I":
