@@ -169,6 +169,19 @@ sp_status sp_set_bilinear_rhs(sp_ctx* ctx, int problem, int nterms, const int32_
  * sp_sync_status, which also reports the first failing pencil). */
 sp_status sp_factor(sp_ctx* ctx, int problem, double dt);
 
+/* Linear boundary value solve (Sec. "Linear boundary value solver"):
+ * L~_p X~_p = P^L_p F_p with the boundary values, X_p = P^R X~_p, for every
+ * pencil, into the problem's state (read it with sp_get_field).  M~ is not
+ * used.  The first call (and the first after sp_factor or sp_eig_target)
+ * factors L~ alone, replacing any stepping factorization (sp_step then
+ * needs sp_factor again).  F: host, nslots blocks [P][N_z] complex FP64 of
+ * T coefficients, block q the right-hand side of equation eqs[q] (other
+ * equations' right-hand sides are zero); differential equations get the
+ * T-to-U conversion and lose their tau row in the kernel, as the stepping
+ * right-hand sides do.  Synchronous.  SP_ERR_ARG for bad slots or equation
+ * indices, SP_ERR_SINGULAR if a pencil's L~ is singular. */
+sp_status sp_solve_lbvp(sp_ctx* ctx, int problem, int nslots, const int32_t* eqs, const void* F_host);
+
 /* Set / get one variable of the state (Sec. "Initial conditions").
  * layout 'c': P*N_z complex (re, im) doubles [p][m], true coefficients;
  * layout 'g': N_z*N_x (3D: N_z*N_y*N_x) real doubles [iz][ix] ([iz][iy][ix])

@@ -158,6 +158,12 @@ struct Problem {
   bool zmma = false;
   bool xs32_valid = false;
   ChebMMA cm;
+  // linear boundary value solve: L~ factored in the first slot, its
+  // right-hand-side slots [slot][P][Nz] and their equations
+  bool lbvp_factored = false;
+  double2* d_lb_F = nullptr;
+  int32_t* d_lb_eq = nullptr;
+  int lb_cap = 0;
   // CFL frequency scratch (sp_cfl_frequency), allocated on first use
   double* d_cfl_grid = nullptr;
   void *d_cfl_mid1 = nullptr, *d_cfl_mid2 = nullptr;
@@ -492,6 +498,7 @@ void free_problem(Problem* pr) {
   F(pr->d_bg); F(pr->d_xg); F(pr->d_yg);
   F(pr->d_sp_s0); F(pr->d_sp_s); F(pr->d_sp_o0); F(pr->d_sp_u);
   cheb_mma_free(pr->cm);
+  F(pr->d_lb_F); F(pr->d_lb_eq);
   F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd);
   F(pr->d_indptrT); F(pr->d_indicesT); F(pr->d_MvT); F(pr->d_LvT);
   F(pr->d_mu[0]); F(pr->d_mu[1]); F(pr->d_LTmu); F(pr->d_MTmu); F(pr->d_JF); F(pr->d_lamx);
@@ -1218,26 +1225,10 @@ sp_status sp_set_bilinear_rhs(sp_ctx* ctx, int problem, int nterms, const int32_
   return SP_OK;
 }
 
-sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
-  Problem* pr = get(ctx, problem);
-  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
-  ctx->err.clear();
-  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, SP_ERR_ARG, "dt must be positive and finite");
-  CK(cudaSetDevice(ctx->device));
-  sp_status st = upload_problem(ctx, pr);
-  if (st != SP_OK) return st;
-  double ab[4][2];
-  int nf = 1;
-  if (is_rk(pr->scheme)) {
-    const Tableau tb = make_tableau(pr->scheme);
-    ab[0][0] = 1.0; ab[0][1] = dt * tb.H[1][1];   // every stage: H_ii = H_11
-  } else if (is_cnab(pr->scheme)) {
-    ab[0][0] = 1.0; ab[0][1] = 0.5 * dt;         // both orders: M + dt/2 L
-  } else {
-    // SBDFq: the matrices a_0 M + dt L of the start-up orders 1 .. q
-    nf = sbdf_order(pr->scheme);
-    for (int f = 0; f < nf; ++f) { ab[f][0] = SBDF_A[f + 1][0]; ab[f][1] = dt; }
-  }
+// Banded LU of alpha_f M~ + beta_f L~ into factor slots f < nf for every
+// pencil (and, per solve kernel, the lane layout or the partitioned
+// substitution's coupling matrices); synchronous.
+static sp_status factor_matrices(sp_ctx* ctx, Problem* pr, int nf, const double (*ab)[2]) {
   const int ldab = 2 * pr->kl + pr->ku + 1;
   double* work = nullptr;
   CK(dalloc(&work, (size_t)pr->P * pr->n * ldab));
@@ -1289,12 +1280,96 @@ sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   cudaFree(work);
   CK(e);
+  return SP_OK;
+}
+
+sp_status sp_factor(sp_ctx* ctx, int problem, double dt) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, SP_ERR_ARG, "dt must be positive and finite");
+  CK(cudaSetDevice(ctx->device));
+  sp_status st = upload_problem(ctx, pr);
+  if (st != SP_OK) return st;
+  double ab[4][2];
+  int nf = 1;
+  if (is_rk(pr->scheme)) {
+    const Tableau tb = make_tableau(pr->scheme);
+    ab[0][0] = 1.0; ab[0][1] = dt * tb.H[1][1];   // every stage: H_ii = H_11
+  } else if (is_cnab(pr->scheme)) {
+    ab[0][0] = 1.0; ab[0][1] = 0.5 * dt;         // both orders: M + dt/2 L
+  } else {
+    // SBDFq: the matrices a_0 M + dt L of the start-up orders 1 .. q
+    nf = sbdf_order(pr->scheme);
+    for (int f = 0; f < nf; ++f) { ab[f][0] = SBDF_A[f + 1][0]; ab[f][1] = dt; }
+  }
+  sp_status fst = factor_matrices(ctx, pr, nf, ab);
+  if (fst != SP_OK) return fst;
+  pr->lbvp_factored = false;
   pr->nfac = nf;
   pr->fac_dt = dt;
   pr->factored = true;
   for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
   pr->graphs.clear();
   drop_batches(ctx, problem);
+  return SP_OK;
+}
+
+sp_status sp_solve_lbvp(sp_ctx* ctx, int problem, int nslots, const int32_t* eqs, const void* F_host) {
+  Problem* pr = get(ctx, problem);
+  if (!pr) return fail(ctx, SP_ERR_ARG, "bad context or problem id");
+  ctx->err.clear();
+  if (nslots < 0 || nslots > pr->S || (nslots > 0 && (!eqs || !F_host)))
+    return fail(ctx, SP_ERR_ARG, "bad right-hand-side slots");
+  for (int q = 0; q < nslots; ++q)
+    if (eqs[q] < 0 || eqs[q] >= pr->S) return fail(ctx, SP_ERR_ARG, "bad equation index %d", eqs[q]);
+  CK(cudaSetDevice(ctx->device));
+  sp_status st = upload_problem(ctx, pr);
+  if (st != SP_OK) return st;
+  cudaStream_t s = ctx->stream;
+  if (!pr->lbvp_factored) {
+    // L~ alone in the first factor slot: any stepping factorization is gone
+    pr->factored = false;
+    for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
+    pr->graphs.clear();
+    drop_batches(ctx, problem);
+    const double ab[1][2] = {{0.0, 1.0}};
+    if ((st = factor_matrices(ctx, pr, 1, ab)) != SP_OK) return st;
+    pr->lbvp_factored = true;
+  }
+  if (nslots > pr->lb_cap) {
+    cudaFree(pr->d_lb_F);
+    cudaFree(pr->d_lb_eq);
+    pr->d_lb_F = nullptr;
+    pr->d_lb_eq = nullptr;
+    pr->lb_cap = 0;
+    CK(dalloc(&pr->d_lb_F, (size_t)nslots * pr->P * pr->Nz));
+    CK(dalloc(&pr->d_lb_eq, (size_t)nslots));
+    pr->lb_cap = nslots;
+  }
+  if (nslots > 0) {
+    CK(cudaMemcpyAsync(pr->d_lb_F, F_host, (size_t)nslots * pr->P * pr->Nz * sizeof(double2),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(pr->d_lb_eq, eqs, (size_t)nslots * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  }
+  // B~ = P^L F (tau rows dropped) + boundary values; X~ = L~^-1 B~; X = P^R X~
+  SolveArgs a = base_args(pr, ctx, 0);
+  a.nvec = 0;
+  a.mv_x = nullptr;
+  a.nfc = nslots > 0 ? 1 : 0;
+  a.fc[0] = pr->d_lb_F; a.fc_coef[0] = 1.0;
+  a.nl_eq = pr->d_lb_eq; a.n_nl = nslots;
+  a.bc_coef = 1.0;
+  a.xc_out = pr->d_Xc;
+  a.xt_out = pr->d_Xt;
+  a.ep_mv_vals = nullptr;
+  if ((st = solve(ctx, pr, s, a)) != SP_OK) return st;
+  CK(cudaStreamSynchronize(s));
+  pr->xt_valid = true;
+  pr->mx_valid = false;
+  pr->iteration = 0;
+  pr->xc32_valid = pr->prec != 0;     // the epilogue wrote the FP32 copies too
+  pr->xs32_valid = pr->zmma;
   return SP_OK;
 }
 
@@ -1967,6 +2042,7 @@ sp_status sp_eig_target(sp_ctx* ctx, int problem, double sigma_t, int iters, con
   cudaStream_t s = ctx->stream;
   // L~ + sigma_T M~ into the first factor slot: the step's factorization is gone
   pr->factored = false;
+  pr->lbvp_factored = false;
   for (auto& kv : pr->graphs) cudaGraphExecDestroy(kv.second);
   pr->graphs.clear();
   drop_batches(ctx, problem);

@@ -12,6 +12,7 @@ import numpy as np
 
 from . import _lib as L
 from . import fisher as fkmod
+from . import qg as qgmod
 from . import rb as rbmod
 
 
@@ -110,6 +111,17 @@ class TauSolver:
         """'auto', 'window', 'lanes' or 'spike' (before the problem moves to the device)."""
         h = self.ctx.handle
         L.check(h, L.lib().sp_set_solve_kernel(h, self.pid, L.SOLVE_KERNELS[kind]))
+
+    def solve_lbvp(self, F):
+        """Linear boundary value solve into the state: F maps equation name
+        -> [P, N_z] complex T coefficients of its right-hand side."""
+        names = list(F)
+        eqs = np.array([self.eq[e] for e in names], np.int32)
+        data = np.ascontiguousarray(np.stack([np.asarray(F[e], np.complex128) for e in names])) if names \
+            else np.zeros((1, self.P, self.Nz), np.complex128)
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_solve_lbvp(h, self.pid, len(names), L.i32(eqs), data.ctypes.data_as(ctypes.c_void_p)))
+        return self.get_state()
 
     def set_z_transform(self, kind):
         """'auto', 'fft' or 'mma' (tensor cores; mixed precision; before the
@@ -374,6 +386,21 @@ class RBOnsetEVP(TauSolver):
     def growth_rates(self, target=0.0, iters=60, x0=None):
         """Growth rate sigma of the mode nearest `target` in every pencil."""
         return self.eig_target(target, iters, x0)
+
+
+class QGInversion(TauSolver):
+    """Potential-vorticity inversion dx dx psi + dz(S(z) dz psi) = q with the
+    stratification S given by its Chebyshev coefficients (a linear boundary
+    value problem with a non-constant coefficient)."""
+
+    def __init__(self, ctx, n_x, n_z, strat, L_x=2 * np.pi, precision="fp64"):
+        problem = qgmod.qg_pencil_problem(strat)
+        super().__init__(ctx, problem, n_x, n_z, L_x, scheme="RK222", precision=precision)
+        self.state_order = qgmod.VARIABLES
+
+    def invert(self, q):
+        """psi and psiz ([2, P, N_z] T coefficients) from q [P, N_z]."""
+        return self.solve_lbvp({"pv": q})
 
 
 class RB3DSolver(TauSolver):

@@ -42,8 +42,9 @@ def _as_fn(c):
 @dataclass
 class Term:
     var: str
-    op: str            # "I" or "dz"
+    op: str            # "I", "dz", "ncc" (g u) or "nccdz" (dz(g u))
     coef: object       # number or function of the wavenumber(s) (evaluated on arrays)
+    ncc: Optional[Sequence[float]] = None   # Chebyshev coefficients of g(z) for the ncc ops
 
 
 @dataclass
@@ -55,7 +56,7 @@ class Equation:
 
     @property
     def differential(self):
-        return any(t.op == "dz" for t in self.M + self.L)
+        return any(t.op in ("dz", "nccdz") for t in self.M + self.L)
 
 
 @dataclass
@@ -91,6 +92,33 @@ def _dtu_entries(N, scale):
 
 def _ident_entries(N):
     return [(j, j, 1.0) for j in range(N)]
+
+
+def _ncc_entries(g, N):
+    """Multiplication by g(z) = sum_n g_n T_n in the T basis (Sec. "Non-
+    constant coefficients"; T_n T_j = (T_{j+n} + T_{|j-n|}) / 2), truncated to
+    N modes: bandwidth len(g) - 1 above and below the diagonal."""
+    acc = {}
+    for n, gn in enumerate(np.asarray(g, dtype=np.float64)):
+        if gn == 0.0:
+            continue
+        for j in range(N):
+            for i in (j + n, abs(j - n)):
+                if i < N:
+                    acc[(i, j)] = acc.get((i, j), 0.0) + 0.5 * gn
+    return [(i, j, v) for (i, j), v in acc.items() if v != 0.0]
+
+
+def _compose(a, b):
+    """Entries of the product A B of two sparse operators given as entries."""
+    rows = {}
+    for (i, k, v) in a:
+        rows.setdefault(k, []).append((i, v))
+    acc = {}
+    for (k, j, w) in b:
+        for (i, v) in rows.get(k, []):
+            acc[(i, j)] = acc.get((i, j), 0.0) + v * w
+    return [(i, j, v) for (i, j), v in acc.items() if v != 0.0]
 
 
 def _recombine(entries, N):
@@ -169,7 +197,17 @@ class PencilProblem:
     # -- assembly ----------------------------------------------------------------
     def _term_entries(self, eq, term, N):
         zscale = 2.0 / (self.b - self.a)
-        if eq.differential:
+        if term.op in ("ncc", "nccdz"):
+            g = _ncc_entries(term.ncc, N)
+            if eq.differential:
+                left = _conv_entries(N) if term.op == "ncc" else _dtu_entries(N, zscale)
+                base = _compose(left, g)
+                base = [(i, j, v) for (i, j, v) in base if i < N - 1]
+            else:
+                if term.op != "ncc":
+                    raise ValueError("algebraic equation with a z-derivative")
+                base = g
+        elif eq.differential:
             base = _conv_entries(N) if term.op == "I" else _dtu_entries(N, zscale)
             base = [(i, j, v) for (i, j, v) in base if i < N - 1]
         else:
