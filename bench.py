@@ -401,7 +401,7 @@ def run_batch(args):
     """64 independent uneven 2D RB instances advanced together (RK222)."""
     import torch
     torch.cuda.set_device(0)
-    from paper_1905_10388_gb300.solver import Context, RBSolver, batch_tile, step_batched
+    from paper_1905_10388_gb300.solver import Context, RBSolver, batch_persistent, batch_tile, step_batched
     ws = si.batched_workloads()
     ctx = Context(0, torch.cuda.current_stream(0).cuda_stream)
     solvers = []
@@ -428,6 +428,17 @@ def run_batch(args):
         raise RuntimeError(f"device status {st} at pencil {pen}")
     ms = e0.elapsed_time(e1)
     dof = sum(w.dof for w in ws)
+    # the same steps of every instance on its own (graph replay, one problem
+    # at a time), for the comparison with the batched launches
+    solo_ms = 0.0
+    for s in solvers:
+        s.step(2, graph=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(args.steps, graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        solo_ms += e0.elapsed_time(e1)
     res = {"metric": METRIC, "value": dof * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
@@ -435,8 +446,13 @@ def run_batch(args):
            "config": {"workload": "rb2d_batch64_rk222", "instances": len(ws), "dof_total": dof,
                       "n_x": sorted({w.n_x for w in ws}), "n_z": sorted({w.n_z for w in ws}),
                       "precision": args.precision, "z_tile": batch_tile(solvers),
-                      "launch": "one batched launch per kernel type per stage, CUDA graph",
+                      "persistent": batch_persistent(solvers),
+                      "launch": ("one batched launch per kernel type per stage, CUDA graph; "
+                                 "launch shape (per-item CTAs or persistent grids on a work queue) and z tile "
+                                 "chosen by the library's autotuner"),
                       "l2": "working set > L2"},
+           "solo": {"ms_per_step_sum_of_instances": solo_ms / args.steps,
+                    "batched_speedup": solo_ms / ms},
            "roofline": None, "gpu_launches": 8 * args.steps, "clocks": clk}
     ctx.close()
     return res

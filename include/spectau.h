@@ -223,6 +223,20 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
                           int nsteps, int use_graph);
 sp_status sp_batch_tile(sp_ctx* ctx, int nproblems, const int* problem_ids, int* tile);
 
+/* Launch shape the batch autotuner chose for these problems on their first
+ * batched step: *persistent = 1 when the batched transform kernels run as
+ * persistent grids (as many CTAs as the GPU holds at once) pulling (problem,
+ * tile) work items from a device counter, largest items first; 0 when each
+ * work item has a CTA of its own.  The batched pencil solves always take one
+ * CTA per pencil.  The autotuner times one batch step of
+ * each shape (with the z tile it picked) on a saved copy of every buffer a
+ * step writes, then restores them.  SP_ERR_STATE before that step. */
+sp_status sp_batch_persistent(sp_ctx* ctx, int nproblems, const int* problem_ids, int* persistent);
+/* Fix the launch shape of these problems' batched steps (mode 1:
+ * persistent grids, 0: one CTA per work item) or hand it back to the
+ * autotuner (-1); takes effect at the next sp_step_batched. */
+sp_status sp_set_batch_persistent(sp_ctx* ctx, int nproblems, const int* problem_ids, int mode);
+
 /* Discrete adjoint of the step (Sec. "Runge-Kutta IMEX integrators": the
  * transpose of each stage equation), for the RK222 and RK111 schemes.  The
  * state space is that of sp_set_field/sp_get_field ('c' layout, all S
@@ -297,6 +311,16 @@ sp_status sp_get_band(sp_ctx* ctx, int problem, int* n, int* kl, int* ku);
  * shifted pencil) are latched in the status word (sp_sync_status). */
 sp_status sp_eig_target(sp_ctx* ctx, int problem, double sigma_t, int iters, const void* x0_host, double* sigma_re,
                         double* sigma_im);
+
+/* Residual of the last sp_eig_target's eigenpairs (the converged iterate x_p
+ * and sigma_p of every pencil): residual[p] = ||(L~ + sigma_p M~) x_p|| /
+ * (||L~ x_p|| + |sigma_p| ||M~ x_p||) (host, [P]) -- a check of every
+ * pencil's pair that needs no other solver (an eigenpair gives rounding
+ * level; an unconverged iterate, whose two nearest eigenvalues the
+ * iteration has not separated, a larger value).  Several modes per pencil:
+ * one sp_eig_target per target (the mode nearest each).  Synchronous.
+ * SP_ERR_STATE before any eigensolve. */
+sp_status sp_eig_residual(sp_ctx* ctx, int problem, double* residual);
 
 /* CFL frequency of the current state (Sec. "Timestep determination"): the
  * largest over the points of the dealiased grid of

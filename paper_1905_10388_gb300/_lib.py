@@ -36,7 +36,8 @@ EXPORTS = (
     "sp_dz_adjoint", "sp_step_record", "sp_set_solve_kernel", "sp_get_solve_work",
     "sp_cfl_frequency", "sp_cfl_dt", "sp_eig_target", "sp_measure_fma_peak",
     "sp_set_spike_blocks", "sp_get_spike_blocks", "sp_set_z_transform", "sp_get_z_transform",
-    "sp_solve_lbvp",
+    "sp_solve_lbvp", "sp_eig_residual", "sp_batch_persistent",
+    "sp_set_batch_persistent",
 )
 
 
@@ -99,6 +100,9 @@ _SIGS = {
     "sp_set_z_transform": [P, I, I],
     "sp_get_z_transform": [P, I, ctypes.POINTER(I)],
     "sp_solve_lbvp": [P, I, I, I32P, P],
+    "sp_eig_residual": [P, I, ctypes.POINTER(D)],
+    "sp_batch_persistent": [P, I, ctypes.POINTER(I), ctypes.POINTER(I)],
+    "sp_set_batch_persistent": [P, I, ctypes.POINTER(I), I],
 }
 Z_TRANSFORMS = {"auto": 0, "fft": 1, "mma": 2}
 

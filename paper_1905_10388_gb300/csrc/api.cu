@@ -161,6 +161,8 @@ struct Problem {
   // linear boundary value solve: L~ factored in the first slot, its
   // right-hand-side slots [slot][P][Nz] and their equations
   bool lbvp_factored = false;
+  // the last eigensolve's vectors (solve variables, [P][n]) and eigenvalues
+  double2 *d_eigx = nullptr, *d_eigsig = nullptr;
   double2* d_lb_F = nullptr;
   int32_t* d_lb_eq = nullptr;
   int lb_cap = 0;
@@ -225,6 +227,8 @@ struct sp_ctx {
   // batches keyed by (problem ids, schedule phase); tile chosen per ids
   std::map<std::pair<std::vector<int>, int>, Batch*> batches;
   std::map<std::vector<int>, int> batch_tile;
+  std::map<std::vector<int>, bool> batch_persist;
+  std::map<std::vector<int>, bool> batch_persist_fixed;   // shapes set by sp_set_batch_persistent
 };
 
 namespace {
@@ -498,7 +502,7 @@ void free_problem(Problem* pr) {
   F(pr->d_bg); F(pr->d_xg); F(pr->d_yg);
   F(pr->d_sp_s0); F(pr->d_sp_s); F(pr->d_sp_o0); F(pr->d_sp_u);
   cheb_mma_free(pr->cm);
-  F(pr->d_lb_F); F(pr->d_lb_eq);
+  F(pr->d_lb_F); F(pr->d_lb_eq); F(pr->d_eigx); F(pr->d_eigsig);
   F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd);
   F(pr->d_indptrT); F(pr->d_indicesT); F(pr->d_MvT); F(pr->d_LvT);
   F(pr->d_mu[0]); F(pr->d_mu[1]); F(pr->d_LTmu); F(pr->d_MTmu); F(pr->d_JF); F(pr->d_lamx);
@@ -871,13 +875,16 @@ struct Batch {
   int nzb = 0, nx = 0, nzf = 0, ns = 0;
   std::vector<BatchStage> stages;
   std::map<int, cudaGraphExec_t> graphs;     // by block length
+  // persistent launches: four work counters per stage, zeroed once per step
+  bool persist = false;
+  int* d_queue = nullptr;
 };
 
 namespace {
 
 void free_batch(Batch* b) {
   auto F = [](void* p) { if (p) cudaFree(p); };
-  F(b->d_wzb); F(b->d_wx); F(b->d_wzf); F(b->d_ws);
+  F(b->d_wzb); F(b->d_wx); F(b->d_wzf); F(b->d_ws); F(b->d_queue);
   for (auto& st : b->stages) { F(st.d_zb); F(st.d_zf); F(st.d_x); F(st.d_args); }
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
 }
@@ -891,8 +898,9 @@ cudaError_t upload_vec(T** d, const std::vector<T>& v) {
 
 // Work lists in descending cost order (largest items first).
 sp_status build_batch(sp_ctx* ctx, const std::vector<Problem*>& ps, const std::vector<int>& ids, int tile,
-                      int parity, Batch* b) {
+                      int parity, bool persist, Batch* b) {
   b->ids = ids;
+  b->persist = persist;
   b->prec = ps[0]->prec;
   b->scheme = ps[0]->scheme;
   b->tile = tile;
@@ -955,6 +963,7 @@ sp_status build_batch(sp_ctx* ctx, const std::vector<Problem*>& ps, const std::v
     CK(upload_vec(&st.d_args, av));
     b->stages.push_back(st);
   }
+  CK(dalloc(&b->d_queue, (size_t)4 * std::max(1, b->nstage)));
   return SP_OK;
 }
 
@@ -976,10 +985,13 @@ void drop_batches(sp_ctx* ctx, int problem) {
 }
 
 sp_status batch_step(sp_ctx* ctx, Batch* b, cudaStream_t s) {
-  for (const BatchStage& st : b->stages) {
-    CK(launch_cheb_backward_batched(s, b->prec, b->tile, st.d_zb, b->d_wzb, b->nzb, b->max_ngz));
-    CK(launch_fourier_rows_batched(s, b->prec, st.d_x, b->d_wx, b->nx, b->x_smem));
-    CK(launch_cheb_forward_batched(s, b->prec, b->tile, st.d_zf, b->d_wzf, b->nzf, b->max_ngz));
+  if (b->persist) CK(cudaMemsetAsync(b->d_queue, 0, (size_t)4 * b->nstage * sizeof(int), s));
+  for (int i = 0; i < b->nstage; ++i) {
+    const BatchStage& st = b->stages[i];
+    int* q = b->persist ? b->d_queue + 4 * i : nullptr;
+    CK(launch_cheb_backward_batched(s, b->prec, b->tile, st.d_zb, b->d_wzb, b->nzb, b->max_ngz, q));
+    CK(launch_fourier_rows_batched(s, b->prec, st.d_x, b->d_wx, b->nx, b->x_smem, q ? q + 1 : nullptr));
+    CK(launch_cheb_forward_batched(s, b->prec, b->tile, st.d_zf, b->d_wzf, b->nzf, b->max_ngz, q ? q + 2 : nullptr));
     CK(launch_pencil_solve_batched(s, st.d_args, b->d_ws, b->ns, b->max_kuu, b->s_smem));
   }
   return SP_OK;
@@ -1581,13 +1593,13 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
     if (multistep && pr->iteration % D != ps[0]->iteration % D)
       return fail(ctx, SP_ERR_STATE, "problems of a batch must be at the same step phase (iteration mod %d)", D);
   // tile autotuning of the z-transform kernels (first call for these ids)
-  auto get_batch = [&](int parity, int tile) -> Batch* {
+  auto get_batch = [&](int parity, int tile, bool persist) -> Batch* {
     auto key = std::make_pair(ids, parity);
     auto it = ctx->batches.find(key);
-    if (it != ctx->batches.end() && it->second->tile == tile) return it->second;
+    if (it != ctx->batches.end() && it->second->tile == tile && it->second->persist == persist) return it->second;
     if (it != ctx->batches.end()) { free_batch(it->second); delete it->second; ctx->batches.erase(it); }
     Batch* b = new Batch();
-    if (build_batch(ctx, ps, ids, tile, parity, b) != SP_OK) { free_batch(b); delete b; return nullptr; }
+    if (build_batch(ctx, ps, ids, tile, parity, persist, b) != SP_OK) { free_batch(b); delete b; return nullptr; }
     ctx->batches[key] = b;
     return b;
   };
@@ -1598,7 +1610,7 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
     int best = 8;
     float best_ms = 1e30f;
     for (int tile : {4, 8, 16}) {
-      Batch* b = get_batch(multistep ? ps[0]->iteration % D : 0, tile);
+      Batch* b = get_batch(multistep ? ps[0]->iteration % D : 0, tile, false);
       if (!b) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
       // the transform kernels write only scratch buffers that the next step overwrites
       const BatchStage& sg = b->stages[0];
@@ -1615,14 +1627,69 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
       }
       if (tot < best_ms) { best_ms = tot; best = tile; }
     }
+    // launch shape: one CTA per work item, or persistent grids pulling the
+    // items from device counters.  A batch step of each is timed; every
+    // buffer a step writes (states, history rings, right-hand-side slots)
+    // is copied aside first and restored afterwards, so the timing leaves
+    // the problems exactly as they were.
+    std::vector<std::pair<void*, size_t>> bufs;
+    for (Problem* pr : ps) {
+      const size_t nvec = (size_t)pr->P * pr->n * sizeof(double2);
+      const size_t nfc = (size_t)std::max<int>(1, (int)pr->nl_eqs.size()) * pr->P * pr->Nz * sizeof(double2);
+      bufs.push_back({pr->d_Xt, nvec});
+      bufs.push_back({pr->d_Xc, nvec});
+      if (pr->d_Xc32) bufs.push_back({pr->d_Xc32, (size_t)pr->P * pr->n * sizeof(float2)});
+      for (double2* b : pr->d_MX) if (b) bufs.push_back({b, nvec});
+      for (double2* b : pr->d_LX) if (b) bufs.push_back({b, nvec});
+      for (double2* b : pr->d_Fc) if (b) bufs.push_back({b, nfc});
+      if (pr->zmma) bufs.push_back({pr->cm.xs32, (size_t)pr->S * 2 * pr->P * pr->Nz * sizeof(float)});
+    }
+    size_t total = 0;
+    for (auto& b : bufs) total += b.second;
+    char* backup = nullptr;
+    CK(cudaMalloc(&backup, total));
+    size_t off = 0;
+    for (auto& b : bufs) {
+      CK(cudaMemcpyAsync(backup + off, b.first, b.second, cudaMemcpyDeviceToDevice, ctx->stream));
+      off += b.second;
+    }
+    bool best_persist = false;
+    float shape_ms[2] = {1e30f, 1e30f};
+    for (int pm = 0; pm < 2; ++pm) {
+      Batch* b = get_batch(multistep ? ps[0]->iteration % D : 0, best, pm == 1);
+      if (!b) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
+      float tot = 0;
+      for (int rep = 0; rep < 3; ++rep) {
+        CK(cudaEventRecord(e0, ctx->stream));
+        if ((st = batch_step(ctx, b, ctx->stream)) != SP_OK) return st;
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) tot += ms;
+      }
+      shape_ms[pm] = tot;
+    }
+    best_persist = shape_ms[1] < shape_ms[0];
+    auto fixed = ctx->batch_persist_fixed.find(ids);
+    if (fixed != ctx->batch_persist_fixed.end()) best_persist = fixed->second;
+    off = 0;
+    for (auto& b : bufs) {
+      CK(cudaMemcpyAsync(b.first, backup + off, b.second, cudaMemcpyDeviceToDevice, ctx->stream));
+      off += b.second;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(backup);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->batch_tile[ids] = best;
+    ctx->batch_persist[ids] = best_persist;
   }
   const int tile = ctx->batch_tile[ids];
+  const bool persist = ctx->batch_persist[ids];
   while (nsteps > 0) {
     const int parity = multistep ? ps[0]->iteration % D : 0;
-    Batch* b = get_batch(parity, tile);
+    Batch* b = get_batch(parity, tile, persist);
     if (!b) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
     if (!use_graph) {
       if ((st = batch_step(ctx, b, ctx->stream)) != SP_OK) return st;
@@ -1637,7 +1704,7 @@ sp_status sp_step_batched(sp_ctx* ctx, int nproblems, const int* problem_ids, co
     if (git == b->graphs.end()) {
       std::vector<Batch*> phase_batch(D, nullptr);
       for (int q = 0; q < D; ++q) {
-        phase_batch[q] = q == parity ? b : get_batch(q, tile);
+        phase_batch[q] = q == parity ? b : get_batch(q, tile, persist);
         if (!phase_batch[q]) return fail(ctx, SP_ERR_CUDA, "building batch: %s", ctx->err.c_str());
       }
       cudaGraph_t g;
@@ -1667,6 +1734,26 @@ sp_status sp_batch_tile(sp_ctx* ctx, int nproblems, const int* problem_ids, int*
   auto it = ctx->batch_tile.find(ids);
   if (it == ctx->batch_tile.end()) return fail(ctx, SP_ERR_STATE, "no batch step has run for these problems");
   *tile = it->second;
+  return SP_OK;
+}
+
+sp_status sp_set_batch_persistent(sp_ctx* ctx, int nproblems, const int* problem_ids, int mode) {
+  if (!ctx || nproblems < 1 || !problem_ids || mode < -1 || mode > 1) return SP_ERR_ARG;
+  std::vector<int> ids(problem_ids, problem_ids + nproblems);
+  if (mode < 0) ctx->batch_persist_fixed.erase(ids);
+  else ctx->batch_persist_fixed[ids] = mode == 1;
+  // the next batched step decides (or applies) the shape again
+  ctx->batch_tile.erase(ids);
+  ctx->batch_persist.erase(ids);
+  return SP_OK;
+}
+
+sp_status sp_batch_persistent(sp_ctx* ctx, int nproblems, const int* problem_ids, int* persistent) {
+  if (!ctx || nproblems < 1 || !problem_ids || !persistent) return SP_ERR_ARG;
+  std::vector<int> ids(problem_ids, problem_ids + nproblems);
+  auto it = ctx->batch_persist.find(ids);
+  if (it == ctx->batch_persist.end()) return fail(ctx, SP_ERR_STATE, "no batch step has run for these problems");
+  *persistent = it->second ? 1 : 0;
   return SP_OK;
 }
 
@@ -2085,14 +2172,42 @@ sp_status sp_eig_target(sp_ctx* ctx, int problem, double sigma_t, int iters, con
   std::vector<double2> hm(pr->P);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), mu, hm.size() * sizeof(double2), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  release();
-  CK(e);
+  if (e != cudaSuccess) { release(); CK(e); }
+  std::vector<double2> hs(pr->P);
   for (int p = 0; p < pr->P; ++p) {
     // sigma = sigma_T - 1 / mu
     const double m2 = hm[p].x * hm[p].x + hm[p].y * hm[p].y;
     sigma_re[p] = m2 > 0 ? sigma_t - hm[p].x / m2 : NAN;
     sigma_im[p] = m2 > 0 ? hm[p].y / m2 : NAN;
+    hs[p] = make_double2(sigma_re[p], sigma_im[p]);
   }
+  // keep the eigenpairs for sp_eig_residual: x (normalized iterate) and sigma
+  cudaFree(pr->d_eigx);
+  cudaFree(pr->d_eigsig);
+  pr->d_eigx = x;
+  x = nullptr;
+  pr->d_eigsig = nullptr;
+  release();
+  CK(dalloc(&pr->d_eigsig, (size_t)pr->P));
+  CK(cudaMemcpy(pr->d_eigsig, hs.data(), hs.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  return SP_OK;
+}
+
+sp_status sp_eig_residual(sp_ctx* ctx, int problem, double* residual) {
+  Problem* pr = get(ctx, problem);
+  if (!pr || !residual) return fail(ctx, SP_ERR_ARG, "bad context, problem id or output");
+  ctx->err.clear();
+  if (!pr->d_eigx || !pr->d_eigsig) return fail(ctx, SP_ERR_STATE, "no eigensolve has run on this problem");
+  CK(cudaSetDevice(ctx->device));
+  double* d = nullptr;
+  CK(dalloc(&d, (size_t)pr->P));
+  cudaError_t e = launch_eig_residual(ctx->stream, pr->P, pr->n, (int)pr->nnz, pr->d_indptr, pr->d_indices, pr->d_Mv,
+                                      pr->d_Lv, pr->d_eigx, pr->d_eigsig, d);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(residual, d, (size_t)pr->P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d);
+  CK(e);
   return SP_OK;
 }
 

@@ -636,7 +636,9 @@ __global__ void __launch_bounds__(512, 2) k_pencil_stage_wide(SolveArgs a) {
 
 // a batch of problems: work item (problem, pencil) per CTA
 template <int RU>
-__global__ void __launch_bounds__(128, 1) k_pencil_solve_batched(const SolveArgs* __restrict__ args,
+// (one CTA per pencil: its items are long dependent chains, so a
+// persistent grid buys nothing here; 128 registers keep three CTAs per SM)
+__global__ void __launch_bounds__(128, 4) k_pencil_solve_batched(const SolveArgs* __restrict__ args,
                                                                  const int4* __restrict__ work) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int4 w = work[blockIdx.x];
@@ -1280,6 +1282,57 @@ __global__ void __launch_bounds__(256) k_eig_update(int P, int n, double2* __res
     const double2 b = yp[r];
     xp[r] = make_double2(b.x * sc, b.y * sc);
   }
+}
+
+// Relative residual of each pencil's eigenpair (sigma_p, x_p) of
+// sigma M~ x + L~ x = 0: ||(L~ + sigma M~) x|| / (||L~ x|| + |sigma| ||M~ x||),
+// one CTA per pencil, the pencils' CSR values on the shared pattern.
+__global__ void __launch_bounds__(256) k_eig_residual(int P, int n, int nnz, const int32_t* __restrict__ indptr,
+                                                      const int32_t* __restrict__ indices,
+                                                      const double* __restrict__ Mv, const double* __restrict__ Lv,
+                                                      const double2* __restrict__ x, const double2* __restrict__ sig,
+                                                      double* __restrict__ res) {
+  const int p = blockIdx.x;
+  if (p >= P) return;
+  const double* M = Mv + (size_t)p * nnz;
+  const double* L = Lv + (size_t)p * nnz;
+  const double2* xp = x + (size_t)p * n;
+  const double2 sg = sig[p];
+  double rr = 0, ll = 0, mm = 0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    double2 lx = make_double2(0.0, 0.0), mx = make_double2(0.0, 0.0);
+    for (int e = indptr[r]; e < indptr[r + 1]; ++e) {
+      const double2 v = xp[indices[e]];
+      lx.x = fma(L[e], v.x, lx.x); lx.y = fma(L[e], v.y, lx.y);
+      mx.x = fma(M[e], v.x, mx.x); mx.y = fma(M[e], v.y, mx.y);
+    }
+    const double rx = lx.x + sg.x * mx.x - sg.y * mx.y, ry = lx.y + sg.x * mx.y + sg.y * mx.x;
+    rr += rx * rx + ry * ry;
+    ll += lx.x * lx.x + lx.y * lx.y;
+    mm += mx.x * mx.x + mx.y * mx.y;
+  }
+  __shared__ double red[3][8];
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    ll += __shfl_xor_sync(0xffffffffu, ll, o);
+    mm += __shfl_xor_sync(0xffffffffu, mm, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { red[0][w] = rr; red[1][w] = ll; red[2][w] = mm; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    rr = ll = mm = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { rr += red[0][k]; ll += red[1][k]; mm += red[2][k]; }
+    const double den = sqrt(ll) + sqrt(sg.x * sg.x + sg.y * sg.y) * sqrt(mm);
+    res[p] = den > 0 ? sqrt(rr) / den : 0.0;
+  }
+}
+
+cudaError_t launch_eig_residual(cudaStream_t s, int P, int n, int nnz, const int32_t* indptr, const int32_t* indices,
+                                const double* Mv, const double* Lv, const double2* x, const double2* sig,
+                                double* res) {
+  k_eig_residual<<<P, 256, 0, s>>>(P, n, nnz, indptr, indices, Mv, Lv, x, sig, res);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_eig_update(cudaStream_t s, int P, int n, double2* x, const double2* y, double2* mu) {

@@ -66,6 +66,29 @@ __device__ __forceinline__ double2 cipow_d(double2 a, int q) {
 }
 
 // ---------------------------------------------------------------------------
+// work items of a batched launch: one per CTA (queue null), or pulled from a
+// device counter by a fixed, persistent grid (the work lists are sorted
+// largest first, so the dynamic order balances uneven items)
+// ---------------------------------------------------------------------------
+template <typename F>
+__device__ __forceinline__ void for_each_item(int nwork, int* queue, F&& body) {
+  if (queue == nullptr) {
+    body((int)blockIdx.x);
+    return;
+  }
+  __shared__ int next_item;
+  while (true) {
+    if (threadIdx.x == 0) next_item = atomicAdd(queue, 1);
+    __syncthreads();
+    const int item = next_item;
+    __syncthreads();                 // every thread has the item before thread 0 takes the next
+    if (item >= nwork) break;
+    body(item);
+    __syncthreads();                 // the item's shared memory is free for the next one
+  }
+}
+
+// ---------------------------------------------------------------------------
 // device status word: first error wins; bad pencil recorded alongside
 // ---------------------------------------------------------------------------
 struct DevStatus {

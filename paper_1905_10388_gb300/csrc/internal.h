@@ -224,7 +224,11 @@ cudaError_t launch_band_factor(cudaStream_t s, int P, int n, int nnz, int kl, in
                                DevStatus* st);
 cudaError_t launch_pencil_solve(cudaStream_t s, const SolveArgs& a);
 cudaError_t launch_eig_update(cudaStream_t s, int P, int n, double2* x, const double2* y, double2* mu);
+cudaError_t launch_eig_residual(cudaStream_t s, int P, int n, int nnz, const int32_t* indptr, const int32_t* indices,
+                                const double* Mv, const double* Lv, const double2* x, const double2* sig,
+                                double* res);
 size_t pencil_solve_smem(int npad, int lpad, int upad);
+// batched pencil solves: one CTA per (problem, pencil) work item
 cudaError_t launch_pencil_solve_batched(cudaStream_t s, const SolveArgs* args, const int4* work, int nwork,
                                         int max_kuu, size_t smem);
 // Lane-per-pencil substitution (many-pencil problems): forward and back
@@ -274,11 +278,13 @@ cudaError_t launch_fourier_y(cudaStream_t s, int prec, const TransformPlan& py, 
                              const void* src, void* dst);
 size_t z_smem_bytes(int prec, int Ng, int tile);
 size_t x_smem_bytes(int prec, int N, int mode, int nf, int ne);
+// batched transforms: queue null: one CTA per work item; else a persistent
+// grid pulling items from the device counter *queue (zero before the launch)
 cudaError_t launch_cheb_backward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,
-                                         int nwork, int max_ng);
+                                         int nwork, int max_ng, int* queue = nullptr);
 cudaError_t launch_cheb_forward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,
-                                        int nwork, int max_ng);
+                                        int nwork, int max_ng, int* queue = nullptr);
 cudaError_t launch_fourier_rows_batched(cudaStream_t s, int prec, const XDesc* ds, const int4* work, int nwork,
-                                        size_t smem);
+                                        size_t smem, int* queue = nullptr);
 
 }  // namespace spectau

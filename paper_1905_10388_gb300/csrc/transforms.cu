@@ -449,10 +449,13 @@ __global__ void __launch_bounds__(Z_THREADS) k_cheb_backward(ZDesc d) {
 }
 template <typename T, int TP>
 __global__ void __launch_bounds__(Z_THREADS) k_cheb_backward_batched(const ZDesc* __restrict__ ds,
-                                                                   const int4* __restrict__ work) {
+                                                                   const int4* __restrict__ work, int nwork,
+                                                                   int* queue) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int4 w = work[blockIdx.x];
-  cheb_backward_body<T, TP>(ds[w.x], w.y, w.z, smem_raw);
+  for_each_item(nwork, queue, [&](int it) {
+    const int4 w = work[it];
+    cheb_backward_body<T, TP>(ds[w.x], w.y, w.z, smem_raw);
+  });
 }
 template <typename T, int TP>
 __global__ void __launch_bounds__(Z_THREADS) k_cheb_forward(ZDesc d) {
@@ -461,10 +464,13 @@ __global__ void __launch_bounds__(Z_THREADS) k_cheb_forward(ZDesc d) {
 }
 template <typename T, int TP>
 __global__ void __launch_bounds__(Z_THREADS) k_cheb_forward_batched(const ZDesc* __restrict__ ds,
-                                                                  const int4* __restrict__ work) {
+                                                                  const int4* __restrict__ work, int nwork,
+                                                                  int* queue) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int4 w = work[blockIdx.x];
-  cheb_forward_body<T, TP>(ds[w.x], w.y, w.z, smem_raw);
+  for_each_item(nwork, queue, [&](int it) {
+    const int4 w = work[it];
+    cheb_forward_body<T, TP>(ds[w.x], w.y, w.z, smem_raw);
+  });
 }
 constexpr int Y_TILE = 4;
 template <typename T>
@@ -484,10 +490,13 @@ __global__ void __launch_bounds__(X_THREADS) k_fourier_rows_adjoint(XDesc d) {
 }
 template <typename T>
 __global__ void __launch_bounds__(X_THREADS) k_fourier_rows_batched(const XDesc* __restrict__ ds,
-                                                                  const int4* __restrict__ work) {
+                                                                  const int4* __restrict__ work, int nwork,
+                                                                  int* queue) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int4 w = work[blockIdx.x];
-  fourier_rows_body<T>(ds[w.x], w.y, smem_raw);
+  for_each_item(nwork, queue, [&](int it) {
+    const int4 w = work[it];
+    fourier_rows_body<T>(ds[w.x], w.y, smem_raw);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -630,17 +639,32 @@ cudaError_t launch_fourier_rows_adjoint(cudaStream_t s, int prec, const Transfor
 }
 
 // batched launches: one CTA per work item
+// Grid of a batched launch: one CTA per item, or (queue set) a persistent
+// grid of as many CTAs as fit on the GPU at once (at most one per item).
+template <typename K>
+static int batched_grid(K kernel, int threads, size_t smem, int nwork, const int* queue) {
+  if (queue == nullptr) return nwork;
+  int dev = 0, sms = 1, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return std::max(1, std::min(nwork, sms * per_sm));
+}
+
 cudaError_t launch_cheb_backward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,
-                                         int nwork, int max_ng) {
+                                         int nwork, int max_ng, int* queue) {
   const size_t smem = z_smem_bytes(prec, max_ng, tile);
   cudaError_t e = cudaSuccess;
 #define CALL(TT)                                                                                   \
   if (prec) {                                                                                      \
     if ((e = set_smem(k_cheb_backward_batched<float, TT>, smem)) == cudaSuccess)                   \
-      k_cheb_backward_batched<float, TT><<<nwork, Z_THREADS, smem, s>>>(ds, work);                  \
+      k_cheb_backward_batched<float, TT><<<batched_grid(k_cheb_backward_batched<float, TT>, Z_THREADS, smem, \
+                                                        nwork, queue), Z_THREADS, smem, s>>>(ds, work, nwork, queue); \
   } else {                                                                                         \
     if ((e = set_smem(k_cheb_backward_batched<double, TT>, smem)) == cudaSuccess)                  \
-      k_cheb_backward_batched<double, TT><<<nwork, Z_THREADS, smem, s>>>(ds, work);                 \
+      k_cheb_backward_batched<double, TT><<<batched_grid(k_cheb_backward_batched<double, TT>, Z_THREADS, smem, \
+                                                         nwork, queue), Z_THREADS, smem, s>>>(ds, work, nwork, queue); \
   }
   SPECTAU_TILE_DISPATCH(tile, CALL)
 #undef CALL
@@ -649,16 +673,18 @@ cudaError_t launch_cheb_backward_batched(cudaStream_t s, int prec, int tile, con
 }
 
 cudaError_t launch_cheb_forward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,
-                                        int nwork, int max_ng) {
+                                        int nwork, int max_ng, int* queue) {
   const size_t smem = z_smem_bytes(prec, max_ng, tile);
   cudaError_t e = cudaSuccess;
 #define CALL(TT)                                                                                   \
   if (prec) {                                                                                      \
     if ((e = set_smem(k_cheb_forward_batched<float, TT>, smem)) == cudaSuccess)                    \
-      k_cheb_forward_batched<float, TT><<<nwork, Z_THREADS, smem, s>>>(ds, work);                   \
+      k_cheb_forward_batched<float, TT><<<batched_grid(k_cheb_forward_batched<float, TT>, Z_THREADS, smem, \
+                                                       nwork, queue), Z_THREADS, smem, s>>>(ds, work, nwork, queue); \
   } else {                                                                                         \
     if ((e = set_smem(k_cheb_forward_batched<double, TT>, smem)) == cudaSuccess)                   \
-      k_cheb_forward_batched<double, TT><<<nwork, Z_THREADS, smem, s>>>(ds, work);                  \
+      k_cheb_forward_batched<double, TT><<<batched_grid(k_cheb_forward_batched<double, TT>, Z_THREADS, smem, \
+                                                        nwork, queue), Z_THREADS, smem, s>>>(ds, work, nwork, queue); \
   }
   SPECTAU_TILE_DISPATCH(tile, CALL)
 #undef CALL
@@ -667,14 +693,16 @@ cudaError_t launch_cheb_forward_batched(cudaStream_t s, int prec, int tile, cons
 }
 
 cudaError_t launch_fourier_rows_batched(cudaStream_t s, int prec, const XDesc* ds, const int4* work, int nwork,
-                                        size_t smem) {
+                                        size_t smem, int* queue) {
   cudaError_t e;
   if (prec) {
     if ((e = set_smem(k_fourier_rows_batched<float>, smem)) != cudaSuccess) return e;
-    k_fourier_rows_batched<float><<<nwork, X_THREADS, smem, s>>>(ds, work);
+    k_fourier_rows_batched<float><<<batched_grid(k_fourier_rows_batched<float>, X_THREADS, smem, nwork, queue),
+                                    X_THREADS, smem, s>>>(ds, work, nwork, queue);
   } else {
     if ((e = set_smem(k_fourier_rows_batched<double>, smem)) != cudaSuccess) return e;
-    k_fourier_rows_batched<double><<<nwork, X_THREADS, smem, s>>>(ds, work);
+    k_fourier_rows_batched<double><<<batched_grid(k_fourier_rows_batched<double>, X_THREADS, smem, nwork, queue),
+                                     X_THREADS, smem, s>>>(ds, work, nwork, queue);
   }
   return cudaGetLastError();
 }

@@ -214,6 +214,23 @@ class TauSolver:
         self.dt = None
         return re + 1j * im
 
+    def eig_residual(self):
+        """Relative residual ||(L~ + sigma M~) x|| / (||L~ x|| + |sigma| ||M~ x||)
+        of the last eigensolve's pair in every pencil."""
+        out = np.zeros(self.P)
+        h = self.ctx.handle
+        L.check(h, L.lib().sp_eig_residual(h, self.pid, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def eig_targets(self, targets, iters=60):
+        """Several modes per pencil: the eigenvalue nearest each target
+        ([len(targets), P]) and the residual of each pair."""
+        vals, res = [], []
+        for t in targets:
+            vals.append(self.eig_target(t, iters))
+            res.append(self.eig_residual())
+        return np.array(vals), np.array(res)
+
     def solve_work(self):
         """(multiply-adds per row and real right-hand side, factor bytes per
         pencil) of the substitution as the solve kernel performs it."""
@@ -443,3 +460,23 @@ def batch_tile(solvers):
     t = ctypes.c_int()
     L.check(ctx.handle, L.lib().sp_batch_tile(ctx.handle, n, ids, ctypes.byref(t)))
     return t.value
+
+
+def batch_persistent(solvers):
+    """True when the batch autotuner chose persistent grids for these solvers."""
+    ctx = solvers[0].ctx
+    n = len(solvers)
+    ids = (ctypes.c_int * n)(*[s.pid for s in solvers])
+    t = ctypes.c_int()
+    L.check(ctx.handle, L.lib().sp_batch_persistent(ctx.handle, n, ids, ctypes.byref(t)))
+    return bool(t.value)
+
+
+def set_batch_persistent(solvers, mode):
+    """Fix the batched launch shape: True (persistent grids), False (one CTA
+    per work item) or None (the autotuner decides)."""
+    ctx = solvers[0].ctx
+    n = len(solvers)
+    ids = (ctypes.c_int * n)(*[s.pid for s in solvers])
+    m = -1 if mode is None else int(bool(mode))
+    L.check(ctx.handle, L.lib().sp_set_batch_persistent(ctx.handle, n, ids, m))
