@@ -308,6 +308,13 @@ sp_status make_plan(sp_ctx* ctx, Problem* pr, int Nc, int Ng, TransformPlan** ou
   return SP_OK;
 }
 
+// the partitioned back substitution starts its blocks from the previous
+// solve's inflows (spike.cu); zero them
+cudaError_t reset_spike_guess(Problem* pr, cudaStream_t s) {
+  if (!pr->spike || !pr->d_sp_u) return cudaSuccess;
+  return cudaMemsetAsync(pr->d_sp_u, 0, (size_t)pr->P * pr->nblk * 2 * 32 * sizeof(double), s);
+}
+
 // Blocks per pencil of the partitioned back substitution: about 1024 / P
 // (two to four chains per GPU sub-partition with its two parts; measured at
 // 256 pencils of 1792 rows: 4 blocks 0.224 ms per solve, 7 blocks 0.254, 14
@@ -463,6 +470,7 @@ sp_status upload_problem(sp_ctx* ctx, Problem* pr) {
     CK(dalloc(&pr->d_sp_s, nvf * 8));
     CK(dalloc(&pr->d_sp_o0, nv * 32));
     CK(dalloc(&pr->d_sp_u, nv * 32));
+    CK(reset_spike_guess(pr, ctx->stream));
   }
   for (int fi = 0; fi < nfactors; ++fi) {
     BandFactor& f = pr->fac[fi];
@@ -645,19 +653,11 @@ sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
       sa.status = ctx->d_status;
       CK(launch_spike_solve(s, sa));
     }
+    // L~ X~ of a stage is the product with L~ itself: recovering it from the
+    // stage's right-hand side, (B~ - alpha M~ X~) / beta, cancels (B~ is
+    // alpha M~ X~ up to O(beta) = O(dt)) and magnifies the rounding by 1/beta
     SolveArgs a2 = a;
     a2.mode = 2; a2.xg = pr->d_xg; a2.bg = pr->d_bg;
-    if (a2.ep_mv_vals == pr->d_Lv) {
-      // L~ X~ of a stage from its own right-hand side: (B~ - alpha M~ X~) / beta
-      // with the factored alpha M~ + beta L~ (compact M~ pattern instead of L~'s)
-      int fi = 0;
-      for (int q = 1; q < 4; ++q)
-        if (a.Lf == pr->fac[q].L && pr->fac[q].L) fi = q;
-      const BandFactor& f = pr->fac[fi];
-      set_ep_M(pr, a2);
-      a2.ep_alpha = f.alpha;
-      a2.ep_from_b = 1.0 / f.beta;
-    }
     CK(launch_pencil_solve(s, a2));
   } else {
     CK(launch_pencil_solve(s, a));
@@ -1241,6 +1241,7 @@ sp_status sp_set_bilinear_rhs(sp_ctx* ctx, int problem, int nterms, const int32_
 // pencil (and, per solve kernel, the lane layout or the partitioned
 // substitution's coupling matrices); synchronous.
 static sp_status factor_matrices(sp_ctx* ctx, Problem* pr, int nf, const double (*ab)[2]) {
+  CK(reset_spike_guess(pr, ctx->stream));
   const int ldab = 2 * pr->kl + pr->ku + 1;
   double* work = nullptr;
   CK(dalloc(&work, (size_t)pr->P * pr->n * ldab));
@@ -1394,6 +1395,7 @@ sp_status sp_set_field(sp_ctx* ctx, int problem, int var, const void* data, int 
   sp_status st = upload_problem(ctx, pr);
   if (st != SP_OK) return st;
   cudaStream_t s = ctx->stream;
+  CK(reset_spike_guess(pr, s));                  // a run from a set state starts from zero inflows
   double2* dst = pr->d_Xc + (size_t)var * pr->P * pr->Nz;
   const size_t ncoef = (size_t)pr->P * pr->Nz;
   if (layout == 'c') {

@@ -156,9 +156,6 @@ struct SolveArgs {
   // (the substitution then runs in k_pencil_lanes)
   int mode;
   double2* bg; const double2* xg;
-  // epilogue (mode 2): store (B~ - ep_alpha M~X~) ep_from_b, i.e. L~X~ from the
-  // stage's own right-hand side, when ep_from_b != 0
-  double ep_from_b, ep_alpha;
   // factor in the lane-interleaved layout (null: not available)
   const double* Lg; const double* Ug; const uint8_t* pg; const unsigned long long* umask; int cmax;
   // coupling matrices of the partitioned substitution (null: not available)

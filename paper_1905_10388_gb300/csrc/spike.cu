@@ -16,6 +16,15 @@
 //      with C_k the block's coupling matrix (its response to unit inflows,
 //      computed once per factorization), gives every block's true inflow;
 //   3. every block runs again with its true inflow, giving its rows.
+// The back substitution starts step 1 from a guess g_k instead of zero
+// inflow, the true inflow of the problem's previous solve, and step 2
+// becomes inflow_{k-1} = o_k + E_k (inflow_k - g_k): exact for any guess,
+// but with zero inflow the velocity rows of a block's top (true values
+// ~1e-3 of the buoyancy's early in a run) come out O(1) and the recurrence
+// cancels them, so their rounding errors are O(1) too; consecutive solves of
+// a time step differ by O(dt), the correction is small and nothing cancels.
+// Factorization and setting a field reset the guesses to zero, and a guess
+// that is not finite reads as zero.
 // Forward substitution uses 8-lane windows (rows j .. j + 7, kl <= 7), four
 // chains per warp, over its own (finer) blocks of about 128 rows: it is
 // cheap in FP64 instructions and bound by its chain latency; back
@@ -214,17 +223,24 @@ __global__ void __launch_bounds__(128) k_spike_fwd_rec(SpikeArgs s) {
 // back substitution of one block, one CTA of two warps (real and imaginary
 // part) per block, with the scaled U columns (U_{j-t,j} / U_jj, t = 0:
 // 1/U_jj) streamed chunk by chunk into a shared-memory ring.  Lane l holds
-// the row congruent to l mod 32 of rows j - 31 .. j.  PASS 1: zero inflow,
-// writes the outflow (and x for the last block, which has no inflow);
-// PASS 2: the true inflow, writes x = y / U_jj for the block's rows.
+// the row congruent to l mod 32 of rows j - 31 .. j.  PASS 1 (blocks 1 ..
+// nblk - 1, or the one block): the guessed inflow, zero for the last
+// block, writes the outflow (and x for the last block, which has no
+// inflow); PASS 2 (blocks 0 .. nblk - 2): the true inflow, writes
+// x = y / U_jj for the block's rows.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double spike_guess(double g) { return isfinite(g) ? g : 0.0; }
+
 template <int PASS>
 __global__ void __launch_bounds__(64, 10) k_spike_bwd(SpikeArgs s) {
   __shared__ __align__(128) double Uring[SPK_RING * SPK_CHUNK * SPK_BW];
   __shared__ __align__(8) uint64_t bar[SPK_RING];
   __shared__ int abort_flag;
-  const int nk = PASS == 1 ? s.nblk : s.nblk - 1;     // PASS 2: the last block is final after PASS 1
-  const int p = blockIdx.x / nk, k = blockIdx.x - p * nk;
+  // PASS 1 skips block 0 (its outflow has no use); PASS 2 the last block,
+  // final after PASS 1
+  const int k0 = (PASS == 1 && s.nblk > 1) ? 1 : 0;
+  const int nk = s.nblk > 1 ? s.nblk - 1 : 1;
+  const int p = blockIdx.x / nk, k = k0 + (blockIdx.x - p * nk);
   const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
   const int m = s.m, j0 = k * m, j1 = j0 + m, n = s.n, kuu = s.kuu;
   const int nch = m / SPK_CHUNK, chi = j1 / SPK_CHUNK - 1;     // chunks chi, chi - 1, ..., chi - nch + 1
@@ -248,7 +264,10 @@ __global__ void __launch_bounds__(64, 10) k_spike_bwd(SpikeArgs s) {
   double w = yv(j1 - SPK_BW + lane);
   const int first_in = SPK_BW - kuu;              // lanes first_in .. 31 hold the inflow rows
   const size_t bidx = (((size_t)p * s.nblk + k) * 2 + c) * SPK_BW;
-  if (PASS == 2 && lane >= first_in) w += s.uin[bidx + lane - first_in];
+  if (lane >= first_in) {
+    if (PASS == 2) w += s.uin[bidx + lane - first_in];
+    else if (k < s.nblk - 1) w += spike_guess(s.uin[bidx + lane - first_in]);
+  }
   // lane l takes row jc - 32 + l when it owns column jc + l of the chunk
   // at jc: nw holds that row, loaded one chunk ahead
   double nw = yv(j1 - 2 * SPK_BW + lane);
@@ -302,11 +321,12 @@ __global__ void __launch_bounds__(64, 10) k_spike_bwd(SpikeArgs s) {
   if (PASS == 1 && k > 0 && lane >= first_in) s.o0[bidx + lane - first_in] = w;
 }
 
-// backward inflows: u_{nblk-2} = o0_{nblk-1} (exact), then
-// u_{k-1} = o0_k + E_k u_k; one CTA of four warps per (pencil, part): warp
-// q multiplies columns 8q .. 8q + 7 of row r = lane (four sub-partitions
-// share each step's FMAs), warp 0 adds the four partial sums.  The next
-// step's matrix entries are loaded before this step's FMAs.
+// backward inflows: u_{nblk-2} = o_{nblk-1} (exact), then
+// u_{k-1} = o_k + E_k (u_k - g_k), g_k the guess PASS 1 started block k
+// from, which u_k replaces in place; one CTA of four warps per (pencil,
+// part): warp q multiplies columns 8q .. 8q + 7 of row r = lane (four
+// sub-partitions share each step's FMAs), warp 0 adds the four partial
+// sums.  The next step's matrix entries are loaded before this step's FMAs.
 constexpr int SPK_REC_WARPS = 4;
 constexpr int SPK_REC_COLS = SPK_BW / SPK_REC_WARPS;
 __global__ void __launch_bounds__(SPK_REC_WARPS * 32) k_spike_bwd_rec(SpikeArgs s) {
@@ -319,7 +339,8 @@ __global__ void __launch_bounds__(SPK_REC_WARPS * 32) k_spike_bwd_rec(SpikeArgs 
   if (s.nblk < 2) return;
   if (wq == 0) {
     const double u = r < kuu ? s.o0[at(s.nblk - 1) + r] : 0.0;
-    ucur[r] = u;
+    const double g = (r < kuu && s.nblk > 2) ? spike_guess(s.uin[at(s.nblk - 2) + r]) : 0.0;
+    ucur[r] = u - g;                                 // u_k - g_k for the next step
     if (r < kuu) s.uin[at(s.nblk - 2) + r] = u;
   }
   double en[SPK_REC_COLS];
@@ -348,7 +369,8 @@ __global__ void __launch_bounds__(SPK_REC_WARPS * 32) k_spike_bwd_rec(SpikeArgs 
       double u = o;
 #pragma unroll
       for (int q = 0; q < SPK_REC_WARPS; ++q) u += part[q][r];
-      ucur[r] = r < kuu ? u : 0.0;
+      const double g = (r < kuu && k > 1) ? spike_guess(s.uin[at(k - 1) + r]) : 0.0;
+      ucur[r] = r < kuu ? u - g : 0.0;
       if (r < kuu) s.uin[at(k - 1) + r] = u;
     }
     __syncthreads();
@@ -372,7 +394,7 @@ cudaError_t launch_spike_solve(cudaStream_t st, const SpikeArgs& s) {
   k_spike_fwd_rec<<<(unsigned)((s.P * 2 * 32 + T - 1) / T), T, 0, st>>>(s);
   const long long lanes2 = (long long)s.P * s.nblk_f * 2 * SPK_FW;
   k_spike_fwd<2><<<(unsigned)((lanes2 + T - 1) / T), T, 0, st>>>(s);
-  k_spike_bwd<1><<<s.P * s.nblk, 64, 0, st>>>(s);
+  k_spike_bwd<1><<<s.P * (s.nblk > 1 ? s.nblk - 1 : 1), 64, 0, st>>>(s);
   if (s.nblk > 1) {
     k_spike_bwd_rec<<<s.P * 2, SPK_REC_WARPS * 32, 0, st>>>(s);
     k_spike_bwd<2><<<s.P * (s.nblk - 1), 64, 0, st>>>(s);
