@@ -11,7 +11,12 @@
 //
 // `tw` holds W_N^t = exp(-2 pi i t / N), t < N, computed on the host in FP64
 // (libm) and rounded to T.  sign = -1: forward DFT (exp(-i...)); sign = +1:
-// unnormalized inverse (exp(+i...)).
+// unnormalized inverse (exp(+i...)).  On GB300 the FP64 pipe issues one warp
+// instruction per 64 cycles per sub-partition and bounds the FP64 transforms,
+// so passes count FP64 instructions: the first pass skips its twiddles (all
+// 1), the radix-3 butterfly takes 4 per point (sums, differences and FMAs
+// with the constants -1/2 and sqrt(3)/2, instead of products with the cube
+// roots of unity), radix-8 about 10 and radix-4 7 per point.
 #pragma once
 #include "common.cuh"
 
@@ -57,11 +62,7 @@ __device__ __forceinline__ void stockham_pass(const C<T>* __restrict__ x, C<T>* 
                                               int nb) {
   const int Q = N / R;
   const int step = N / (R * Ns);
-  C<T> w1 = mk<T>(0, 0), w2 = mk<T>(0, 0);
-  if (R == 3) {
-    w1 = tw_get<T>(tw, N / 3, sign);
-    w2 = tw_get<T>(tw, 2 * (N / 3), sign);
-  }
+  const bool twiddle = Ns > 1;                     // the first pass's twiddles are all 1
   // butterflies of all nb sequences share one thread loop; the sequence of
   // butterfly idx is floor((idx + 1/2) / Q), exact in FP32 for idx < 2^20
   const float invQ = 1.0f / (float)Q;
@@ -79,16 +80,21 @@ __device__ __forceinline__ void stockham_pass(const C<T>* __restrict__ x, C<T>* 
 #pragma unroll
       for (int t = 0; t < R; ++t) {
         a[t] = xb[j + t * Q];
-        if (t > 0) a[t] = cmul<T>(a[t], tw_get<T>(tw, t * k * step, sign));
+        if (t > 0 && twiddle) a[t] = cmul<T>(a[t], tw_get<T>(tw, t * k * step, sign));
       }
       const int o = jq * R * Ns + k;
       if (R == 2) {
         yb[o] = cadd<T>(a[0], a[1]);
         yb[o + Ns] = csub<T>(a[0], a[1]);
       } else if (R == 3) {
-        yb[o] = cadd<T>(a[0], cadd<T>(a[1], a[2]));
-        yb[o + Ns] = cadd<T>(a[0], cadd<T>(cmul<T>(w1, a[1]), cmul<T>(w2, a[2])));
-        yb[o + 2 * Ns] = cadd<T>(a[0], cadd<T>(cmul<T>(w2, a[1]), cmul<T>(w1, a[2])));
+        // root w = exp(sign 2 pi i / 3) = -1/2 + sign i sqrt(3)/2:
+        // X_0 = a0 + (a1 + a2), X_{1,2} = a0 - (a1 + a2)/2 +- sign i (sqrt(3)/2) (a1 - a2)
+        const T c = (sign < 0 ? (T)-1 : (T)1) * (T)0.86602540378443864676;
+        const C<T> s12 = cadd<T>(a[1], a[2]), d12 = csub<T>(a[1], a[2]);
+        const C<T> m = mk<T>(fma((T)-0.5, s12.x, a[0].x), fma((T)-0.5, s12.y, a[0].y));
+        yb[o] = cadd<T>(a[0], s12);
+        yb[o + Ns] = mk<T>(fma(-c, d12.y, m.x), fma(c, d12.x, m.y));
+        yb[o + 2 * Ns] = mk<T>(fma(c, d12.y, m.x), fma(-c, d12.x, m.y));
       } else if (R == 4) {
         C<T> d[4];
         dft4<T>(a[0], a[1], a[2], a[3], sign, d);
