@@ -204,6 +204,7 @@ struct XDesc {
   const float* t_coef32;
   const void* hin; void* gzadj;             // adjoint rows: inputs / outputs
   int xscale;                                // bit 1: transpose of forward x on input; bit 2: of backward x on output
+  int pairs;                                 // field pairs per backward FFT round (0: two)
 };
 
 // Complex Fourier y transform of nf x nz planes of N_y slots x K columns.
@@ -274,7 +275,7 @@ cudaError_t launch_cfl_max(cudaStream_t s, const double* grid, int nvel, const i
 cudaError_t launch_fourier_y(cudaStream_t s, int prec, const TransformPlan& py, int dir, int nf, int nz, int K,
                              const void* src, void* dst);
 size_t z_smem_bytes(int prec, int Ng, int tile);
-size_t x_smem_bytes(int prec, int N, int mode, int nf, int ne);
+size_t x_smem_bytes(int prec, int N, int mode, int nf, int ne, int pairs = 0);
 // batched transforms: queue null: one CTA per work item; else a persistent
 // grid pulling items from the device counter *queue (zero before the launch)
 cudaError_t launch_cheb_backward_batched(cudaStream_t s, int prec, int tile, const ZDesc* ds, const int4* work,

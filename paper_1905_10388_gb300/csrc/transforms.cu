@@ -133,10 +133,14 @@ __device__ __forceinline__ void cheb_forward_body(const ZDesc& d, int bx, int e,
 //   mode & 2: evaluate the bilinear terms (else pass the fields through)
 //   mode & 4: output spectra to h (else real rows to grid_out)
 // ---------------------------------------------------------------------------
-// Field pairs transformed at once in the x-row kernel: the FFT buffers hold
-// this many pairs, so many-field rows (3D: 15 fields) keep shared memory low
-// enough for several CTAs per SM.
+// Field pairs transformed at once in the x-row kernel by default: the FFT
+// buffers hold this many pairs, so many-field rows (3D: 15 fields) keep
+// shared memory low enough for several CTAs per SM.  The one-problem FP64
+// launch takes every pair in one round instead (XDesc::pairs): its FP64
+// passes, not shared memory, bound it, and one round of five pairs gives the
+// radix-8 passes 480 butterflies for 512 threads with three fewer barriers.
 constexpr int X_PAIRS = 2;
+constexpr int X_THREADS_FP64 = 512;
 
 template <typename T>
 __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsigned char* smem_raw) {
@@ -144,7 +148,8 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
   const float invN = 1.0f / (float)N, invK = 1.0f / (float)K;
   const int nout = (mode & 2) ? ne : nf;
   const int nbi = (nf + 1) / 2, nbo = (nout + 1) / 2;
-  const int nbmax = max(min(nbi, X_PAIRS), nbo);
+  const int xp = d.pairs > 0 ? d.pairs : X_PAIRS;
+  const int nbmax = max(min(nbi, xp), nbo);
   C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
   C<T>* b1 = b0 + (size_t)nbmax * N;
   C<T>* tws = b1 + (size_t)nbmax * N;
@@ -156,8 +161,8 @@ __device__ __forceinline__ void fourier_rows_body(const XDesc& d, int row, unsig
   const int tid = threadIdx.x, nt = blockDim.x;
 
   if (mode & 1) {
-   for (int q0 = 0; q0 < nbi; q0 += X_PAIRS) {
-    const int nb = min(X_PAIRS, nbi - q0);
+   for (int q0 = 0; q0 < nbi; q0 += xp) {
+    const int nb = min(xp, nbi - q0);
     for (int idx = tid; idx < nb * N; idx += nt) {
       const int qq = div_idx(idx, invN);
       const int q = q0 + qq, k = idx - qq * N;
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(Z_THREADS) k_fourier_y(YDesc d) {
   fourier_y_body<T, Y_TILE>(d, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 template <typename T>
-__global__ void __launch_bounds__(X_THREADS) k_fourier_rows(XDesc d) {
+__global__ void __launch_bounds__(X_THREADS_FP64) k_fourier_rows(XDesc d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fourier_rows_body<T>(d, blockIdx.x, smem_raw);
 }
@@ -505,9 +510,9 @@ __global__ void __launch_bounds__(X_THREADS) k_fourier_rows_batched(const XDesc*
 size_t z_smem_bytes(int prec, int Ng, int tile) {
   return (2ull * tile + 1) * Ng * (prec ? sizeof(float2) : sizeof(double2));
 }
-size_t x_smem_bytes(int prec, int N, int mode, int nf, int ne) {
+size_t x_smem_bytes(int prec, int N, int mode, int nf, int ne, int pairs) {
   const int nout = (mode & 2) ? ne : nf;
-  const int nbmax = std::max(std::min((nf + 1) / 2, X_PAIRS), (nout + 1) / 2);
+  const int nbmax = std::max(std::min((nf + 1) / 2, pairs > 0 ? pairs : X_PAIRS), (nout + 1) / 2);
   const size_t esz = prec ? sizeof(float) : sizeof(double);
   size_t smem = (2ull * nbmax + 1) * N * 2 * esz + (size_t)nf * N * esz;
   if (mode & 2) smem += (size_t)ne * N * esz;
@@ -602,14 +607,17 @@ cudaError_t launch_fourier_rows(cudaStream_t s, int prec, const TransformPlan& p
   d.nterms = nterms; d.t_eq = t_eq; d.t_coef = t_coef; d.t_fa = t_fa; d.t_fb = t_fb; d.ne = ne; d.h = h;
   d.t_coef32 = t_coef32;
   if (prec && nterms > 0 && !t_coef32) return cudaErrorInvalidValue;
-  const size_t smem = x_smem_bytes(prec, px.Ng, mode, nf, ne);
+  if (!prec)   // FP64: as many pairs per round as shared memory holds
+    for (int q = (nf + 1) / 2; q > X_PAIRS && !d.pairs; --q)
+      if (x_smem_bytes(prec, px.Ng, mode, nf, ne, q) <= 227 * 1024) d.pairs = q;
+  const size_t smem = x_smem_bytes(prec, px.Ng, mode, nf, ne, d.pairs);
   cudaError_t e;
   if (prec) {
     if ((e = set_smem(k_fourier_rows<float>, smem)) != cudaSuccess) return e;
     k_fourier_rows<float><<<rows, X_THREADS, smem, s>>>(d);
   } else {
     if ((e = set_smem(k_fourier_rows<double>, smem)) != cudaSuccess) return e;
-    k_fourier_rows<double><<<rows, X_THREADS, smem, s>>>(d);
+    k_fourier_rows<double><<<rows, X_THREADS_FP64, smem, s>>>(d);
   }
   return cudaGetLastError();
 }
