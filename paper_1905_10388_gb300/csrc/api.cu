@@ -653,11 +653,27 @@ sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
       sa.status = ctx->d_status;
       CK(launch_spike_solve(s, sa));
     }
-    // L~ X~ of a stage is the product with L~ itself: recovering it from the
-    // stage's right-hand side, (B~ - alpha M~ X~) / beta, cancels (B~ is
-    // alpha M~ X~ up to O(beta) = O(dt)) and magnifies the rounding by 1/beta
     SolveArgs a2 = a;
     a2.mode = 2; a2.xg = pr->d_xg; a2.bg = pr->d_bg;
+    if (a2.ep_mv_vals == pr->d_Lv && pr->prec) {
+      // L~ X~ of a stage.  FP64 form: the product with L~ itself.  Mixed
+      // form: from the stage's own right-hand side, (B~ - alpha M~ X~) / beta
+      // with the factored alpha M~ + beta L~, M~'s compact pattern instead of
+      // L~'s (3D: 1508 against 6073 entries per pencil, ~0.5 ms of FP64 pipe
+      // per stage at 256 x 256 x 128).  B~ is alpha M~ X~ up to O(beta), so
+      // the difference cancels; the error it leaves in a later stage's
+      // right-hand side, dt a_ij L~X~ = (a_ij / a_jj)(B~ - alpha M~ X~), is a
+      // few FP64 roundings of M~X~, far below the FP32 transforms' 1e-7 but
+      // above the FP64 form's own rounding (the 500-step RK222 adjoint
+      // gradient drifts 15x past the oracle floor), hence FP64 keeps L~.
+      int fi = 0;
+      for (int q = 1; q < 4; ++q)
+        if (a.Lf == pr->fac[q].L && pr->fac[q].L) fi = q;
+      const BandFactor& f = pr->fac[fi];
+      set_ep_M(pr, a2);
+      a2.ep_alpha = f.alpha;
+      a2.ep_from_b = 1.0 / f.beta;
+    }
     CK(launch_pencil_solve(s, a2));
   } else {
     CK(launch_pencil_solve(s, a));

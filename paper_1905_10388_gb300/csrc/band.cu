@@ -560,9 +560,18 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     const double* vals = a.ep_mv_vals + (size_t)p * a.ep_nnz;
     const bool listed = a.ep_rows != nullptr;
     if (listed) {
-      // rows without entries first (zero), then the listed rows with every
-      // lane on a row that has entries; the barrier orders the two stores
-      for (int r = tid; work && r < n; r += nt) a.ep_mv_store[prow + r] = make_double2(0.0, 0.0);
+      // rows without entries first (zero, or B~/beta for L~X~ from the
+      // stage right-hand side), then the listed rows with every lane on a
+      // row that has entries; the barrier orders the two stores of a row
+      for (int r = tid; work && r < n; r += nt) {
+        double2 s = make_double2(0.0, 0.0);
+        if (mode == 2 && a.ep_from_b != 0.0) {
+          const double2 bb = a.bg[prow + r];
+          s.x = bb.x * a.ep_from_b;
+          s.y = bb.y * a.ep_from_b;
+        }
+        a.ep_mv_store[prow + r] = s;
+      }
       __syncthreads();
     }
     const int nrows = listed ? a.ep_nrows : n;
@@ -579,6 +588,12 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
         }
         s.x = fma(m, x.x, s.x);
         s.y = fma(m, x.y, s.y);
+      }
+      if (mode == 2 && a.ep_from_b != 0.0) {
+        // L~ X~ = (B~ - alpha M~ X~) / beta for the stage matrix alpha M~ + beta L~
+        const double2 bb = a.bg[prow + r];
+        s.x = (bb.x - a.ep_alpha * s.x) * a.ep_from_b;
+        s.y = (bb.y - a.ep_alpha * s.y) * a.ep_from_b;
       }
       a.ep_mv_store[prow + r] = s;
     }

@@ -140,6 +140,9 @@ struct SolveArgs {
   double2* xt_out; double2* xc_out; float2* xc32_out;   // xc32_out: FP32 copy (mixed precision)
   float* xs32_out;                             // split FP32 copy [var][2p + c][m] (tensor-core z transform)
   const double* ep_mv_vals; double2* ep_mv_store;
+  // epilogue (mode 2): store (B~ - ep_alpha M~X~) ep_from_b, i.e. L~X~ from the
+  // stage's own right-hand side, when ep_from_b != 0 (mixed precision only)
+  double ep_from_b, ep_alpha;
   const double2* ep_mv_addvec;                 // epilogue matvec acts on (X~ + addvec) if set
   const int32_t* ep_indptr; const int32_t* ep_indices; int ep_nnz;    // pattern of ep_mv_vals
   const int32_t* ep_rows; int ep_nrows;   // the pattern's non-empty rows (M~), or null: every row
