@@ -57,15 +57,18 @@ def measured_peaks():
 STAGES = {"RK222": 2, "RK443": 4, "RK111": 1, "SBDF1": 1, "SBDF2": 1, "SBDF3": 1, "SBDF4": 1}
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# k_pencil_solve launch of the 512x256 SBDF2 mixed-precision step, from one
-# ncu capture of `bench.py --steps 3 --warmup 3 --no-cpu-baseline`
-# (metrics dram__bytes_read.sum, dram__bytes_write.sum, one launch).  It is
-# reported only while the kernel's sources hash to the captured ones.
-SOLVE_TRAFFIC = {"workload": "rb2d_512x256_sbdf2", "precision": "mixed", "bytes": 179.707904e6,
-                 "sources_sha256": "2a8f4afefffb64c033833b3598be4e82cb29ebddf9245b16673f0fbd52cddac3"}
-SOLVE_SOURCES = ("paper_1905_10388_gb300/csrc/band.cu", "paper_1905_10388_gb300/csrc/internal.h",
-                 "paper_1905_10388_gb300/csrc/common.cuh")
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one pencil
+# solve of the 512x256 SBDF2 FP64 step, summed over its eight launches
+# (assembly, partitioned substitution, epilogue), from one ncu capture of
+# `bench.py --precision fp64 --no-cpu-baseline --no-error --steps 3 --warmup 3`
+# (metrics gpu__time_duration.sum, dram__bytes_read.sum, dram__bytes_write.sum;
+# -k regex:"k_spike|k_pencil_stage_wide" -s 16 -c 8).  It is reported only
+# while the kernels' sources hash to the captured ones.
+SOLVE_TRAFFIC = {"workload": "rb2d_512x256_sbdf2", "precision": "fp64", "bytes": 306.291456e6,
+                 "sources_sha256": "f55f3b5561b4e81a32482121d5d919a511b70a554c8f58d19d13dfc9413237d6"}
+SOLVE_SOURCES = ("paper_1905_10388_gb300/csrc/band.cu", "paper_1905_10388_gb300/csrc/spike.cu",
+                 "paper_1905_10388_gb300/csrc/internal.h", "paper_1905_10388_gb300/csrc/common.cuh",
+                 "paper_1905_10388_gb300/csrc/tma.cuh")
 
 
 def solve_traffic(workload, precision):
@@ -170,7 +173,7 @@ def solve_flops_bytes(s):
     return flops, factor_bytes + vec_bytes
 
 
-def _make_solver(ctx, w, precision, rank):
+def _make_solver(ctx, w, precision, rank, z_transform=None):
     from paper_1905_10388_gb300.solver import FisherKPPSolver, RB3DSolver, RBSolver
     if isinstance(w, si.FisherWorkload):
         s = FisherKPPSolver(ctx, w.n_x, w.n_z, w.D, w.R, w.L_x, scheme=w.scheme, precision=precision)
@@ -181,6 +184,8 @@ def _make_solver(ctx, w, precision, rank):
     else:
         s = RBSolver(ctx, w.n_x, w.n_z, w.Ra, w.Pr, w.L_x, scheme=w.scheme, precision=precision)
         xi = si.rb_noise(w.seed + rank, w.n_z, w.n_x)
+    if z_transform:
+        s.set_z_transform(z_transform)
     s.factor(w.dt)
     s.set_initial_state(xi)
     return s, xi
@@ -259,6 +264,55 @@ def field_errors(s, X_ref, xi, nsteps):
     return out
 
 
+def z_path_times(local, w, rank, stream, nsteps=6):
+    """3D mixed form: ms per step with the Chebyshev backward transform as the
+    FFT-based DCT and as the tensor-core matrix product, each on a solver and
+    context of its own (CUDA-graph steps after a rehearsal; outside every
+    timed region)."""
+    import torch
+    from paper_1905_10388_gb300.solver import Context
+    out = {}
+    for kind in ("fft", "mma"):
+        c = Context(local, stream.cuda_stream)
+        try:
+            s, _ = _make_solver(c, w, "mixed", rank, z_transform=kind)
+            s.step(nsteps, graph=True)
+            s.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s.step(nsteps, graph=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[f"{kind}_ms_per_step"] = e0.elapsed_time(e1) / nsteps
+        finally:
+            c.close()
+    out["faster"] = min(("fft", "mma"), key=lambda k: out[f"{k}_ms_per_step"])
+    out["steps"] = nsteps
+    return out
+
+
+def stored_3d_errors(s, xi):
+    """Per-field error of one step from the seeded state against the stored
+    FP64 oracle reference of the 3D workload (written by
+    tests/golden/make_references.py from the oracle alone), on its sampled
+    pencils; None when that file is absent."""
+    path = os.path.join(ROOT, "tests", "golden", "ref_rb3d_256x256x128_rk222_1.npz")
+    if not os.path.exists(path):
+        return None
+    R = np.load(path)
+    s.set_initial_state(xi)
+    s.step(1)
+    s.sync()
+    got = s.get_state()[:, R["pencils"], :]
+    out = {}
+    for i, name in enumerate(R["names"]):
+        nr = float(np.linalg.norm(R["ref"][i]))
+        d = float(np.linalg.norm(got[i] - R["ref"][i]))
+        out[str(name)] = d if nr < 1e-30 else d / nr
+    return out
+
+
 def run_ours(args):
     import torch
     distributed = int(os.environ.get("WORLD_SIZE", "1")) > 1
@@ -288,7 +342,8 @@ def run_ours(args):
     timed = {}
     solvers = {}
     for prec in forms:
-        s, xi = _make_solver(ctx, w, prec, rank)
+        zt = args.z_transform if (prec == "mixed" and args.z_transform != "auto") else None
+        s, xi = _make_solver(ctx, w, prec, rank, z_transform=zt)
         timed[prec] = _time_form(s, args, stages, stream, distributed)
         solvers[prec] = s
     clk = clocks.stop()
@@ -318,11 +373,23 @@ def run_ours(args):
     # per-field error against the FP64 oracle (outside every timed region)
     errors = {}
     err_steps = None
+    err_vs = "FP64 oracle, same seeded initial state"
     if rank == 0 and w.n_y == 1 and not args.no_error:
         err_steps = error_steps(w)
         X_ref = oracle_states(w, xi, err_steps)
         for prec in forms:
             errors[prec] = field_errors(solvers[prec], X_ref, xi, err_steps)
+    elif rank == 0 and args.workload == "rb3d_256x256x128_rk222" and not args.no_error:
+        err_steps = 1
+        err_vs = "stored FP64 oracle reference of one step from the same seeded state, 64 sampled pencils"
+        for prec in forms:
+            e = stored_3d_errors(solvers[prec], xi)
+            if e is not None:
+                errors[prec] = e
+    z_paths = None
+    if rank == 0 and w.n_y > 1 and "mixed" in forms and not args.no_z_compare:
+        z_paths = dict({"timed_path": solvers["mixed"].z_transform()},
+                       **z_path_times(local, w, rank, stream))
 
     flops, nbytes = solve_flops_bytes(s)
     n_, kl_, ku_ = s.band()
@@ -372,7 +439,7 @@ def run_ours(args):
                               "l2": (f"working set > L2 (factor {factor_mb:.0f} MB read every solve)"
                                      if factor_mb > 129 else
                                      f"L2-resident (factor {factor_mb:.0f} MB < 129 MB L2; no flush)")}),
-            "error": ({"vs": "FP64 oracle, same seeded initial state", "steps": err_steps,
+            "error": ({"vs": err_vs, "steps": err_steps,
                        "norm": "per field ||x_gpu - x_ref||_2 / ||x_ref||_2 over the coefficients",
                        "fields": errors.get(head), "max": max(errors[head].values())}
                       if head in errors else None),
@@ -383,6 +450,8 @@ def run_ours(args):
             "gpu_launches": launches * len(forms),
             "clocks": clk,
         }
+        if z_paths is not None:
+            result["z_backward"] = z_paths
         for prec in forms[1:]:
             ms2, eager2, solve2, _ = timed[prec]
             result[prec] = {
@@ -753,6 +822,10 @@ def main():
     ap.add_argument("--no-error", action="store_true", help="skip the per-field error check against the oracle")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--z-transform", default="auto", choices=["auto", "fft", "mma"],
+                    help="mixed form: Chebyshev backward path of the timed solver (default: the library's choice)")
+    ap.add_argument("--no-z-compare", action="store_true",
+                    help="3D: skip timing the FFT and tensor-core Chebyshev backward paths side by side")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 500 if args.workload.endswith("_adjoint") else 200

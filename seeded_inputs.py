@@ -94,6 +94,11 @@ WORKLOADS = {
     # Chebyshev modes (about 2.5 GB on the device instead of about 25 GB)
     "rb3d_256x256x16_rk222": RBWorkload("rb3d_256x256x16_rk222", 256, 16, 1e7,
                                         scheme="RK222", dt=5e-4, steps=200, n_y=256),
+    # profiling case of the 3D z transforms: 128 Chebyshev modes (N_gz = 192,
+    # the tensor-core path's size) on 64 x 64 Fourier modes, 2048 pencils
+    # (about 1.6 GB on the device)
+    "rb3d_64x64x128_rk222": RBWorkload("rb3d_64x64x128_rk222", 64, 128, 1e7,
+                                       scheme="RK222", dt=5e-4, steps=200, n_y=64),
 }
 
 
