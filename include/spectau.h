@@ -384,14 +384,19 @@ sp_status sp_set_solve_kernel(sp_ctx* ctx, int problem, int kind);
 
 /* Partitioned substitution (SP_SOLVE_SPIKE; Sec. "Matrix solvers": the
  * pencil solves are O(n) with the stored factor).  With fewer pencils than
- * the GPU has dependent-chain slots, each pencil's rows are cut into nblk
- * blocks of whole 32-row chunks, substituted in parallel: a zero-inflow pass
- * per block, a recurrence over blocks with coupling matrices computed at
+ * the GPU has dependent-chain slots, each pencil's back substitution is cut
+ * into nblk blocks of whole 32-row chunks (the forward one into blocks of
+ * about 128 rows), substituted in parallel: a pass per block from guessed
+ * inflows, a recurrence over blocks with coupling matrices computed at
  * sp_factor (kl x kl forward, (kl+ku) x (kl+ku) backward per block), then a
- * pass with the true inflows.  Results equal the whole-row-order
+ * pass with the true inflows.  The back substitution's guesses are the true
+ * inflows of the problem's previous solve (zero after sp_factor or
+ * sp_set_field, and for a guess that is not finite): exact for any guess,
+ * and consecutive time-step solves then correct by small differences, so no
+ * rounding is amplified by cancellation.  Results equal the whole-row-order
  * substitution to rounding.  SP_SOLVE_AUTO picks it for 2D problems with
  * fewer than 608 pencils of at least 512 rows when kl <= 7 and kl + ku <= 31.
- * sp_set_spike_blocks sets nblk (0: automatic, blocks of about 256 rows);
+ * sp_set_spike_blocks sets nblk (0: automatic, about 1024 / P blocks);
  * SP_ERR_ARG if the padded rows do not split into nblk whole 32-row chunks,
  * SP_ERR_STATE once the problem is on the device (like sp_set_solve_kernel).
  * sp_get_spike_blocks returns the block count in use (0: not partitioned,

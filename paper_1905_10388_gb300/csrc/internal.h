@@ -14,7 +14,7 @@ namespace spectau {
 // Column chunk streamed per bulk copy by the pencil-solve kernel, and the
 // ring depth.  Factor arrays are padded to a multiple of SOLVE_CHUNK columns.
 constexpr int SOLVE_CHUNK = 32;
-constexpr int SOLVE_RING = 4;
+constexpr int SOLVE_RING = 2;
 
 // Banded LU factors of one matrix a*M~ + b*L~ for all pencils.
 struct BandFactor {
