@@ -483,8 +483,11 @@ __global__ void __launch_bounds__(Z_THREADS) k_fourier_y(YDesc d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fourier_y_body<T, Y_TILE>(d, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
+// FP32: 48 registers, so that five 256-thread CTAs fit an SM (the 3D rows'
+// ~45 KB of shared memory allows five); FP64: 512 threads, 64 registers
 template <typename T>
-__global__ void __launch_bounds__(X_THREADS_FP64) k_fourier_rows(XDesc d) {
+__global__ void __launch_bounds__(sizeof(T) == 8 ? X_THREADS_FP64 : X_THREADS, sizeof(T) == 8 ? 2 : 5)
+    k_fourier_rows(XDesc d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fourier_rows_body<T>(d, blockIdx.x, smem_raw);
 }
