@@ -194,6 +194,7 @@ struct Problem {
   int spike_blocks = 0;                      // requested (0: automatic)
   int nblk = 0, nblk_f = 0;
   double *d_sp_s0 = nullptr, *d_sp_s = nullptr, *d_sp_o0 = nullptr, *d_sp_u = nullptr;
+  double* d_spT_u = nullptr;                 // inflow guesses of the transposed solves
   std::map<std::pair<int, int>, TransformPlan> plans;
   // stepping state
   int iteration = 0;
@@ -511,7 +512,7 @@ void free_problem(Problem* pr) {
   F(pr->d_sp_s0); F(pr->d_sp_s); F(pr->d_sp_o0); F(pr->d_sp_u);
   cheb_mma_free(pr->cm);
   F(pr->d_lb_F); F(pr->d_lb_eq); F(pr->d_eigx); F(pr->d_eigsig);
-  F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd);
+  F(pr->facT.L); F(pr->facT.piv); F(pr->facT.U); F(pr->facT.rd); F(pr->facT.spE); F(pr->d_spT_u);
   F(pr->d_indptrT); F(pr->d_indicesT); F(pr->d_MvT); F(pr->d_LvT);
   F(pr->d_mu[0]); F(pr->d_mu[1]); F(pr->d_LTmu); F(pr->d_MTmu); F(pr->d_JF); F(pr->d_lamx);
   F(pr->d_Xbar); F(pr->d_Fbar); F(pr->d_Fbar32); F(pr->d_gzadj);
@@ -634,6 +635,31 @@ void set_ep_L(Problem* pr, SolveArgs& a) {
 sp_status solve(sp_ctx* ctx, Problem* pr, cudaStream_t s, const SolveArgs& a) {
   const bool t = pr->timing && pr->ev_used + 2 <= pr->ev.size();
   if (t) CK(cudaEventRecord(pr->ev[pr->ev_used], s));
+  if (pr->spike && a.Lf && a.Lf == pr->facT.L && pr->facT.spE && pr->d_spT_u) {
+    // transposed solve: assembly and whole-row forward substitution (mode 3),
+    // partitioned back substitution from the last transposed solve's inflows,
+    // epilogue
+    SolveArgs a3 = a;
+    a3.mode = 3; a3.yg = pr->d_yg;
+    CK(launch_pencil_solve(s, a3));
+    SpikeArgs sa{};
+    sa.P = pr->P; sa.n = pr->n; sa.npad = pr->npad; sa.kl = a.kl; sa.kuu = a.kuu; sa.lpad = a.lpad;
+    sa.upad = a.upad; sa.nblk = pr->nblk; sa.m = pr->npad / pr->nblk;
+    sa.nblk_f = pr->nblk_f; sa.m_f = pr->npad / pr->nblk_f;
+    sa.U = a.Uf; sa.rd = a.rd; sa.E = pr->facT.spE;
+    sa.yg = pr->d_yg; sa.xg = pr->d_xg;
+    sa.o0 = pr->d_sp_o0; sa.uin = pr->d_spT_u;
+    sa.status = ctx->d_status;
+    CK(launch_spike_backward(s, sa));
+    SolveArgs a2 = a;
+    a2.mode = 2; a2.xg = pr->d_xg; a2.bg = pr->d_bg;
+    CK(launch_pencil_solve(s, a2));
+    if (t) {
+      CK(cudaEventRecord(pr->ev[pr->ev_used + 1], s));
+      pr->ev_used += 2;
+    }
+    return SP_OK;
+  }
   if ((a.Lg && pr->lanes) || (a.spD && pr->spike)) {
     // assembly -> lane-per-pencil or partitioned substitution -> epilogue
     SolveArgs a1 = a;
@@ -1845,6 +1871,17 @@ sp_status sp_adjoint_init(sp_ctx* ctx, int problem) {
   CK(e);
   pr->facT.alpha = pr->fac[0].alpha;
   pr->facT.beta = pr->fac[0].beta;
+  // the transposed solves' back substitution is partitioned like the forward
+  // solves' (kl' + ku' = kl + ku); their forward substitution stays whole-row,
+  // since kl' = ku is wider than the partitioned forward windows
+  const int kuuT = pr->klT + pr->kuT;
+  if (pr->spike && pr->upad == 32 && spike_bwd_supported(kuuT, pr->npad, pr->nblk)) {
+    if (!pr->facT.spE) CK(dalloc(&pr->facT.spE, (size_t)pr->P * pr->nblk * kuuT * 32));
+    if (!pr->d_spT_u) CK(dalloc(&pr->d_spT_u, (size_t)pr->P * pr->nblk * 2 * 32));
+    CK(cudaMemsetAsync(pr->d_spT_u, 0, (size_t)pr->P * pr->nblk * 2 * 32 * sizeof(double), s));
+    CK(launch_spike_coupling_bwd(s, pr->P, pr->npad, pr->nblk, kuuT, pr->upad, pr->facT.U, pr->facT.spE));
+    CK(cudaStreamSynchronize(s));
+  }
   return SP_OK;
 }
 

@@ -259,7 +259,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   // MODE >= 0 fixes the stage at compile time (assembly-only and
   // epilogue-only kernels carry neither the factor ring nor the substitution)
   const int mode = MODE >= 0 ? MODE : a.mode;
-  const int lp = mode == 0 ? a.lpad : 0, up = mode == 0 ? a.upad : 0;
+  const int lp = (mode == 0 || mode == 3) ? a.lpad : 0, up = mode == 0 ? a.upad : 0;
   const int half = (PPC == 2) ? (int)(threadIdx.x / (NT / 2)) : 0;
   const int p = block * PPC + half;
   const bool active = p < a.P;
@@ -306,15 +306,17 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
 
   if (tid == 0 && active) {
     *sm.abort_flag = 0;
-    if (mode == 0) {
+    if (mode == 0 || mode == 3) {
       for (int s = 0; s < SOLVE_RING; ++s) {
         mbar_init(&sm.barL[s], 1);
         mbar_init(&sm.barU[s], 1);
       }
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       // the factor does not depend on the prologue: start streaming now
+      // (mode 3, forward substitution only: L alone)
       for (int c = 0; c < min(SOLVE_RING, nchunks); ++c) issue_L(c);
-      for (int k = 0; k < min(SOLVE_RING, nchunks); ++k) issue_U(k);
+      if (mode == 0)
+        for (int k = 0; k < min(SOLVE_RING, nchunks); ++k) issue_U(k);
     }
   }
 
@@ -410,7 +412,7 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
   //      Both warps read each ring slot; named barrier 1 (64 threads) at the
   //      top of every chunk both agrees on a timed-out wait and frees the
   //      previous slot for refilling.
-  if (mode == 0 && active && tid < 64) {
+  if ((mode == 0 || mode == 3) && active && tid < 64) {
     const int lane = tid & 31;
     const int comp = tid >> 5;                 // 0: real part, 1: imaginary part
     double* Bd = reinterpret_cast<double*>(sm.B) + comp;   // element j at Bd[2 j]
@@ -464,6 +466,8 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
     }
     // backward: scaled U columns (U_{j-t,j}/U_jj), window of 32*RU entries;
     // x_j = b_j / U_jj is applied once per chunk, lane l to row j0 + l
+    // (mode 3 stops after the forward pass: y is in B)
+    if (mode == 0) {
     constexpr int W = 32 * RU;
     const double* rdp = a.rd + (size_t)pp * a.npad;
     const int npad = a.npad;
@@ -518,18 +522,24 @@ __device__ __forceinline__ void pencil_solve_body(const SolveArgs& a, int block,
       }
       Bd[2 * (j0 + lane)] = xo * rdl;
     }
+    }
     if (!ok && tid == 0) {
       // report, then let every copy in flight land before the CTA exits
       raise_status(a.status, SP_ERR_TIMEOUT, p);
       // chunks issued: RING up front, then chunk q - 1 + RING at the top of chunk q
       const int issL = min(nchunks, doneL == 0 ? SOLVE_RING : doneL - 1 + SOLVE_RING);
-      const int issU = min(nchunks, doneU == 0 ? SOLVE_RING : doneU - 1 + SOLVE_RING);
+      const int issU = mode == 0 ? min(nchunks, doneU == 0 ? SOLVE_RING : doneU - 1 + SOLVE_RING) : 0;
       for (int q = doneL; q < issL; ++q) bounded_wait(&sm.barL[q % SOLVE_RING], (q / SOLVE_RING) & 1);
       for (int q = doneU; q < issU; ++q) bounded_wait(&sm.barU[q % SOLVE_RING], (q / SOLVE_RING) & 1);
     }
   }
   __syncthreads();
   const bool work = active && !*sm.abort_flag;
+  if (mode == 3) {
+    // y = L^-1 P B~ for the partitioned back substitution
+    for (int r = tid; work && r < n; r += nt) a.yg[prow + r] = sm.B[r];
+    return;
+  }
 
   // ---- epilogue: store X~, recombine to T coefficients, optional M~ X~
   bool finite = true;
@@ -1129,7 +1139,7 @@ cudaError_t launch_adj_gather(cudaStream_t s, int P, int Nz, int Ng, int n, int 
   VecList4 vl{};
   vl.n = nvec;
   for (int k = 0; k < nvec; ++k) { vl.p[k] = vecs[k]; vl.c[k] = coefs[k]; }
-  k_adj_gather<<<P, 128, 0, s>>>(P, Nz, Ng, n, nslot, nl_eq, row_map, eq_diff, eq_phase, vl, fbar, fbar32);
+  k_adj_gather<<<P, 256, 0, s>>>(P, Nz, Ng, n, nslot, nl_eq, row_map, eq_diff, eq_phase, vl, fbar, fbar32);
   return cudaGetLastError();
 }
 
@@ -1184,31 +1194,60 @@ cudaError_t launch_adj_combine(cudaStream_t s, int P, int Nz, int S, int n, int 
   VecList4 al{};
   al.n = nadd;
   for (int k = 0; k < nadd; ++k) { al.p[k] = adds[k]; al.c[k] = add_coefs[k]; }
-  k_adj_combine<<<P, 128, 0, s>>>(P, Nz, S, n, nf, f_var, f_op, kx, xbar, col_map, var_rec, var_phase, al, out);
+  k_adj_combine<<<P, 512, 0, s>>>(P, Nz, S, n, nf, f_var, f_op, kx, xbar, col_map, var_rec, var_phase, al, out);
   return cudaGetLastError();
 }
 
-// Inverse of the transposed change of variables: Xb_v[m] = i^{q_v} xt[col(v, m)] + rec_v Xb_v[m-2]
-__global__ void k_adj_tinvh(int P, int Nz, int S, int n, const double2* __restrict__ xt,
-                            const int32_t* __restrict__ col_map, const int32_t* __restrict__ var_rec,
-                            const int32_t* __restrict__ var_phase, double2* __restrict__ out) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= P * S) return;
-  const int v = idx / P, p = idx - v * P;
-  double2 m1 = make_double2(0.0, 0.0), m2 = make_double2(0.0, 0.0);   // Xb[m-1], Xb[m-2]
-  for (int m = 0; m < Nz; ++m) {
-    double2 y = cipow_d(xt[(size_t)p * n + col_map[v * Nz + m]], var_phase[v]);
-    if (var_rec[v]) { y.x += m2.x; y.y += m2.y; }
-    out[((size_t)v * P + p) * Nz + m] = y;
-    m2 = m1;
-    m1 = y;
+// Inverse of the transposed change of variables: Xb_v[m] = i^{q_v} xt[col(v, m)] + rec_v Xb_v[m-2].
+// With recombination Xb_v[m] is the sum of the y[j] = i^{q_v} xt[col(v, j)]
+// with j <= m of the parity of m.  One warp per (variable, pencil): lane l
+// takes modes 64c + 2l (even) and 64c + 2l + 1 (odd) of chunk c, one
+// inclusive warp scan per parity adds them up, and the scans' last lane
+// carries into the next chunk (a thread per row walking its modes in order
+// left the launch waiting on one dependent load chain per row).
+__global__ void __launch_bounds__(256) k_adj_tinvh(int P, int Nz, int S, int n, const double2* __restrict__ xt,
+                                                   const int32_t* __restrict__ col_map,
+                                                   const int32_t* __restrict__ var_rec,
+                                                   const int32_t* __restrict__ var_phase, double2* __restrict__ out) {
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= P * S) return;                      // whole warps leave together
+  const int v = row / P, p = row - v * P;
+  const bool rec = var_rec[v] != 0;
+  const int q = var_phase[v];
+  const double2* xp = xt + (size_t)p * n;
+  double2* op = out + ((size_t)v * P + p) * Nz;
+  double2 ce = make_double2(0.0, 0.0), co = make_double2(0.0, 0.0);   // carries of the two parities
+  for (int c0 = 0; c0 < Nz; c0 += 64) {
+    const int me = c0 + 2 * lane, mo = me + 1;
+    double2 ye = me < Nz ? cipow_d(xp[col_map[v * Nz + me]], q) : make_double2(0.0, 0.0);
+    double2 yo = mo < Nz ? cipow_d(xp[col_map[v * Nz + mo]], q) : make_double2(0.0, 0.0);
+    if (rec) {
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const double ex = __shfl_up_sync(0xffffffffu, ye.x, d), ey = __shfl_up_sync(0xffffffffu, ye.y, d);
+        const double ox = __shfl_up_sync(0xffffffffu, yo.x, d), oy = __shfl_up_sync(0xffffffffu, yo.y, d);
+        if (lane >= d) {
+          ye.x += ex; ye.y += ey;
+          yo.x += ox; yo.y += oy;
+        }
+      }
+      ye.x += ce.x; ye.y += ce.y;
+      yo.x += co.x; yo.y += co.y;
+      ce = make_double2(__shfl_sync(0xffffffffu, ye.x, 31), __shfl_sync(0xffffffffu, ye.y, 31));
+      co = make_double2(__shfl_sync(0xffffffffu, yo.x, 31), __shfl_sync(0xffffffffu, yo.y, 31));
+    }
+    if (me < Nz) op[me] = ye;
+    if (mo < Nz) op[mo] = yo;
   }
 }
 
 cudaError_t launch_adj_tinvh(cudaStream_t s, int P, int Nz, int S, int n, const double2* xt_bar,
                              const int32_t* col_map, const int32_t* var_rec, const int32_t* var_phase,
                              double2* out) {
-  k_adj_tinvh<<<(P * S + 127) / 128, 128, 0, s>>>(P, Nz, S, n, xt_bar, col_map, var_rec, var_phase, out);
+  const size_t threads = (size_t)P * S * 32;
+  k_adj_tinvh<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(P, Nz, S, n, xt_bar, col_map, var_rec, var_phase,
+                                                                out);
   return cudaGetLastError();
 }
 

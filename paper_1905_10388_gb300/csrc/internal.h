@@ -54,6 +54,10 @@ struct SpikeArgs {
 constexpr int SPIKE_MAX_PENCILS = 608;
 constexpr int SPIKE_MIN_ROWS = 512;
 bool spike_supported(int kl, int kuu, int npad, int nblk);
+bool spike_bwd_supported(int kuu, int npad, int nblk);
+cudaError_t launch_spike_coupling_bwd(cudaStream_t s, int P, int npad, int nblk, int kuu, int upad, const double* U,
+                                      double* E);
+cudaError_t launch_spike_backward(cudaStream_t st, const SpikeArgs& s);
 cudaError_t launch_spike_coupling(cudaStream_t s, int P, int npad, int nblk_f, int nblk, int kl, int kuu, int lpad,
                                   int upad, const BandFactor& f);
 // forward blocks of the partitioned substitution: 128 rows, or 64 or 32 when
@@ -156,9 +160,11 @@ struct SolveArgs {
   DevStatus* status;
   // mode 0: assembly, substitution and epilogue in one kernel; 1: assembly
   // only, B~ to bg [p][n]; 2: epilogue only, from xg [p][n] (x~ = y / U_jj)
-  // (the substitution then runs in k_pencil_lanes)
+  // (the substitution then runs in k_pencil_lanes or the partitioned
+  // kernels); 3: assembly and forward substitution, y = L^-1 P B~ to yg
+  // [p][n] (the partitioned back substitution follows)
   int mode;
-  double2* bg; const double2* xg;
+  double2* bg; const double2* xg; double2* yg;
   // factor in the lane-interleaved layout (null: not available)
   const double* Lg; const double* Ug; const uint8_t* pg; const unsigned long long* umask; int cmax;
   // coupling matrices of the partitioned substitution (null: not available)

@@ -378,7 +378,36 @@ __global__ void __launch_bounds__(SPK_REC_WARPS * 32) k_spike_bwd_rec(SpikeArgs 
 }
 
 bool spike_supported(int kl, int kuu, int npad, int nblk) {
-  return kl <= SPK_FS && kuu < SPK_BW && nblk >= 1 && npad % (nblk * SPK_CHUNK) == 0;
+  return kl <= SPK_FS && spike_bwd_supported(kuu, npad, nblk);
+}
+
+bool spike_bwd_supported(int kuu, int npad, int nblk) {
+  return kuu < SPK_BW && nblk >= 1 && npad % (nblk * SPK_CHUNK) == 0;
+}
+
+// the back substitution's coupling matrices alone, for factors whose lower
+// band is wider than the forward windows (the transposed factor of the
+// adjoint: kl' = ku)
+cudaError_t launch_spike_coupling_bwd(cudaStream_t s, int P, int npad, int nblk, int kuu, int upad, const double* U,
+                                      double* E) {
+  if (!spike_bwd_supported(kuu, npad, nblk) || upad != SPK_BW) return cudaErrorInvalidValue;
+  const long long total = (long long)P * nblk * kuu;
+  k_spike_coupling<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(P, npad, 0, nblk, 0, kuu, 0, upad, nullptr,
+                                                                  nullptr, U, nullptr, E);
+  return cudaGetLastError();
+}
+
+// y (yg) -> x~ = y / U_jj (xg): the back substitution's two passes and their
+// recurrence (the forward substitution done elsewhere)
+cudaError_t launch_spike_backward(cudaStream_t st, const SpikeArgs& s) {
+  if (!spike_bwd_supported(s.kuu, s.npad, s.nblk) || s.m * s.nblk != s.npad || s.upad != SPK_BW)
+    return cudaErrorInvalidValue;
+  k_spike_bwd<1><<<s.P * (s.nblk > 1 ? s.nblk - 1 : 1), 64, 0, st>>>(s);
+  if (s.nblk > 1) {
+    k_spike_bwd_rec<<<s.P * 2, SPK_REC_WARPS * 32, 0, st>>>(s);
+    k_spike_bwd<2><<<s.P * (s.nblk - 1), 64, 0, st>>>(s);
+  }
+  return cudaGetLastError();
 }
 
 // B~ (bg) -> x~ = y / U_jj (xg) through y (yg); five launches
