@@ -9,7 +9,9 @@ device buffers, twice in a row with different fields and sizes, and checks
 each result against the FP64 oracle's backward transform (Chebyshev z, then
 Fourier x, Sec. "Scaled transforms & dealiasing") and against
 ``sp_transform`` (which allocates its own scratch), to the FP64 transform
-tolerance used elsewhere (1e-13 relative).  It lives in a file of its own
+tolerance used elsewhere (1e-13 relative); then, after that eager set-up,
+captures a call into a CUDA graph on a side stream, replays the graph and
+checks the result against the oracle again.  It lives in a file of its own
 that pytest collects last.
 """
 import ctypes
@@ -59,6 +61,34 @@ def test_static_backward_two_calls_in_a_row():
         assert rel_err(got, oracle_grid) < 1e-13
         assert rel_err(got, ref) < 1e-13
     ctx.close()
+
+
+def test_static_backward_inside_a_captured_graph():
+    n_x, n_z, scale, nf = 64, 32, (3, 2), 3
+    rng = np.random.default_rng(5)
+    c = rng.standard_normal((nf, n_x // 2, n_z)) + 1j * rng.standard_normal((nf, n_x // 2, n_z))
+    c[:, 0, :] = c[:, 0, :].real
+    ngx, ngz = n_x * scale[0] // scale[1], n_z * scale[0] // scale[1]
+    sysr = orb.RB2D(n_x, n_z, 1e6)
+    oracle_grid = np.stack([sysr.to_grid(c[f], ngx, ngz) for f in range(nf)])
+    _static_backward(c, n_x, n_z, scale)              # eager: the per-device set-up
+    src = torch.from_numpy(np.ascontiguousarray(c).view(np.float64)).cuda()
+    dst = torch.zeros(nf * ngz * ngx, dtype=torch.float64, device="cuda")
+    err = ctypes.create_string_buffer(256)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        st = _lib.lib().sp_transform_backward_static(
+            ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), nf, n_x, n_z,
+            scale[0], scale[1], ctypes.c_void_p(side.cuda_stream), err, len(err))
+    assert st == _lib.SP_OK, err.value.decode()
+    torch.cuda.synchronize()
+    dst.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    got = dst.cpu().numpy().reshape(nf, ngz, ngx)
+    assert rel_err(got, oracle_grid) < 1e-13
 
 
 def test_static_backward_rejects_oversize():
