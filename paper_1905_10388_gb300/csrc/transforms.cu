@@ -478,8 +478,9 @@ __global__ void __launch_bounds__(Z_THREADS) k_cheb_forward_batched(const ZDesc*
   });
 }
 constexpr int Y_TILE = 4;
+// FP32: 48 registers, five CTAs per SM (about 27 KB of shared memory each)
 template <typename T>
-__global__ void __launch_bounds__(Z_THREADS) k_fourier_y(YDesc d) {
+__global__ void __launch_bounds__(Z_THREADS, sizeof(T) == 8 ? 3 : 5) k_fourier_y(YDesc d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fourier_y_body<T, Y_TILE>(d, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
