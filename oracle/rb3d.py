@@ -76,7 +76,8 @@ class RB3D:
     Chebyshev mode.
     """
 
-    def __init__(self, n_x, n_y, n_z, Ra, Pr=1.0, L_x=4.0, L_y=4.0, dealias=1.5, lu_method="auto"):
+    def __init__(self, n_x, n_y, n_z, Ra, Pr=1.0, L_x=4.0, L_y=4.0, dealias=1.5, lu_method="auto",
+                 cheb_method="mmt"):
         self.Nx, self.Ny, self.Nz = int(n_x), int(n_y), int(n_z)
         self.Lx, self.Ly = float(L_x), float(L_y)
         self.Ra, self.Pr = float(Ra), float(Pr)
@@ -93,6 +94,15 @@ class RB3D:
         self.Ngz = int(round(dealias * self.Nz))
         self.var = {v: i for i, v in enumerate(RB3D_VARIABLES)}
         self.lu_method = lu_method
+        # "mmt": explicit T_n(x_i) quadrature (default); "dct": scipy DCT, the
+        # same definition summed in another order, with numpy's derivative
+        # recurrence for the initial bz (as in the 2D oracle): a rounding-floor
+        # variant
+        self.cheb_method = cheb_method
+        if cheb_method == "dct":
+            self._cf, self._cb = bases.chebyshev_forward_dct, bases.chebyshev_backward_dct
+        else:
+            self._cf, self._cb = bases.chebyshev_forward, bases.chebyshev_backward
         self._mats = None
 
     # -- pencils ------------------------------------------------------------
@@ -120,7 +130,7 @@ class RB3D:
         n_gy = self.Ngy if n_gy is None else n_gy
         n_gz = self.Ngz if n_gz is None else n_gz
         c3 = np.asarray(c).reshape(self.Ny, self.K, self.Nz)
-        gz = bases.chebyshev_backward(c3, n_gz, axis=2)           # [iy, ix, zg]
+        gz = self._cb(c3, n_gz, axis=2)                           # [iy, ix, zg]
         gy = bases.fourier_c_backward(gz, n_gy, axis=0)           # [yg, ix, zg]
         g = bases.fourier_backward(gy, n_gx, axis=1)              # [yg, xg, zg]
         return np.transpose(g, (2, 0, 1)).copy()
@@ -129,7 +139,7 @@ class RB3D:
         """Real grid g[z, y, x] -> coefficients c[p, n] (x, then y, then z)."""
         fx = bases.fourier_forward(g, self.Nx, axis=2)            # [z, y, ix]
         fy = bases.fourier_c_forward(fx, self.Ny, axis=1)         # [z, iy, ix]
-        c = bases.chebyshev_forward(fy, self.Nz, axis=0)          # [n, iy, ix]
+        c = self._cf(fy, self.Nz, axis=0)                         # [n, iy, ix]
         return np.transpose(c, (1, 2, 0)).reshape(self.P, self.Nz).copy()
 
     def dx(self, c):
@@ -163,7 +173,11 @@ class RB3D:
         X = np.zeros((self.S, self.P, self.Nz), dtype=np.complex128)
         cb = self.to_coeff(b_grid)
         X[self.var["b"]] = cb
-        X[self.var["bz"]] = bases.chebyshev_derivative(cb, 0.0, 1.0, axis=1)
+        if self.cheb_method == "dct":
+            import numpy.polynomial.chebyshev as C
+            X[self.var["bz"], :, : self.Nz - 1] = C.chebder(cb, m=1, scl=2.0, axis=1)
+        else:
+            X[self.var["bz"]] = bases.chebyshev_derivative(cb, 0.0, 1.0, axis=1)
         return X
 
     def conductive_state(self):

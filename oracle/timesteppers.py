@@ -87,9 +87,9 @@ class PencilLU:
 
     method "auto": dense LAPACK getrf up to DENSE_LIMIT rows, else SuperLU
     with COLAMD column ordering; "natural": SuperLU in the natural column
-    order (partial pivoting, the elimination order of a band solver).  Both
-    solve the same systems; the second gives another rounding order for
-    floor estimates.
+    order (partial pivoting, the elimination order of a band solver);
+    "dense": dense LAPACK getrf at any size.  All solve the same systems; the
+    others give other rounding orders for floor estimates.
     """
 
     def __init__(self, mats, a, b, method="auto"):
@@ -98,7 +98,7 @@ class PencilLU:
             A = (a * M + b * L)
             if method == "natural":
                 self.factors.append(("sparse", spla.splu(sps.csc_matrix(A), permc_spec="NATURAL")))
-            elif A.shape[0] <= DENSE_LIMIT:
+            elif method == "dense" or A.shape[0] <= DENSE_LIMIT:
                 self.factors.append(("dense", sla.lu_factor(A.toarray())))
             else:
                 self.factors.append(("sparse", spla.splu(sps.csc_matrix(A))))
