@@ -996,6 +996,7 @@ sp_status build_batch(sp_ctx* ctx, const std::vector<Problem*>& ps, const std::v
       xv.push_back(xdesc_rows(ps[q]));
       zfv.push_back(zdesc_forward(ps[q], plans[q][i].fc_out));
       av.push_back(plans[q][i].args);
+      av.back().fwd16 = 1;            // throughput-bound: both parts' forward in one warp
       fill_f_halves(av.back());
     }
     BatchStage st;

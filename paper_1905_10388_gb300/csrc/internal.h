@@ -165,6 +165,11 @@ struct SolveArgs {
   // [p][n] (the partitioned back substitution follows)
   int mode;
   double2* bg; const double2* xg; double2* yg;
+  // 1: with kl <= 15, one warp runs both parts' forward substitution in two
+  // 16-lane windows (half the FP64 issue; the batched solve, bound by the
+  // FP64 pipe, sets it; a lone problem's whole-row chains are bound by their
+  // latency and keep a 32-lane window per part)
+  int fwd16;
   // factor in the lane-interleaved layout (null: not available)
   const double* Lg; const double* Ug; const uint8_t* pg; const unsigned long long* umask; int cmax;
   // coupling matrices of the partitioned substitution (null: not available)
