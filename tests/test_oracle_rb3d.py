@@ -7,7 +7,11 @@
 * the linear growth rate depends on (k_x, k_y) only through |k| (rotation
   invariance), and an oblique wave at |k| = k_c is marginal at the textbook
   Ra_c (tests/golden/rb_onset.txt);
-* the conductive state is an exact steady state of the nonlinear step.
+* the conductive state is an exact steady state of the nonlinear step;
+* the rounding-floor variants (DCT transforms with numpy's derivative
+  recurrence, dense LAPACK or natural-order SuperLU for the pencils) step a
+  random state to the default's result up to rounding, so they compute the
+  same thing.
 """
 import os
 
@@ -109,3 +113,23 @@ def test_conductive_state_is_steady():
     for _ in range(2):
         X = st.step(X, 1e-2)
     assert np.abs(X - X0).max() < 1e-12
+
+
+def test_rounding_floor_variants_agree():
+    args = (8, 8, 16, 1e6)
+    noise = np.random.default_rng(4).standard_normal((16, 8, 8)) * 30.0
+    ref = None
+    for cheb, lu in (("mmt", "auto"), ("dct", "auto"), ("mmt", "dense"), ("mmt", "natural")):
+        sysr = rb3d.RB3D(*args, cheb_method=cheb, lu_method=lu)
+        X = sysr.initial_state(noise)
+        st = ts.RungeKuttaIMEX(sysr, ts.RK222)
+        for _ in range(2):
+            X = st.step(X, 1e-3)
+        if ref is None:
+            ref = X
+            continue
+        for i, v in enumerate(rb3d.RB3D_VARIABLES):
+            nr = np.linalg.norm(ref[i])
+            err = np.linalg.norm(X[i] - ref[i]) / max(nr, 1e-300)
+            assert err < 1e-9 or np.linalg.norm(X[i] - ref[i]) < 1e-14, (cheb, lu, v, err)
+
