@@ -310,10 +310,15 @@ sp_status make_plan(sp_ctx* ctx, Problem* pr, int Nc, int Ng, TransformPlan** ou
 }
 
 // the partitioned back substitution starts its blocks from the previous
-// solve's inflows (spike.cu); zero them
+// solve's inflows (spike.cu); zero them, the transposed solves' too, so that
+// a run (or a gradient) from a set state repeats bit for bit
 cudaError_t reset_spike_guess(Problem* pr, cudaStream_t s) {
-  if (!pr->spike || !pr->d_sp_u) return cudaSuccess;
-  return cudaMemsetAsync(pr->d_sp_u, 0, (size_t)pr->P * pr->nblk * 2 * 32 * sizeof(double), s);
+  if (!pr->spike) return cudaSuccess;
+  const size_t bytes = (size_t)pr->P * pr->nblk * 2 * 32 * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (pr->d_sp_u) e = cudaMemsetAsync(pr->d_sp_u, 0, bytes, s);
+  if (e == cudaSuccess && pr->d_spT_u) e = cudaMemsetAsync(pr->d_spT_u, 0, bytes, s);
+  return e;
 }
 
 // Blocks per pencil of the partitioned back substitution: about 1024 / P
