@@ -244,7 +244,11 @@ sp_status sp_set_batch_persistent(sp_ctx* ctx, int nproblems, const int* problem
  * (re, im) components.
  * sp_adjoint_init: after sp_factor, factors the transposed pencils
  *   A~^T = M~^T + dt H_ii L~^T (banded LU with partial pivoting, FP64) and
- *   allocates the adjoint work buffers.
+ *   allocates the adjoint work buffers; for problems on the partitioned
+ *   substitution it also computes the transposed factor's back-substitution
+ *   coupling matrices (the transposed solves substitute forward whole-row,
+ *   since kl' = ku is wider than the partitioned forward windows, and back
+ *   in blocks) and zeroes their inflow guesses.
  * sp_step_adjoint: given the states of one forward step (states_dev,
  *   device, nstates consecutive arrays of S*P*N_z complex: X^n alone
  *   (nstates = 1; the first stage is then recomputed from X^n) or X^n
